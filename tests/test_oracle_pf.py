@@ -1,0 +1,185 @@
+"""Pins of the FP64 phasor-field (radial RSD) oracle.
+
+Each test compares the oracle with something other than itself: the paper's
+worked example, tabulated values and the integral definition of J0, the
+analytic 2D Fourier transform of a ring computed by angular quadrature, the
+closed-form Hankel transform of a Gaussian, focusing of rendered point
+reflectors, and the direct spatial RSD summation.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import pf, rsd_direct
+from paper_2608_28183_gb300 import synth
+
+C = synth.C_LIGHT
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _peak(vol):
+    return np.unravel_index(int(np.argmax(vol)), vol.shape)
+
+
+def test_worked_example_radial_sampling():
+    """Supplementary worked example: 190 x 190 non-confocal capture."""
+    g = json.load(open(os.path.join(GOLDEN, "pf_worked_example.json")))
+    N = g["grid"]
+    dx = math.sqrt(2.0) / (2.0 * g["rho_max_per_m"])     # square pitch giving the printed rho_max
+    for lam_min in (0.02969, 0.0299, 0.03000):            # inside [2.968, 3.001) cm
+        rs = pf.radial_sampling(N, N, dx, dx, g["sigma_s"], lam_min)
+        assert rs.nyquist_rings == g["n_rings_nyquist_minimum"]
+        assert rs.n_r == g["n_rings"]
+        assert rs.nyquist_rho == g["n_rho_minimum"]
+        assert rs.n_rho == g["n_rho"]
+        assert round(rs.rho_max, 2) == g["rho_max_per_m"]
+        assert round(rs.rho_cut, 2) == g["rho_cutoff_per_m"]
+        rs2 = pf.radial_sampling(N, N, dx, dx, 2, lam_min)
+        assert rs2.n_r == g["n_rings_confocal"]
+
+
+def test_j0_against_table_and_integral_definition():
+    """J0 used by the ring basis matches A&S tables and its integral form
+    J0(x) = (1/pi) int_0^pi cos(x sin th) dth."""
+    from scipy import special
+    for line in open(os.path.join(GOLDEN, "j0_values.txt")):
+        if line.startswith("value"):
+            _, x, v = line.split()
+            assert abs(special.j0(float(x)) - float(v)) < 1e-14
+        elif line.startswith("zero"):
+            _, _, v = line.split()
+            assert abs(special.j0(float(v))) < 1e-14
+    th = (np.arange(4096) + 0.5) * (np.pi / 4096)
+    for x in (0.3, 2.0, 7.5, 21.0):
+        quad = np.mean(np.cos(x * np.sin(th)))
+        assert abs(special.j0(x) - quad) < 1e-12
+
+
+def test_ring_basis_is_ring_fourier_transform():
+    """B(r, rho) = 2 pi r J0(2 pi r rho) equals the 2D Fourier transform of a
+    unit ring of radius r: r int_0^{2 pi} exp(-2 pi i rho r cos th) dth."""
+    th = np.arange(2048) * (2 * np.pi / 2048)
+    for r in (0.05, 0.4, 1.3):
+        for rho in (0.0, 0.7, 5.0, 31.0):
+            ft = r * np.sum(np.exp(-2j * np.pi * rho * r * np.cos(th))) * (2 * np.pi / 2048)
+            B = pf.ring_basis(np.array([r]), np.array([rho]))[0, 0]
+            assert abs(ft.imag) < 1e-10
+            assert abs(ft.real - B) < 1e-10 * max(1.0, abs(B))
+
+
+def test_radial_quadrature_hankel_gaussian():
+    """Trapezoid ring quadrature of Eq. 6 reproduces the closed-form Hankel
+    transform int_0^inf exp(-r^2/(2 s^2)) 2 pi r J0(2 pi r rho) dr
+    = 2 pi s^2 exp(-2 pi^2 s^2 rho^2)."""
+    s = 0.3
+    n_r = 1024
+    r_max = 3.0
+    dr = r_max / (n_r - 1)
+    r = np.arange(n_r) * dr
+    q = pf.trapezoid_weights(n_r, dr)
+    assert np.isclose(q.sum(), r_max)
+    rho = np.linspace(0.0, 3.0, 40)
+    K = pf.ring_integral(np.exp(-r ** 2 / (2 * s * s)), r, q, rho)
+    exact = 2 * np.pi * s * s * np.exp(-2 * np.pi ** 2 * s * s * rho ** 2)
+    # trapezoid error for an integrand starting as 2 pi r: (dr^2 / 12) * 2 pi
+    bound = 2 * (dr * dr / 12) * 2 * np.pi
+    np.testing.assert_allclose(K, exact, atol=bound)
+    assert np.max(abs(K - exact)) > 0.25 * bound / 2   # the error is the quadrature's, not noise
+
+
+def test_taper_endpoints_and_smoothness():
+    rc = 300.25
+    a = pf.taper(np.array([0.0, rc - 8.0, rc - 4.0, rc - 1e-9, rc, rc + 3.0]), rc)
+    np.testing.assert_allclose(a, [1.0, 1.0, 0.5, 0.0, 0.0, 0.0], atol=1e-8)
+    x = np.linspace(rc - 9, rc + 1, 2001)
+    d = np.diff(pf.taper(x, rc))
+    assert np.all(d <= 1e-15)                       # monotone non-increasing
+    assert np.max(abs(np.diff(d))) < 1e-4           # no jumps in slope (C1)
+
+
+def test_band_of_virtual_wave_config2():
+    """Band of the 128 x 128, 2 m, 1024 x 16 ps workload (derived from the
+    stated virtual-wave reading; the paper prints no band for it)."""
+    p = pf.make_plan(128, 128, 1024, 16e-12, 2.0, 2.0, 4, 0.5, 2.5)
+    b = p.band
+    assert (b.k0, b.k_half, len(b.bins), b.bins[0], b.bins[-1]) == (79, 75, 151, 4, 154)
+    assert np.argmax(b.weights) == np.argmin(abs(b.bins - b.k0))
+    assert (p.radial.n_r, p.radial.n_rho) == (512, 512)
+    assert np.isclose(p.radial.rho_cut, p.radial.rho_max)
+
+
+def test_phasor_sign_and_band_indexing():
+    """A cosine at band bin k with phase phi gives P_k = (n/2) e^{+i phi}
+    (forward DFT sign e^{-i}) and nothing at the other band bins."""
+    p = pf.make_plan(4, 4, 128, 50e-12, 0.4, 0.4, 2, 0.3, 0.6)
+    n = 128
+    k = int(p.band.bins[len(p.band.bins) // 2])
+    phi = 0.7
+    t = np.arange(n)
+    H = np.broadcast_to(np.cos(2 * np.pi * k * t / n + phi), (4, 4, n)).copy()
+    P = pf.phasor_field(H, p)
+    fi = int(np.where(p.band.bins == k)[0][0])
+    np.testing.assert_allclose(P[..., fi], (n / 2) * np.exp(1j * phi), atol=1e-9)
+    others = np.delete(P, fi, axis=2)
+    assert np.max(abs(others)) < 1e-9
+
+
+def test_cos_sin_linearity_identity():
+    """Propagating P_cos and P_sin separately and combining equals propagating
+    the complex phasor once (offline-RSD identity of the supplementary)."""
+    p = pf.make_plan(8, 8, 256, 32e-12, 0.6, 0.6, 6, 0.4, 0.9)
+    rng = np.random.default_rng(5)
+    F = len(p.band.bins)
+    Pc = rng.standard_normal((8, 8, F))
+    Ps = rng.standard_normal((8, 8, F))
+    lhs = pf.propagate(Pc, p) + 1j * pf.propagate(Ps, p)
+    rhs = pf.propagate(Pc + 1j * Ps, p)
+    np.testing.assert_allclose(lhs, rhs, atol=1e-12 * np.abs(rhs).max())
+
+
+@pytest.mark.parametrize("geom,pt,depths", [
+    (synth.Geometry(32, 32, 512, 16e-12, 1.0, 1.0), (0.12, -0.2, 0.9), (32, 0.4, 1.2)),
+    (synth.Geometry(24, 32, 512, 16e-12, 0.9, 1.2), (-0.2, 0.1, 0.8), (24, 0.5, 1.1)),
+])
+def test_point_reflector_focus(geom, pt, depths):
+    """A single point reflector reconstructs at the nearest depth plane (+-1)
+    and within one lateral voxel."""
+    p = pf.make_plan(geom.nx, geom.ny, geom.nt, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m,
+                     *depths)
+    cap = synth.point_capture(geom, [(*pt, 1.0)])
+    I = pf.pf_reconstruct(cap.counts, p)
+    got = _peak(I)
+    xs = synth.wall_coords(geom.nx, geom.wall_w_m)
+    ys = synth.wall_coords(geom.ny, geom.wall_h_m)
+    exp = (np.argmin(abs(xs - pt[0])), np.argmin(abs(ys - pt[1])), np.argmin(abs(p.depths - pt[2])))
+    assert all(abs(int(g) - int(e)) <= 1 for g, e in zip(got, exp)), (got, exp)
+
+
+def test_agrees_with_direct_rsd_peak():
+    """On 16 x 16 grids the radial operator and the direct spatial RSD sum
+    (no FFT, no radial approximation) have the same peak voxel."""
+    geom = synth.Geometry(16, 16, 512, 16e-12, 1.0, 1.0)
+    for pt in [(0.1, 0.15, 0.8), (-0.2, -0.05, 0.65)]:
+        p = pf.make_plan(16, 16, 512, 16e-12, 1.0, 1.0, 24, 0.5, 1.1)
+        cap = synth.point_capture(geom, [(*pt, 1.0)])
+        I = pf.pf_reconstruct(cap.counts, p)
+        P = pf.phasor_field(cap.counts, p)
+        Id = np.abs(rsd_direct.rsd_direct(P, p.band.freqs, p.band.weights, p.depths, 1.0, 1.0))
+        assert _peak(I) == _peak(Id), (_peak(I), _peak(Id))
+
+
+def test_lerp_index_rules():
+    """Neighbour indices never exceed the cutoff bin, and interpolation is
+    exact for a kernel that is linear in rho."""
+    n_rho = 64
+    rb = np.linspace(0, 63, 500)
+    for rc in (63.0, 40.5):
+        i0, i1, al = pf.lerp_indices(rb, rc, n_rho)
+        assert np.all(i1 <= math.floor(rc)) and np.all(i0 >= 0) and np.all(i1 >= i0)
+        lin = 3.0 + 0.5 * np.arange(n_rho)
+        inside = rb <= math.floor(rc)
+        np.testing.assert_allclose(((1 - al) * lin[i0] + al * lin[i1])[inside],
+                                   (3.0 + 0.5 * rb)[inside], atol=1e-12)
