@@ -1,0 +1,173 @@
+/*
+ * nlos.h - C ABI of the GB300 wave-based NLOS reconstruction library
+ * (confocal f-k migration and radial phasor-field RSD reconstruction).
+ *
+ * Conventions shared by every entry point
+ *   - Transient input H is [x][y][t] (t fastest, "index-major" temporal bins,
+ *     Sec. 4.1/4.2), nx * ny * nt elements of the plan's storage type:
+ *     float32 (NLOS_F32), IEEE half (NLOS_F16) or bfloat16 (NLOS_BF16).
+ *   - Output volume is float32 [x][y][z] (z fastest), nx * ny * nz elements:
+ *       f-k:     nz = nt, voxel (i, j, k) = |Psi|^2 at depth k * c * dt / 2
+ *                (Eq. 2), wall sample (i, j);
+ *       phasor:  nz = n_depths, |I| on depth plane d_min + k (d_max - d_min)/(D-1).
+ *   - Device pointers are caller-owned device memory; the library never frees
+ *     or retains them after the call's work completes. Calls are asynchronous
+ *     on `stream` (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream) unless stated otherwise; inputs are never modified.
+ *   - A plan owns its constant tables and one default workspace. Two calls
+ *     that use the same workspace must not overlap on the device; use
+ *     nlos_reconstruct_ws with distinct workspaces for concurrent calls.
+ *   - No exception crosses the ABI. Every call returns nlos_status_t; on
+ *     failure nlos_last_error() (per thread) describes it. Invalid arguments
+ *     are rejected before any device work is enqueued.
+ *   - Every step runs on the GPU in this library's kernels; there is no CPU
+ *     fallback.
+ */
+#ifndef NLOS_H_
+#define NLOS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { NLOS_FK = 0, NLOS_PHASOR_RSD = 1 } nlos_method_t;
+typedef enum { NLOS_F32 = 0, NLOS_F16 = 1, NLOS_BF16 = 2 } nlos_storage_t;
+typedef enum {
+  NLOS_OK = 0,
+  NLOS_ERR_INVALID_ARG = 1,
+  NLOS_ERR_OUT_OF_MEMORY = 2,
+  NLOS_ERR_CUDA = 3,
+  NLOS_ERR_UNSUPPORTED = 4,
+  NLOS_ERR_TIMEOUT = 5
+} nlos_status_t;
+
+typedef struct nlos_plan_s* nlos_plan_t;
+
+/*
+ * Capture and method description (problem statement of Sec. 3: confocal
+ * transient H(x_s, x_s, t) sampled on an nx x ny wall grid over a
+ * wall_w_m x wall_h_m relay wall, nt bins of bin_width_s).
+ *   nx, ny        scan grid; powers of two in [8, 1024]
+ *   nt            time bins; power of two in [16, 2048] for f-k, [16, 4096] for phasor
+ *   bin_width_s   time-bin width dt (> 0)
+ *   wall_w_m/h_m  scanned wall extent along x / y (> 0); wall samples are cell centres
+ *   method        nlos_method_t
+ *   storage       nlos_storage_t of the input and of stored intermediates;
+ *                 reduced precision uses a per-volume scale, arithmetic is float32
+ *   pad_factor    2 (zero padding x2 on every axis, Sec. 4.2); 1 -> NLOS_ERR_UNSUPPORTED
+ * Phasor-field only (Sec. 4.3, Eqs. 4-7):
+ *   wavelength_m  virtual wavelength (0 -> 4 * wall_w_m / nx)
+ *   cycles        Gaussian virtual-wave width in periods (0 -> 5)
+ *   n_depths, depth_min_m, depth_max_m   D reconstruction planes, d_min..d_max
+ *   sigma_s, sigma_t   modality pair (0,0 -> confocal (2,0); (1,1) non-confocal)
+ *   delta_m       calibration path offset Delta (Eq. 4)
+ */
+typedef struct {
+  int nx, ny, nt;
+  double bin_width_s;
+  double wall_w_m, wall_h_m;
+  int method;
+  int storage;
+  int pad_factor;
+  double wavelength_m;
+  double cycles;
+  int n_depths;
+  double depth_min_m, depth_max_m;
+  int sigma_s, sigma_t;
+  double delta_m;
+} nlos_plan_desc_t;
+
+/* Fill *desc with defaults (f-k, float32, pad 2, cycles 5, confocal). */
+void nlos_plan_desc_default(nlos_plan_desc_t* desc);
+
+/*
+ * Build a plan: validates the description, generates the float64 tables
+ * (FFT twiddles, Stolt coordinate constants; for phasor fields the
+ * virtual-wave band, the radial kernel K_r(rho, f, d) of Eq. 6 and the
+ * pixel-to-radius chunks of the supplementary lookup), uploads them, and
+ * allocates the default workspace. Synchronous. *out receives an opaque
+ * handle owned by the caller until nlos_plan_destroy.
+ * Errors: INVALID_ARG (null pointer, sizes, extents <= 0, empty band),
+ * UNSUPPORTED (pad_factor 1, non-power-of-two sizes), OUT_OF_MEMORY, CUDA.
+ */
+nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out);
+
+/*
+ * Shape and byte counts of a plan: out_shape = {nx, ny, nz}; workspace_bytes
+ * is the size nlos_reconstruct_ws needs; input/output_bytes are the sizes of
+ * one transient and one volume. Any output pointer may be NULL.
+ */
+nlos_status_t nlos_plan_query(nlos_plan_t plan, size_t out_shape[3], size_t* workspace_bytes,
+                              size_t* input_bytes, size_t* output_bytes);
+
+/*
+ * Reconstruct one capture (f-k: Alg. 1/2 with Eq. 2; phasor: Alg. 4) from the
+ * device transient into the device volume, using the plan's workspace.
+ * Asynchronous on stream.
+ */
+nlos_status_t nlos_reconstruct(nlos_plan_t plan, const void* transient, void* volume, void* stream);
+
+/*
+ * Same as nlos_reconstruct with a caller-owned device workspace of at least
+ * workspace_bytes (from nlos_plan_query), 256-byte aligned. Lets several
+ * reconstructions of one plan run concurrently on different streams.
+ */
+nlos_status_t nlos_reconstruct_ws(nlos_plan_t plan, const void* transient, void* volume, void* workspace,
+                                  size_t workspace_bytes, void* stream);
+
+/*
+ * End-to-end call on HOST buffers: copies the transient host->device, runs
+ * nlos_reconstruct, copies the volume device->host and waits for completion
+ * (synchronous). Host buffers may be pageable or pinned; device staging
+ * buffers are owned by the plan.
+ */
+nlos_status_t nlos_reconstruct_host(nlos_plan_t plan, const void* transient_host, void* volume_host,
+                                    void* stream);
+
+/*
+ * Reconstruct n captures with one launch sequence each, forked over the
+ * library's internal streams so that small captures overlap on the device and
+ * joined back to `stream`. plans[i] describes capture i;
+ * workspaces[i] (each at least that plan's workspace_bytes) must be distinct;
+ * pass NULL for workspaces to use each plan's default workspace (then every
+ * plan may appear only once). Asynchronous on stream; may be captured into a
+ * CUDA graph.
+ */
+nlos_status_t nlos_reconstruct_batch(const nlos_plan_t* plans, const void* const* transients,
+                                     void* const* volumes, void* const* workspaces, int n, void* stream);
+
+/*
+ * Stage tracing. While enabled, every reconstruction with this plan records a
+ * CUDA event before its first stage and after each stage, on the call's
+ * stream (use one stream per plan while profiling).
+ */
+nlos_status_t nlos_plan_set_profiling(nlos_plan_t plan, int enable);
+
+/*
+ * Wait for the recorded events, add each stage's elapsed milliseconds into
+ * times_ms[0 .. min(capacity, *n_stages)), return the stage count and the
+ * number of profiled calls, and clear the record. Synchronous.
+ */
+nlos_status_t nlos_plan_stage_times(nlos_plan_t plan, double* times_ms, int capacity, int* n_stages,
+                                    long long* calls);
+
+/* Name of stage i of the plan's sequence (NULL if out of range). */
+const char* nlos_plan_stage_name(nlos_plan_t plan, int stage);
+
+/* Release the plan's tables, workspace and staging buffers (synchronises the device). */
+nlos_status_t nlos_plan_destroy(nlos_plan_t plan);
+
+/* Description of the calling thread's most recent failure ("" if none). */
+const char* nlos_last_error(void);
+
+/* Library version string. */
+const char* nlos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLOS_H_ */

@@ -1,0 +1,204 @@
+// f-k migration, temporal-frequency stage (Sec. 4.2, Alg. 1 Stolt step).
+//
+// The x/y transforms before this stage keep only kx in [0, a] of the real
+// input's spectrum (Hermitian half along x). Each stored pencil (kx, ky) is
+// transformed along t (length 2n, upper half zero) into U(kx, ky, m), held in
+// shared memory. The Stolt step reads U at the source coordinate
+// mu = sqrt(A + m^2), A = (n s_x p~/a)^2 + (n s_y q~/b)^2, with a two-tap
+// linear interpolation along the contiguous axis, weights it by Z/Z' = m/mu
+// and keeps 1 <= m <= n-1 with mu <= n-1 (Z > 0 and interpn's zero fill).
+// The same pencil also yields its Hermitian partner (-kx, -ky): there
+// U(-p~, -q~, k) = conj(U(p~, q~, -k)), so the partner's resampled spectrum is
+// conj(lerp(U[-k0], U[-k1])) * m/mu. Both resampled spectra are inverse
+// transformed (length 2n, only z < n kept) and written, so the Stolt output
+// never round-trips through global memory.
+//
+// mu is computed in float-float: A comes from float64 per-plan tables split
+// into (hi, lo) floats, m^2 is exact, and the square root gets one Newton
+// correction from an exact FMA residual. Plain float would put the
+// interpolation weight off by up to 6e-5 near m ~ 1000.
+#include "nlos_fft.cuh"
+#include "nlos_internal.h"
+
+namespace nlos {
+
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+
+struct StoltCoord {
+  int k0, k1;
+  float alpha, jac;
+  bool valid;
+};
+
+__device__ __forceinline__ StoltCoord stolt_coord(float Ahi, float Alo, int m, int n) {
+  StoltCoord c;
+  float2 s = two_sum(Ahi, (float)(m * m));
+  s = fast_two_sum(s.x, s.y + Alo);
+  const float y0 = sqrtf(s.x);
+  const float res = fmaf(-y0, y0, s.x) + s.y;     // (A + m^2) - y0^2
+  const float mlo = res * (0.5f / y0);            // mu = y0 + mlo
+  int k0 = (int)floorf(y0);
+  float al = (y0 - (float)k0) + mlo;
+  if (al < 0.f) {
+    k0 -= 1;
+    al += 1.f;
+  } else if (al >= 1.f) {
+    k0 += 1;
+    al -= 1.f;
+  }
+  c.valid = (k0 < n - 1) || (k0 == n - 1 && al == 0.f);
+  c.k0 = k0;
+  c.k1 = min(k0 + 1, n - 1);
+  c.alpha = al;
+  c.jac = (float)m / y0;
+  return c;
+}
+
+template <int L, class TS>
+struct FkFwdCtx {
+  const TS* g;
+  float2* U;
+  float2* W;
+  const float2* tw;
+  int n;
+  bool valid;
+  float ldmul;
+  __device__ __forceinline__ float2 load(int l) const {
+    if (!valid || l >= n) return make_float2(0.f, 0.f);
+    return cscale(Cpx<TS>::get(g + l), ldmul);
+  }
+  __device__ __forceinline__ float2& at(int l) const { return W[pad16(l)]; }
+  __device__ __forceinline__ void store(int l, float2 v) const { U[pad16(l)] = v; }
+};
+
+template <int L, class TS, bool kMirror>
+struct FkInvCtx {
+  const float2* U;
+  float2* W;
+  const float2* tw;
+  TS* out;
+  int n;
+  float Ahi, Alo;
+  bool do_store;
+  float stmul;
+  __device__ __forceinline__ float2 load(int m) const {
+    if (m < 1 || m > n - 1) return make_float2(0.f, 0.f);
+    const StoltCoord c = stolt_coord(Ahi, Alo, m, n);
+    if (!c.valid) return make_float2(0.f, 0.f);
+    float2 u0, u1;
+    if (!kMirror) {
+      u0 = U[pad16(c.k0)];
+      u1 = U[pad16(c.k1)];
+    } else {
+      u0 = U[pad16((L - c.k0) & (L - 1))];
+      u1 = U[pad16((L - c.k1) & (L - 1))];
+    }
+    float2 v = make_float2(fmaf(c.alpha, u1.x - u0.x, u0.x), fmaf(c.alpha, u1.y - u0.y, u0.y));
+    v = cscale(v, c.jac);
+    // inverse DFT as conj(DFT(conj(V))): the direct pencil loads conj(V); the
+    // partner's V is conj(lerp) * m/mu, whose conjugate is lerp * m/mu.
+    return kMirror ? v : cconj(v);
+  }
+  __device__ __forceinline__ float2& at(int l) const { return W[pad16(l)]; }
+  __device__ __forceinline__ void store(int l, float2 v) const {
+    if (do_store && l < n) Cpx<TS>::put(out + l, cscale(cconj(v), stmul));
+  }
+};
+
+template <int L> struct FkTile {
+  static constexpr int PPC = L <= 256 ? 8 : (L <= 1024 ? 4 : 2);   // pencils per CTA
+  static constexpr int THREADS = PPC * (L / 16);
+  static constexpr size_t SMEM = sizeof(float2) * 2 * PPC * FftShape<L>::SMEM;
+};
+
+template <int L, class TS>
+__global__ void __launch_bounds__(FkTile<L>::THREADS)
+fk_zstage_kernel(const FkZParams p) {
+  using S = FftShape<L>;
+  constexpr int PPC = FkTile<L>::PPC;
+  extern __shared__ float2 fk_sm[];
+  const int w = threadIdx.x / S::TPC;
+  const int j0 = threadIdx.x % S::TPC;
+  const long long pid = (long long)blockIdx.x * PPC + w;
+  const bool valid = pid < p.npencils;
+  const int twob = 2 * p.b;
+  const int kx = valid ? (int)(pid / twob) : 0;
+  const int ky = valid ? (int)(pid % twob) : 0;
+  float2* U = fk_sm + w * S::SMEM;
+  float2* W = fk_sm + (PPC + w) * S::SMEM;
+  const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
+  {
+    FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W, p.tw, p.n, valid, ldmul};
+    fft_run<L>(ctx, j0);
+  }
+  __syncthreads();
+  const float2 ax = p.ax[kx];
+  const float2 ay = p.ay[ky];
+  float2 A = two_sum(ax.x, ay.x);
+  A = fast_two_sum(A.x, A.y + (ax.y + ay.y));
+  TS* psi = static_cast<TS*>(p.psi);
+  const long long o_direct = ((long long)kx * twob + ky) * p.n;
+  const int mkx = (kx == 0) ? 0 : 2 * p.a - kx;
+  const int mky = (twob - ky) & (twob - 1);
+  const long long o_mirror = ((long long)mkx * twob + mky) * p.n;
+  {
+    FkInvCtx<L, TS, false> ctx{U, W, p.tw, psi + o_direct, p.n, A.x, A.y, valid, p.st_scale};
+    fft_run<L>(ctx, j0);
+  }
+  __syncthreads();
+  {
+    // run for every pencil so all threads meet the same barriers; stored only
+    // where the partner is not itself a stored pencil
+    FkInvCtx<L, TS, true> ctx{U, W, p.tw, psi + o_mirror, p.n, A.x, A.y,
+                              valid && kx > 0 && kx < p.a, p.st_scale};
+    fft_run<L>(ctx, j0);
+  }
+}
+
+template <int L, class TS>
+static cudaError_t launch_fk_one(const FkZParams& p, cudaStream_t s) {
+  using T = FkTile<L>;
+  auto k = fk_zstage_kernel<L, TS>;
+  if (T::SMEM > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  const long long blocks = (p.npencils + T::PPC - 1) / T::PPC;
+  k<<<(unsigned)blocks, T::THREADS, T::SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <class TS>
+static cudaError_t launch_fk_typed(const FkZParams& p, cudaStream_t s) {
+  switch (2 * p.n) {
+    case 32: return launch_fk_one<32, TS>(p, s);
+    case 64: return launch_fk_one<64, TS>(p, s);
+    case 128: return launch_fk_one<128, TS>(p, s);
+    case 256: return launch_fk_one<256, TS>(p, s);
+    case 512: return launch_fk_one<512, TS>(p, s);
+    case 1024: return launch_fk_one<1024, TS>(p, s);
+    case 2048: return launch_fk_one<2048, TS>(p, s);
+    case 4096: return launch_fk_one<4096, TS>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fk_zstage(const FkZParams& p, int storage, cudaStream_t s) {
+  if (p.npencils <= 0) return cudaErrorInvalidValue;
+  switch (storage) {
+    case kF32: return launch_fk_typed<float2>(p, s);
+    case kF16: return launch_fk_typed<__half2>(p, s);
+    case kBF16: return launch_fk_typed<__nv_bfloat162>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace nlos

@@ -1,0 +1,790 @@
+// Host side of the library: plan creation (float64 tables), the stage
+// sequences of f-k migration and phasor-field reconstruction, and the C ABI
+// declared in include/nlos.h.
+#include <math.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "nlos.h"
+#include "nlos_internal.h"
+
+namespace nlos {
+cudaError_t launch_axis_fft_f32(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f16(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_bf16(const AxisLaunch& l, cudaStream_t s);
+
+cudaError_t launch_axis_fft(const AxisLaunch& l, cudaStream_t s) {
+  switch (l.storage) {
+    case kF32: return launch_axis_fft_f32(l, s);
+    case kF16: return launch_axis_fft_f16(l, s);
+    case kBF16: return launch_axis_fft_bf16(l, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace nlos
+
+using namespace nlos;
+
+namespace {
+
+constexpr double kC = 299792458.0;   // speed of light, m/s
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTaperBins = 8.0;   // smoothstep width below the radial cutoff
+constexpr float kVolumeTarget = 4096.0f;   // ||scaled input||_2 for reduced-precision storage
+constexpr int kScalePartials = 512;
+constexpr int kBatchStreams = 8;
+
+thread_local std::string g_err;
+
+nlos_status_t fail(nlos_status_t st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+nlos_status_t cuda_fail(cudaError_t e, const char* where) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(NLOS_ERR_OUT_OF_MEMORY, "%s: %s", where, cudaGetErrorString(e));
+  return fail(NLOS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define NLOS_CU(call, where)                     \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2i(long long v) { int k = 0; while ((1LL << k) < v) ++k; return k; }
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+int ceil_int_guarded(double x) { return (int)ceil(x - 1e-9); }
+int pow2_at_least(int x) { int p = 1; while (p < x) p <<= 1; return p; }
+
+// per-pass scale keeping reduced-precision intermediates bounded: the
+// nearest power of two at or above 1/sqrt(L)
+float pass_scale(int storage, int L) {
+  if (storage == kF32) return 1.0f;
+  return ldexpf(1.0f, -(ilog2i(L) / 2));
+}
+
+size_t complex_bytes(int storage) { return storage == kF32 ? 8 : 4; }
+size_t real_bytes(int storage) { return storage == kF32 ? 4 : 2; }
+
+}  // namespace
+
+struct nlos_plan_s {
+  nlos_plan_desc_t d{};
+  int a = 0, b = 0, n = 0;
+  int storage = kF32;
+  int nz = 0;
+  std::map<int, float2*> tw;            // twiddle table per FFT length
+  // f-k Stolt constants
+  float2* ax = nullptr;
+  float2* ay = nullptr;
+  // phasor-field tables
+  int F = 0, D = 0, k_lo = 0, nchunks = 0, kr_storage = kF32;
+  float* w = nullptr;
+  void* Kr = nullptr;
+  int2* ch_i01 = nullptr;
+  int* ch_pix = nullptr;
+  float* ch_alpha = nullptr;
+  float* ch_acut = nullptr;
+  double kr_scale = 1.0;
+  // workspace layout: up to three complex buffers + scale scalars + partials
+  size_t off[3] = {0, 0, 0};
+  size_t off_scal = 0, off_part = 0;
+  size_t ws_bytes = 0;
+  void* ws = nullptr;
+  // host-call staging
+  void* d_in = nullptr;
+  void* d_out = nullptr;
+  std::vector<void*> allocs;
+  // stage tracing
+  std::vector<std::string> stage_names;
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_pool;
+  std::vector<int> prof_stage;          // stage index of each recorded event (-1: call start)
+  size_t prof_used = 0;
+};
+
+namespace {
+
+nlos_status_t dalloc(nlos_plan_s* p, void** ptr, size_t bytes, const char* what) {
+  cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return cuda_fail(e, what);
+  }
+  p->allocs.push_back(*ptr);
+  return NLOS_OK;
+}
+
+template <class T>
+nlos_status_t upload(nlos_plan_s* p, T** dst, const std::vector<T>& src, const char* what) {
+  void* ptr = nullptr;
+  nlos_status_t st = dalloc(p, &ptr, sizeof(T) * src.size(), what);
+  if (st != NLOS_OK) return st;
+  NLOS_CU(cudaMemcpy(ptr, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice), what);
+  *dst = static_cast<T*>(ptr);
+  return NLOS_OK;
+}
+
+// Stockham pass twiddle tables of an L-point transform (same schedule as
+// FftShape<L>): for pass p with span Ns and radix R, T_p[r Ns + k] =
+// exp(-2 pi i k r / (Ns R)), float64 then rounded to float.
+std::vector<float2> make_twiddles(int L) {
+  const int LOG = ilog2i(L), NFULL = LOG / 4, REM = LOG % 4;
+  const int npass = NFULL + (REM ? 1 : 0);
+  std::vector<float2> t;
+  int span = 1;
+  for (int pss = 0; pss < npass; ++pss) {
+    const int R = pss < NFULL ? 16 : (1 << REM);
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < span; ++k) {
+        const long long m = (long long)k * r;           // exponent over span*R
+        const double ang = -2.0 * kPi * (double)m / (double)(span * R);
+        t.push_back(make_float2((float)cos(ang), (float)sin(ang)));
+      }
+    span *= R;
+  }
+  return t;
+}
+
+nlos_status_t ensure_twiddles(nlos_plan_s* p, int L) {
+  if (p->tw.count(L)) return NLOS_OK;
+  float2* d = nullptr;
+  nlos_status_t st = upload(p, &d, make_twiddles(L), "twiddle upload");
+  if (st != NLOS_OK) return st;
+  p->tw[L] = d;
+  return NLOS_OK;
+}
+
+// (hi, lo) float pair of a float64 value
+float2 split_ff(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
+// ---------------------------------------------------------------------------
+// f-k plan: Stolt constants A_x(p) = (n s_x p~ / a)^2 with s_x = c dt / (2 dx)
+// (Alg. 1's s per axis), signed index p~ of the 2a-point padded axis.
+// ---------------------------------------------------------------------------
+nlos_status_t build_fk(nlos_plan_s* p) {
+  const auto& d = p->d;
+  const double dx = d.wall_w_m / d.nx, dy = d.wall_h_m / d.ny;
+  const double sx = kC * d.bin_width_s / (2.0 * dx);
+  const double sy = kC * d.bin_width_s / (2.0 * dy);
+  std::vector<float2> ax(2 * p->a), ay(2 * p->b);
+  for (int i = 0; i < 2 * p->a; ++i) {
+    const int pt = i < p->a ? i : i - 2 * p->a;
+    const double v = (double)p->n * sx * pt / p->a;
+    ax[i] = split_ff(v * v);
+  }
+  for (int i = 0; i < 2 * p->b; ++i) {
+    const int qt = i < p->b ? i : i - 2 * p->b;
+    const double v = (double)p->n * sy * qt / p->b;
+    ay[i] = split_ff(v * v);
+  }
+  nlos_status_t st;
+  if ((st = upload(p, &p->ax, ax, "stolt table")) != NLOS_OK) return st;
+  if ((st = upload(p, &p->ay, ay, "stolt table")) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, 2 * p->a)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, 2 * p->b)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, 2 * p->n)) != NLOS_OK) return st;
+  const size_t cb = complex_bytes(p->storage);
+  const long long a = p->a, b = p->b, n = p->n;
+  const size_t b0 = std::max((a + 1) * b * n, 2 * a * b * n) * cb;   // G1, then the y-inverse output
+  const size_t b1 = (a + 1) * 2 * b * n * cb;                         // G (kx <= a)
+  const size_t b2 = 2 * a * 2 * b * n * cb;                           // psi_z
+  p->off[0] = 0;
+  p->off[1] = align256(b0);
+  p->off[2] = p->off[1] + align256(b1);
+  p->off_scal = p->off[2] + align256(b2);
+  p->off_part = p->off_scal + 256;
+  p->ws_bytes = p->off_part + align256(sizeof(float) * kScalePartials);
+  p->nz = p->n;
+  return NLOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// phasor-field plan (Sec. 4.3 Eqs. 4-7, supplementary radial sampling)
+// ---------------------------------------------------------------------------
+double taper_weight(double rb, double rc) {
+  if (rb <= rc - kTaperBins) return 1.0;
+  if (rb >= rc) return 0.0;
+  const double t = (rc - rb) / kTaperBins;
+  return t * t * (3.0 - 2.0 * t);
+}
+
+nlos_status_t build_pf(nlos_plan_s* p) {
+  const auto& d = p->d;
+  const double dx = d.wall_w_m / d.nx, dy = d.wall_h_m / d.ny;
+  // virtual-wave band: f0 = c / lambda, sigma_t = cycles / (6 f0), +-5 sigma_f
+  const double lam = d.wavelength_m > 0 ? d.wavelength_m : 4.0 * dx;
+  const double cyc = d.cycles > 0 ? d.cycles : 5.0;
+  const double f0 = kC / lam;
+  const double df = 1.0 / (p->n * d.bin_width_s);
+  const int k0 = (int)llround(f0 / df);
+  const double sigma_f = 1.0 / (2.0 * kPi * (cyc / (6.0 * f0)));
+  const int kh = (int)llround(5.0 * sigma_f / df);
+  const int lo = std::max(1, k0 - kh), hi = std::min(p->n / 2 - 1, k0 + kh);
+  if (hi < lo) return fail(NLOS_ERR_INVALID_ARG, "virtual-wave band is empty (k0=%d, n=%d)", k0, p->n);
+  p->k_lo = lo;
+  p->F = hi - lo + 1;
+  std::vector<float> w(p->F);
+  std::vector<double> kappa(p->F);
+  for (int f = 0; f < p->F; ++f) {
+    const double fk = (lo + f) * df;
+    w[f] = (float)exp(-(fk - f0) * (fk - f0) / (2.0 * sigma_f * sigma_f));
+    kappa[f] = 2.0 * kPi * fk / kC;
+  }
+  const double lambda_min = kC / (hi * df);
+  // radial sampling over the padded aperture
+  const int Nu = 2 * p->a, Nv = 2 * p->b;
+  const double r_max = sqrt(pow(0.5 * Nu * dx, 2) + pow(0.5 * Nv * dy, 2));
+  const double rho_max = sqrt(pow(1.0 / (2.0 * dx), 2) + pow(1.0 / (2.0 * dy), 2));
+  const int sig_s = d.sigma_s > 0 ? d.sigma_s : 2;
+  const int sig_t = (d.sigma_s > 0 || d.sigma_t > 0) ? d.sigma_t : 0;
+  const int n_r = std::max(2, pow2_at_least(ceil_int_guarded(2.0 * sig_s * r_max / lambda_min) + 1));
+  const int n_rho = pow2_at_least(ceil_int_guarded(2.0 * r_max * rho_max) + 1);
+  const double dr = r_max / (n_r - 1);
+  const double rho_cut = std::min(rho_max, 0.5 * (n_r - 1) / r_max);
+  const double rc_bin = rho_cut * (n_rho - 1) / rho_max;
+  p->D = d.n_depths;
+  std::vector<double> depth(p->D), r(n_r), rho(n_rho);
+  for (int j = 0; j < p->D; ++j)
+    depth[j] = p->D == 1 ? d.depth_min_m : d.depth_min_m + j * (d.depth_max_m - d.depth_min_m) / (p->D - 1);
+  for (int j = 0; j < n_r; ++j) r[j] = j * dr;
+  for (int i = 0; i < n_rho; ++i) rho[i] = i * (rho_max / (n_rho - 1));
+  // ring basis with trapezoid weights (Eq. 5, Eq. 6), zero beyond the cutoff
+  std::vector<double> B((size_t)n_rho * n_r, 0.0);
+  for (int i = 0; i < n_rho; ++i) {
+    if (rho[i] > rho_cut) continue;
+    for (int j = 0; j < n_r; ++j) {
+      const double q = (j == 0 || j == n_r - 1) ? 0.5 * dr : dr;
+      B[(size_t)i * n_r + j] = q * 2.0 * kPi * r[j] * j0(2.0 * kPi * r[j] * rho[i]);
+    }
+  }
+  // radial kernel on the device in float64
+  double *dB = nullptr, *dr_ = nullptr, *dk = nullptr, *ddep = nullptr;
+  double2 *dA = nullptr, *dK64 = nullptr;
+  const long long NFD = (long long)p->F * p->D;
+  std::vector<void*> tmp;
+  auto tmp_alloc = [&](void** ptr, size_t bytes) -> cudaError_t {
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) tmp.push_back(*ptr); else cudaGetLastError();
+    return e;
+  };
+  auto free_tmp = [&]() { for (void* v : tmp) cudaFree(v); tmp.clear(); };
+  cudaError_t e = cudaSuccess;
+  if ((e = tmp_alloc((void**)&dB, sizeof(double) * B.size())) != cudaSuccess ||
+      (e = tmp_alloc((void**)&dr_, sizeof(double) * n_r)) != cudaSuccess ||
+      (e = tmp_alloc((void**)&dk, sizeof(double) * p->F)) != cudaSuccess ||
+      (e = tmp_alloc((void**)&ddep, sizeof(double) * p->D)) != cudaSuccess ||
+      (e = tmp_alloc((void**)&dA, sizeof(double2) * (size_t)n_r * NFD)) != cudaSuccess ||
+      (e = tmp_alloc((void**)&dK64, sizeof(double2) * (size_t)n_rho * NFD)) != cudaSuccess) {
+    free_tmp();
+    return cuda_fail(e, "radial kernel scratch");
+  }
+  cudaMemcpy(dB, B.data(), sizeof(double) * B.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(dr_, r.data(), sizeof(double) * n_r, cudaMemcpyHostToDevice);
+  cudaMemcpy(dk, kappa.data(), sizeof(double) * p->F, cudaMemcpyHostToDevice);
+  cudaMemcpy(ddep, depth.data(), sizeof(double) * p->D, cudaMemcpyHostToDevice);
+  KrBuildParams kp{dB, dr_, dk, ddep, n_rho, n_r, p->F, p->D, (double)sig_s, (double)sig_t, d.delta_m, dA, dK64};
+  e = launch_kr_build(kp, 0);
+  // stored kernel: float32 for float32 plans, float16 (scaled into range) otherwise
+  p->kr_storage = p->storage;
+  p->kr_scale = 1.0;
+  if (p->storage != kF32) {
+    const double bound = kPi * r_max * r_max;   // >= sum_j q_j 2 pi r_j |J0|
+    p->kr_scale = ldexp(1.0, (int)floor(log2(16384.0 / bound)));
+  }
+  void* Kr = nullptr;
+  nlos_status_t st = NLOS_OK;
+  if (e == cudaSuccess) {
+    st = dalloc(p, &Kr, complex_bytes(p->kr_storage) * (size_t)n_rho * NFD, "radial kernel");
+    if (st == NLOS_OK) e = launch_kr_store(dK64, Kr, (long long)n_rho * NFD, p->kr_storage, p->kr_scale, 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  free_tmp();
+  if (st != NLOS_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "radial kernel build");
+  p->Kr = Kr;
+  // pixel-to-radius lookup, grouped into chunks sharing (i0, i1)
+  struct Pix { int i0, i1, pix; float alpha, acut; };
+  std::vector<Pix> px;
+  px.reserve((size_t)Nu * Nv);
+  const int i_c = (int)floor(rc_bin);
+  const int last_base = std::max(0, std::min(i_c - 1, n_rho - 2));
+  for (int kx = 0; kx < Nu; ++kx) {
+    const double fx = (kx < Nu / 2 ? kx : kx - Nu) / (Nu * dx);
+    for (int ky = 0; ky < Nv; ++ky) {
+      const double fy = (ky < Nv / 2 ? ky : ky - Nv) / (Nv * dy);
+      const double rb = sqrt(fx * fx + fy * fy) * (n_rho - 1) / rho_max;
+      const double ac = taper_weight(rb, rc_bin);
+      if (ac <= 0.0) continue;
+      const int i0 = std::max(0, std::min((int)floor(rb), last_base));
+      const int i1 = std::min(i0 + 1, i_c);
+      px.push_back({i0, i1, kx * Nv + ky, (float)(rb - i0), (float)ac});
+    }
+  }
+  std::stable_sort(px.begin(), px.end(), [](const Pix& u, const Pix& v) {
+    return u.i0 != v.i0 ? u.i0 < v.i0 : u.i1 < v.i1;
+  });
+  std::vector<int2> ci;
+  std::vector<int> cp;
+  std::vector<float> ca, cc;
+  for (size_t s = 0; s < px.size();) {
+    size_t e2 = s;
+    while (e2 < px.size() && px[e2].i0 == px[s].i0 && px[e2].i1 == px[s].i1) ++e2;
+    for (size_t c = s; c < e2; c += kPfChunk) {
+      ci.push_back(make_int2(px[s].i0, px[s].i1));
+      for (int q = 0; q < kPfChunk; ++q) {
+        const size_t idx = c + q;
+        const bool ok = idx < e2;
+        cp.push_back(ok ? px[idx].pix : -1);
+        ca.push_back(ok ? px[idx].alpha : 0.f);
+        cc.push_back(ok ? px[idx].acut : 0.f);
+      }
+    }
+    s = e2;
+  }
+  p->nchunks = (int)ci.size();
+  if (p->nchunks > 0) {
+    if ((st = upload(p, &p->ch_i01, ci, "chunk table")) != NLOS_OK) return st;
+    if ((st = upload(p, &p->ch_pix, cp, "chunk table")) != NLOS_OK) return st;
+    if ((st = upload(p, &p->ch_alpha, ca, "chunk table")) != NLOS_OK) return st;
+    if ((st = upload(p, &p->ch_acut, cc, "chunk table")) != NLOS_OK) return st;
+  }
+  if ((st = upload(p, &p->w, w, "band weights")) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, p->n)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, Nu)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, Nv)) != NLOS_OK) return st;
+  const size_t cb = complex_bytes(p->storage);
+  const long long a = p->a, b = p->b, F = p->F, D = p->D;
+  const size_t b0 = std::max(a * b * F, 2 * a * b * D) * cb;       // P, then the y-inverse output
+  const size_t b1 = std::max(a * 2 * b * F, 4 * a * b * D) * cb;   // y-transformed P, then C
+  const size_t b2 = 4 * a * b * F * cb;                            // Phat
+  p->off[0] = 0;
+  p->off[1] = align256(b0);
+  p->off[2] = p->off[1] + align256(b1);
+  p->off_scal = p->off[2] + align256(b2);
+  p->off_part = p->off_scal + 256;
+  p->ws_bytes = p->off_part + align256(sizeof(float) * kScalePartials);
+  p->nz = p->D;
+  return NLOS_OK;
+}
+
+// records a tracing event after `stage` (or a call start for stage -1)
+nlos_status_t mark(nlos_plan_s* p, cudaStream_t s, int stage) {
+  if (!p->prof_on) return NLOS_OK;
+  if (p->prof_used == p->prof_pool.size()) {
+    cudaEvent_t e;
+    NLOS_CU(cudaEventCreate(&e), "profiling event");
+    p->prof_pool.push_back(e);
+  }
+  NLOS_CU(cudaEventRecord(p->prof_pool[p->prof_used], s), "profiling event");
+  p->prof_stage.push_back(stage);
+  ++p->prof_used;
+  return NLOS_OK;
+}
+
+#define NLOS_MARK(p, s, stage)                     \
+  do {                                             \
+    nlos_status_t m_ = mark((p), (s), (stage));    \
+    if (m_ != NLOS_OK) return m_;                  \
+  } while (0)
+
+AxisLaunch axis(int storage, int L, long long n_outer, const void* in, void* out, long long inner,
+                long long in_outer, long long in_axis, long long out_outer, long long out_axis, int L_in,
+                int L_out, int inverse, float scale, const float2* tw) {
+  AxisLaunch l{};
+  l.storage = storage;
+  l.L = L;
+  l.n_outer = n_outer;
+  l.load_mode = kLoadCpx;
+  l.store_mode = kStoreCpx;
+  l.p.in = in;
+  l.p.out = out;
+  l.p.tw = tw;
+  l.p.inner = inner;
+  l.p.in_outer = in_outer;
+  l.p.in_axis = in_axis;
+  l.p.out_outer = out_outer;
+  l.p.out_axis = out_axis;
+  l.p.L_in = L_in;
+  l.p.L_out = L_out;
+  l.p.inverse = inverse;
+  l.p.scale = scale;
+  return l;
+}
+
+nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStream_t s) {
+  const int st = p->storage;
+  const long long a = p->a, b = p->b, n = p->n;
+  void* b0 = ws + p->off[0];
+  void* b1 = ws + p->off[1];
+  void* b2 = ws + p->off[2];
+  float* scal = reinterpret_cast<float*>(ws + p->off_scal);
+  const float* s_in = nullptr;
+  const float* inv_s2 = nullptr;
+  int sid = 0;
+  NLOS_MARK(p, s, -1);
+  if (st != kF32) {
+    NLOS_CU(launch_volume_scale(H, a * b * n, (int)n, 1.0f / (float)(n - 1), st, kVolumeTarget,
+                                reinterpret_cast<float*>(ws + p->off_part), kScalePartials, scal, s),
+            "volume scale");
+    NLOS_MARK(p, s, sid++);
+    s_in = scal;
+    inv_s2 = scal + 2;
+  }
+  const float g2a = pass_scale(st, 2 * a), g2b = pass_scale(st, 2 * b), g2n = pass_scale(st, 2 * n);
+  // FK1: x forward (real input, scaled by t/(n-1), zero-padded to 2a, kx in [0, a])
+  AxisLaunch l = axis(st, 2 * a, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)a + 1, 0, g2a, p->tw[2 * a]);
+  l.load_mode = kLoadReal;
+  l.p.t_len = (int)n;
+  l.p.t_scale = 1.0f / (float)(n - 1);
+  l.p.ld_dev_scale = s_in;
+  NLOS_CU(launch_axis_fft(l, s), "fk x-forward");
+  NLOS_MARK(p, s, sid++);
+  // FK1: y forward (zero-padded to 2b)
+  l = axis(st, 2 * b, a + 1, b0, b1, n, b * n, n, 2 * b * n, n, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b]);
+  NLOS_CU(launch_axis_fft(l, s), "fk y-forward");
+  NLOS_MARK(p, s, sid++);
+  // FK3: t forward + Stolt + inverse along z for both Hermitian partners
+  FkZParams z{};
+  z.G = b1;
+  z.psi = b2;
+  z.tw = p->tw[2 * n];
+  z.ax = p->ax;
+  z.ay = p->ay;
+  z.a = (int)a;
+  z.b = (int)b;
+  z.n = (int)n;
+  z.npencils = (a + 1) * 2 * b;
+  z.ld_scale = g2n;
+  z.st_scale = g2n;
+  NLOS_CU(launch_fk_zstage(z, st, s), "fk stolt stage");
+  NLOS_MARK(p, s, sid++);
+  // FK4: y inverse (keep y < b)
+  l = axis(st, 2 * b, 2 * a, b2, b0, n, 2 * b * n, n, b * n, n, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b]);
+  NLOS_CU(launch_axis_fft(l, s), "fk y-inverse");
+  NLOS_MARK(p, s, sid++);
+  // FK4: x inverse (keep x < a), |psi|^2 with the 1/(8abn) normalisation
+  const double N = 8.0 * a * b * n;
+  const double gprod = (double)g2a * g2b * g2n * g2n * g2b * g2a;
+  const float fscale = (float)(1.0 / (N * N * gprod * gprod));
+  l = axis(st, 2 * a, 1, b0, vol, b * n, 0, b * n, 0, b * n, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a]);
+  l.store_mode = kStoreAbs2;
+  l.p.st_dev_scale = inv_s2;
+  NLOS_CU(launch_axis_fft(l, s), "fk x-inverse");
+  NLOS_MARK(p, s, sid++);
+  return NLOS_OK;
+}
+
+nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStream_t s) {
+  const int st = p->storage;
+  const long long a = p->a, b = p->b, n = p->n, F = p->F, D = p->D;
+  void* b0 = ws + p->off[0];
+  void* b1 = ws + p->off[1];
+  void* b2 = ws + p->off[2];
+  float* scal = reinterpret_cast<float*>(ws + p->off_scal);
+  const float* s_in = nullptr;
+  const float* inv_s = nullptr;
+  int sid = 0;
+  NLOS_MARK(p, s, -1);
+  if (st != kF32) {
+    NLOS_CU(launch_volume_scale(H, a * b * n, (int)n, 0.0f, st, kVolumeTarget,
+                                reinterpret_cast<float*>(ws + p->off_part), kScalePartials, scal, s),
+            "volume scale");
+    NLOS_MARK(p, s, sid++);
+    s_in = scal;
+    inv_s = scal + 1;
+  }
+  const float gn = pass_scale(st, n), g2a = pass_scale(st, 2 * a), g2b = pass_scale(st, 2 * b);
+  const float c3 = st == kF32 ? 1.0f : (float)(1.0 / (16.0 * p->kr_scale));
+  // PF1: temporal band transform with w(f)
+  PfBandParams bp{};
+  bp.H = H;
+  bp.P = b0;
+  bp.tw = p->tw[n];
+  bp.w = p->w;
+  bp.n = (int)n;
+  bp.k_lo = p->k_lo;
+  bp.F = (int)F;
+  bp.npencils = a * b;
+  bp.ld_scale = 1.0f;
+  bp.ld_dev_scale = s_in;
+  bp.st_scale = gn;
+  NLOS_CU(launch_pf_band(bp, st, s), "pf band transform");
+  NLOS_MARK(p, s, sid++);
+  // PF2: top-left padding and 2D forward transform (y then x) of every band slice
+  AxisLaunch l = axis(st, 2 * b, a, b0, b1, F, b * F, F, 2 * b * F, F, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b]);
+  NLOS_CU(launch_axis_fft(l, s), "pf y-forward");
+  NLOS_MARK(p, s, sid++);
+  l = axis(st, 2 * a, 1, b1, b2, 2 * b * F, 0, 2 * b * F, 0, 2 * b * F, (int)a, 2 * (int)a, 0, g2a, p->tw[2 * a]);
+  NLOS_CU(launch_axis_fft(l, s), "pf x-forward");
+  NLOS_MARK(p, s, sid++);
+  // PF3: depth sum (pixels beyond the cutoff stay zero)
+  NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * 4 * a * b * D, s), "pf clear");
+  PfDepthParams dp{};
+  dp.Phat = b2;
+  dp.K = p->Kr;
+  dp.C = b1;
+  dp.chunk_i01 = p->ch_i01;
+  dp.chunk_pix = p->ch_pix;
+  dp.chunk_alpha = p->ch_alpha;
+  dp.chunk_acut = p->ch_acut;
+  dp.nchunks = p->nchunks;
+  dp.F = (int)F;
+  dp.D = (int)D;
+  dp.scale = c3;
+  NLOS_CU(launch_pf_depth(dp, st, p->kr_storage, s), "pf depth sum");
+  NLOS_MARK(p, s, sid++);
+  // PF4: 2D inverse transform per depth (y then x), crop, |.| with 1/(4ab)
+  l = axis(st, 2 * b, 2 * a, b1, b0, D, 2 * b * D, D, b * D, D, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b]);
+  NLOS_CU(launch_axis_fft(l, s), "pf y-inverse");
+  NLOS_MARK(p, s, sid++);
+  const double gprod = (double)gn * g2b * g2a * c3 * g2b * g2a;
+  const float fscale = (float)(1.0 / (4.0 * a * b * gprod));
+  l = axis(st, 2 * a, 1, b0, vol, b * D, 0, b * D, 0, b * D, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a]);
+  l.store_mode = kStoreAbs;
+  l.p.st_dev_scale = inv_s;
+  NLOS_CU(launch_axis_fft(l, s), "pf x-inverse");
+  NLOS_MARK(p, s, sid++);
+  return NLOS_OK;
+}
+
+nlos_status_t run_plan(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaStream_t s) {
+  char* w = static_cast<char*>(ws);
+  return p->d.method == NLOS_FK ? run_fk(p, H, vol, w, s) : run_pf(p, H, vol, w, s);
+}
+
+std::mutex g_pool_mu;
+cudaStream_t g_streams[kBatchStreams];
+cudaEvent_t g_fork = nullptr;
+cudaEvent_t g_join[kBatchStreams];
+bool g_pool_ready = false;
+
+nlos_status_t ensure_pool() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (g_pool_ready) return NLOS_OK;
+  NLOS_CU(cudaEventCreateWithFlags(&g_fork, cudaEventDisableTiming), "batch pool");
+  for (int i = 0; i < kBatchStreams; ++i) {
+    NLOS_CU(cudaStreamCreateWithFlags(&g_streams[i], cudaStreamNonBlocking), "batch pool");
+    NLOS_CU(cudaEventCreateWithFlags(&g_join[i], cudaEventDisableTiming), "batch pool");
+  }
+  g_pool_ready = true;
+  return NLOS_OK;
+}
+
+nlos_status_t validate(const nlos_plan_desc_t* d) {
+  if (!d) return fail(NLOS_ERR_INVALID_ARG, "desc is NULL");
+  if (d->method != NLOS_FK && d->method != NLOS_PHASOR_RSD)
+    return fail(NLOS_ERR_INVALID_ARG, "unknown method %d", d->method);
+  if (d->storage != NLOS_F32 && d->storage != NLOS_F16 && d->storage != NLOS_BF16)
+    return fail(NLOS_ERR_INVALID_ARG, "unknown storage %d", d->storage);
+  if (d->nx <= 0 || d->ny <= 0 || d->nt <= 0) return fail(NLOS_ERR_INVALID_ARG, "sizes must be positive");
+  if (!(d->bin_width_s > 0) || !(d->wall_w_m > 0) || !(d->wall_h_m > 0))
+    return fail(NLOS_ERR_INVALID_ARG, "bin width and wall extent must be > 0");
+  if (d->pad_factor != 2) return fail(NLOS_ERR_UNSUPPORTED, "only pad_factor 2 is supported");
+  if (!is_pow2(d->nx) || !is_pow2(d->ny) || !is_pow2(d->nt))
+    return fail(NLOS_ERR_UNSUPPORTED, "sizes must be powers of two");
+  if (d->nx < 8 || d->ny < 8 || d->nx > 1024 || d->ny > 1024)
+    return fail(NLOS_ERR_UNSUPPORTED, "nx, ny must be in [8, 1024]");
+  const int tmax = d->method == NLOS_FK ? 2048 : 4096;
+  if (d->nt < 16 || d->nt > tmax) return fail(NLOS_ERR_UNSUPPORTED, "nt must be in [16, %d]", tmax);
+  if (d->method == NLOS_PHASOR_RSD) {
+    if (d->n_depths < 1 || d->n_depths > 8192) return fail(NLOS_ERR_INVALID_ARG, "n_depths must be in [1, 8192]");
+    if (!(d->depth_min_m > 0) || d->depth_max_m < d->depth_min_m)
+      return fail(NLOS_ERR_INVALID_ARG, "depth range must satisfy 0 < min <= max");
+    if (d->wavelength_m < 0 || d->cycles < 0) return fail(NLOS_ERR_INVALID_ARG, "wavelength/cycles must be >= 0");
+    const bool conf = d->sigma_s == 0 && d->sigma_t == 0;
+    if (!conf && !(d->sigma_s >= 1 && d->sigma_t >= 0)) return fail(NLOS_ERR_INVALID_ARG, "bad modality pair");
+  }
+  return NLOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nlos_plan_desc_default(nlos_plan_desc_t* d) {
+  if (!d) return;
+  memset(d, 0, sizeof *d);
+  d->method = NLOS_FK;
+  d->storage = NLOS_F32;
+  d->pad_factor = 2;
+  d->cycles = 5.0;
+}
+
+nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out) {
+  g_err.clear();
+  if (!out) return fail(NLOS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  nlos_status_t st = validate(desc);
+  if (st != NLOS_OK) return st;
+  nlos_plan_s* p = new nlos_plan_s();
+  p->d = *desc;
+  p->a = desc->nx;
+  p->b = desc->ny;
+  p->n = desc->nt;
+  p->storage = desc->storage;
+  if (p->storage != kF32) p->stage_names.push_back("volume_scale");
+  const char* fk_names[] = {"fk_x_forward", "fk_y_forward", "fk_stolt_z", "fk_y_inverse", "fk_x_inverse"};
+  const char* pf_names[] = {"pf_band", "pf_y_forward", "pf_x_forward", "pf_depth_sum", "pf_y_inverse",
+                            "pf_x_inverse"};
+  if (desc->method == NLOS_FK) for (const char* nm : fk_names) p->stage_names.push_back(nm);
+  else for (const char* nm : pf_names) p->stage_names.push_back(nm);
+  st = desc->method == NLOS_FK ? build_fk(p) : build_pf(p);
+  if (st == NLOS_OK) st = dalloc(p, &p->ws, p->ws_bytes, "workspace");
+  if (st == NLOS_OK) {
+    cudaError_t e = cudaMemset(p->ws, 0, p->ws_bytes);
+    if (e != cudaSuccess) st = cuda_fail(e, "workspace clear");
+  }
+  if (st != NLOS_OK) {
+    for (void* v : p->allocs) cudaFree(v);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_plan_query(nlos_plan_t p, size_t out_shape[3], size_t* workspace_bytes, size_t* input_bytes,
+                              size_t* output_bytes) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (out_shape) {
+    out_shape[0] = p->a;
+    out_shape[1] = p->b;
+    out_shape[2] = p->nz;
+  }
+  if (workspace_bytes) *workspace_bytes = p->ws_bytes;
+  if (input_bytes) *input_bytes = (size_t)p->a * p->b * p->n * real_bytes(p->storage);
+  if (output_bytes) *output_bytes = (size_t)p->a * p->b * p->nz * sizeof(float);
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_reconstruct_ws(nlos_plan_t p, const void* transient, void* volume, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (!transient || !volume) return fail(NLOS_ERR_INVALID_ARG, "transient/volume is NULL");
+  if (!workspace || workspace_bytes < p->ws_bytes)
+    return fail(NLOS_ERR_INVALID_ARG, "workspace too small (%zu < %zu)", workspace_bytes, p->ws_bytes);
+  if (reinterpret_cast<uintptr_t>(workspace) & 255) return fail(NLOS_ERR_INVALID_ARG, "workspace not 256-byte aligned");
+  return run_plan(p, transient, volume, workspace, static_cast<cudaStream_t>(stream));
+}
+
+nlos_status_t nlos_reconstruct(nlos_plan_t p, const void* transient, void* volume, void* stream) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  return nlos_reconstruct_ws(p, transient, volume, p->ws, p->ws_bytes, stream);
+}
+
+nlos_status_t nlos_reconstruct_host(nlos_plan_t p, const void* th, void* vh, void* stream) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (!th || !vh) return fail(NLOS_ERR_INVALID_ARG, "host buffer is NULL");
+  size_t ib = 0, ob = 0;
+  nlos_plan_query(p, nullptr, nullptr, &ib, &ob);
+  nlos_status_t st;
+  if (!p->d_in && (st = dalloc(p, &p->d_in, ib, "host staging")) != NLOS_OK) return st;
+  if (!p->d_out && (st = dalloc(p, &p->d_out, ob, "host staging")) != NLOS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  NLOS_CU(cudaMemcpyAsync(p->d_in, th, ib, cudaMemcpyHostToDevice, s), "host->device copy");
+  st = run_plan(p, p->d_in, p->d_out, p->ws, s);
+  if (st != NLOS_OK) return st;
+  NLOS_CU(cudaMemcpyAsync(vh, p->d_out, ob, cudaMemcpyDeviceToHost, s), "device->host copy");
+  NLOS_CU(cudaStreamSynchronize(s), "host call sync");
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_reconstruct_batch(const nlos_plan_t* plans, const void* const* transients, void* const* volumes,
+                                     void* const* workspaces, int n, void* stream) {
+  if (n < 0 || (n > 0 && (!plans || !transients || !volumes))) return fail(NLOS_ERR_INVALID_ARG, "bad batch arrays");
+  if (n == 0) return NLOS_OK;
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !transients[i] || !volumes[i]) return fail(NLOS_ERR_INVALID_ARG, "batch item %d is NULL", i);
+    if (!workspaces)
+      for (int j = 0; j < i; ++j)
+        if (plans[j] == plans[i]) return fail(NLOS_ERR_INVALID_ARG, "plan repeated in batch without workspaces");
+    if (workspaces && (!workspaces[i] || (reinterpret_cast<uintptr_t>(workspaces[i]) & 255)))
+      return fail(NLOS_ERR_INVALID_ARG, "batch workspace %d is NULL or misaligned", i);
+  }
+  nlos_status_t st = ensure_pool();
+  if (st != NLOS_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int used = std::min(n, kBatchStreams);
+  NLOS_CU(cudaEventRecord(g_fork, s), "batch fork");
+  for (int k = 0; k < used; ++k) NLOS_CU(cudaStreamWaitEvent(g_streams[k], g_fork, 0), "batch fork");
+  for (int i = 0; i < n; ++i) {
+    void* ws = workspaces ? workspaces[i] : plans[i]->ws;
+    st = run_plan(plans[i], transients[i], volumes[i], ws, g_streams[i % kBatchStreams]);
+    if (st != NLOS_OK) return st;
+  }
+  for (int k = 0; k < used; ++k) {
+    NLOS_CU(cudaEventRecord(g_join[k], g_streams[k]), "batch join");
+    NLOS_CU(cudaStreamWaitEvent(s, g_join[k], 0), "batch join");
+  }
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_plan_set_profiling(nlos_plan_t p, int enable) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  p->prof_on = enable != 0;
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_plan_stage_times(nlos_plan_t p, double* times_ms, int capacity, int* n_stages,
+                                    long long* calls) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  const int ns = (int)p->stage_names.size();
+  if (n_stages) *n_stages = ns;
+  long long nc = 0;
+  for (size_t i = 0; i < p->prof_used; ++i) {
+    NLOS_CU(cudaEventSynchronize(p->prof_pool[i]), "profiling read");
+    const int stg = p->prof_stage[i];
+    if (stg < 0) {
+      ++nc;
+      continue;
+    }
+    if (i == 0) continue;
+    float ms = 0.f;
+    NLOS_CU(cudaEventElapsedTime(&ms, p->prof_pool[i - 1], p->prof_pool[i]), "profiling read");
+    if (times_ms && stg < capacity) times_ms[stg] += ms;
+  }
+  if (calls) *calls = nc;
+  p->prof_used = 0;
+  p->prof_stage.clear();
+  return NLOS_OK;
+}
+
+const char* nlos_plan_stage_name(nlos_plan_t p, int i) {
+  if (!p || i < 0 || i >= (int)p->stage_names.size()) return nullptr;
+  return p->stage_names[i].c_str();
+}
+
+nlos_status_t nlos_plan_destroy(nlos_plan_t p) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
+  for (void* v : p->allocs) cudaFree(v);
+  delete p;
+  return NLOS_OK;
+}
+
+const char* nlos_last_error(void) { return g_err.c_str(); }
+
+const char* nlos_version(void) { return "nlos-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+// Device-side FFT building blocks for the NLOS kernels (sm_103a).
+//
+// Every transform here is a power-of-two Stockham FFT (self-sorting, natural
+// order in and out) executed by TPC = L/16 threads, each holding 16 complex
+// values in registers. A pass of radix R (16, or 8/4/2 for the remainder)
+// gathers R values per butterfly at stride L/R, multiplies by the pass
+// twiddles W_{Ns R}^{k r}, runs an in-register radix-R DFT and scatters to
+// (j/Ns) Ns R + j%Ns + r Ns. Between passes data goes through shared memory
+// in place (read, barrier, write, barrier). The first pass reads straight from
+// global memory through a caller-supplied functor (zero padding, scaling and
+// type conversion fused there) and the last pass writes straight to global
+// memory through another (cropping, magnitude, band selection fused there).
+//
+// Inverse transforms use conj(DFT(conj(x))), so a context conjugates on load
+// and on store; there is one butterfly implementation.
+//
+// Twiddle tables come from the plan (generated in float64 on the host,
+// stored as float2): for pass p the table T_p[r * Ns + k] = exp(-2 pi i k r /
+// (Ns R)), laid out with k fastest so that lanes with consecutive k read
+// consecutive addresses.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace nlos {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// a * (-i)
+__device__ __forceinline__ float2 cmul_mi(float2 a) { return make_float2(a.y, -a.x); }
+
+// cos(2 pi m / 32) for m = 0..8 (values of the circle function, listed).
+__device__ __forceinline__ float cos32_q(int m) {
+  switch (m) {
+    case 0: return 1.0f;
+    case 1: return 0.98078528040323043f;
+    case 2: return 0.92387953251128674f;
+    case 3: return 0.83146961230254524f;
+    case 4: return 0.70710678118654752f;
+    case 5: return 0.55557023301960218f;
+    case 6: return 0.38268343236508984f;
+    case 7: return 0.19509032201612833f;
+    default: return 0.0f;
+  }
+}
+__device__ __forceinline__ float cos32(int m) {
+  m &= 31;
+  if (m <= 8) return cos32_q(m);
+  if (m <= 16) return -cos32_q(16 - m);
+  if (m <= 24) return -cos32_q(m - 16);
+  return cos32_q(32 - m);
+}
+__device__ __forceinline__ float sin32(int m) { return cos32(m - 8); }
+
+// a * exp(-2 pi i m / 32); m is a compile-time constant after unrolling, so
+// the branches and table reads fold away.
+__device__ __forceinline__ float2 mul_w32(float2 a, int m) {
+  m &= 31;
+  if (m == 0) return a;
+  if (m == 8) return make_float2(a.y, -a.x);
+  if (m == 16) return make_float2(-a.x, -a.y);
+  if (m == 24) return make_float2(-a.y, a.x);
+  const float c = cos32(m), s = sin32(m);
+  return make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+}
+
+// ---------------------------------------------------------------------------
+// in-register radix-R DFTs, natural order in and out, forward sign e^{-i}
+// ---------------------------------------------------------------------------
+template <int R> struct Dft;
+
+template <> struct Dft<1> {
+  static __device__ __forceinline__ void run(float2*) {}
+};
+template <> struct Dft<2> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float2 t = v[0];
+    v[0] = cadd(t, v[1]);
+    v[1] = csub(t, v[1]);
+  }
+};
+template <> struct Dft<4> {
+  static __device__ __forceinline__ void run(float2* v) {
+    const float2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    const float2 c = cadd(v[1], v[3]), d = cmul_mi(csub(v[1], v[3]));
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = cadd(b, d);
+    v[3] = csub(b, d);
+  }
+};
+// R = R1 * R2 with n = n1 + R1 n2 and k = k2 + R2 k1:
+//   X[k2 + R2 k1] = sum_n1 W_R^{n1 k2} W_R1^{n1 k1} (sum_n2 x[n1 + R1 n2] W_R2^{n2 k2})
+template <int R> struct Dft {
+  static constexpr int R1 = (R >= 16) ? 4 : 2;
+  static constexpr int R2 = R / R1;
+  static __device__ __forceinline__ void run(float2* v) {
+    float2 y[R1][R2];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) {
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) y[n1][n2] = v[n1 + R1 * n2];
+      Dft<R2>::run(y[n1]);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) y[n1][k2] = mul_w32(y[n1][k2], (32 / R) * n1 * k2);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) {
+      float2 t[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) t[n1] = y[n1][k2];
+      Dft<R1>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) v[k2 + R2 * k1] = t[k1];
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// pass schedule of an L-point transform
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+
+template <int L> struct FftShape {
+  static_assert(L >= 16 && (L & (L - 1)) == 0, "power-of-two length >= 16");
+  static constexpr int E = 16;            // complex values held per thread
+  static constexpr int TPC = L / E;       // threads per transform
+  static constexpr int LOG = ilog2c(L);
+  static constexpr int NFULL = LOG / 4;
+  static constexpr int REM = LOG % 4;
+  static constexpr int NPASS = NFULL + (REM ? 1 : 0);
+  static constexpr int SMEM = L + L / 16;  // padded shared-memory elements per transform
+  __host__ __device__ static constexpr int radix(int p) { return p < NFULL ? 16 : (1 << REM); }
+  __host__ __device__ static constexpr int span(int p) { return p == 0 ? 1 : span(p - 1) * radix(p - 1); }
+  __host__ __device__ static constexpr int twoff(int p) {
+    return p == 0 ? 0 : twoff(p - 1) + span(p - 1) * radix(p - 1);
+  }
+  static constexpr int TWSIZE = twoff(NPASS);
+};
+
+// One padding element per 16 keeps the radix-16 scatter of the first pass
+// (stride 16) and the contiguous gathers free of bank conflicts.
+__device__ __forceinline__ int pad16(int l) { return l + (l >> 4); }
+
+// Runs passes P..NPASS-1 of an L-point transform for one thread.
+// Ctx provides:
+//   float2 load(int l)           element l of the input (first pass only)
+//   void   store(int l, float2)  element l of the output (last pass only)
+//   float2& at(int l)            shared-memory slot of element l (middle passes)
+//   const float2* tw             twiddle table of the plan for length L
+template <int L, int P, class Ctx>
+__device__ __forceinline__ void fft_passes(Ctx& ctx, const int j0, float2 (&v)[16]) {
+  using S = FftShape<L>;
+  constexpr int R = S::radix(P);
+  constexpr int NS = S::span(P);
+  constexpr int BPT = 16 / R;
+  constexpr bool kFirst = (P == 0);
+  constexpr bool kLast = (P == S::NPASS - 1);
+#pragma unroll
+  for (int i = 0; i < BPT; ++i) {
+    const int j = j0 + i * S::TPC;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int l = j + r * (L / R);
+      if constexpr (kFirst) v[i * R + r] = ctx.load(l);
+      else v[i * R + r] = ctx.at(l);
+    }
+  }
+  if constexpr (!kFirst) __syncthreads();
+#pragma unroll
+  for (int i = 0; i < BPT; ++i) {
+    const int j = j0 + i * S::TPC;
+    if constexpr (!kFirst) {
+      const int k = j & (NS - 1);
+      const float2* t = ctx.tw + S::twoff(P) + k;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i * R + r] = cmul(v[i * R + r], __ldg(t + r * NS));
+    }
+    Dft<R>::run(&v[i * R]);
+  }
+#pragma unroll
+  for (int i = 0; i < BPT; ++i) {
+    const int j = j0 + i * S::TPC;
+    const int base = (j / NS) * NS * R + (j & (NS - 1));
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int l = base + r * NS;
+      if constexpr (kLast) ctx.store(l, v[i * R + r]);
+      else ctx.at(l) = v[i * R + r];
+    }
+  }
+  if constexpr (!kLast) {
+    __syncthreads();
+    fft_passes<L, P + 1>(ctx, j0, v);
+  }
+}
+
+template <int L, class Ctx>
+__device__ __forceinline__ void fft_run(Ctx& ctx, const int j0) {
+  float2 v[16];
+  fft_passes<L, 0>(ctx, j0, v);
+}
+
+// ---------------------------------------------------------------------------
+// storage types for complex intermediates and real inputs
+// ---------------------------------------------------------------------------
+template <class T> struct Cpx;
+template <> struct Cpx<float2> {
+  static __device__ __forceinline__ float2 get(const float2* p) { return *p; }
+  static __device__ __forceinline__ void put(float2* p, float2 v) { *p = v; }
+};
+template <> struct Cpx<__half2> {
+  static __device__ __forceinline__ float2 get(const __half2* p) { return __half22float2(*p); }
+  static __device__ __forceinline__ void put(__half2* p, float2 v) { *p = __float22half2_rn(v); }
+};
+template <> struct Cpx<__nv_bfloat162> {
+  static __device__ __forceinline__ float2 get(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+  static __device__ __forceinline__ void put(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+};
+
+template <class T> struct Real;
+template <> struct Real<float> {
+  static __device__ __forceinline__ float get(const float* p) { return *p; }
+};
+template <> struct Real<__half> {
+  static __device__ __forceinline__ float get(const __half* p) { return __half2float(*p); }
+};
+template <> struct Real<__nv_bfloat16> {
+  static __device__ __forceinline__ float get(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+};
+
+}  // namespace nlos

@@ -1,0 +1,121 @@
+// Internal interfaces between the host plan code and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace nlos {
+
+// Element types of stored intermediates / inputs.
+enum Storage : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
+
+// Load/store modes of the strided-axis FFT.
+enum AxisLoad : int { kLoadReal = 0, kLoadCpx = 1 };
+enum AxisStore : int { kStoreCpx = 0, kStoreAbs2 = 1, kStoreAbs = 2 };
+
+// FFT of length L along one axis of a [outer][L][inner] array (inner
+// contiguous). Elements along the axis beyond L_in are zero; outputs with
+// index >= L_out are not written. Strides are in elements of the stored type
+// (complex elements for complex arrays).
+struct AxisParams {
+  const void* in;
+  void* out;
+  const float2* tw;            // twiddles of the plan for length L
+  long long inner;
+  long long in_outer, in_axis;
+  long long out_outer, out_axis;
+  int L_in, L_out;
+  int inverse;                 // conjugate on load and on store
+  float scale;                 // multiplies every stored value (|.|^2 and |.| included)
+  const float* ld_dev_scale;   // optional device scalar multiplying loads
+  const float* st_dev_scale;   // optional device scalar multiplying stores
+  int t_len;                   // real loads: multiply by (inner index % t_len) * t_scale
+  float t_scale;
+};
+
+struct AxisLaunch {
+  AxisParams p;
+  int L;
+  long long n_outer;
+  int storage;                 // element type of complex arrays (and of real input)
+  int load_mode;               // AxisLoad
+  int store_mode;              // AxisStore
+};
+cudaError_t launch_axis_fft(const AxisLaunch& l, cudaStream_t s);
+
+// f-k temporal-frequency stage: forward length-2n FFT of each stored pencil
+// G[kx][ky][0..n) (kx in [0, a], ky in [0, 2b)), Stolt resampling with the
+// Jacobian and the Z > 0 mask, and inverse length-2n FFTs producing the pencil
+// (kx, ky) and, for 0 < kx < a, its Hermitian partner (2a-kx, -ky), keeping
+// z < n. Output psi[kx'][ky'][z] for kx' in [0, 2a).
+struct FkZParams {
+  const void* G;
+  void* psi;
+  const float2* tw;            // twiddles for L = 2n
+  const float2* ax;            // [2a] float-float (hi, lo) of (n s_x p~ / a)^2
+  const float2* ay;            // [2b] float-float of (n s_y q~ / b)^2
+  int a, b, n;
+  long long npencils;          // (a + 1) * 2b
+  float ld_scale;              // multiplies forward loads
+  const float* ld_dev_scale;   // optional device scalar multiplying forward loads
+  float st_scale;              // multiplies stored values
+};
+cudaError_t launch_fk_zstage(const FkZParams& p, int storage, cudaStream_t s);
+
+// Phasor-field temporal band transform: per wall pencil H[x][y][0..n) (real),
+// length-n DFT, keep bins k_lo..k_lo+F-1, multiply by w(f): P[x][y][f].
+struct PfBandParams {
+  const void* H;
+  void* P;
+  const float2* tw;            // twiddles for L = n
+  const float* w;              // [F]
+  int n, k_lo, F;
+  long long npencils;          // a * b
+  float ld_scale;
+  const float* ld_dev_scale;
+  float st_scale;
+};
+cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s);
+
+// Phasor-field depth sum over pixel chunks sharing a radial index i0:
+// C[pix][d] = acut * sum_f Phat[pix][f] * ((1 - alpha) K[i0][f][d] + alpha K[i1][f][d]).
+constexpr int kPfChunk = 16;
+struct PfDepthParams {
+  const void* Phat;            // [Nu*Nv][F] complex (storage type)
+  const void* K;               // [N_rho][F][D] complex (kernel storage type)
+  void* C;                     // [Nu*Nv][D] complex (storage type)
+  const int2* chunk_i01;       // [nchunks] (i0, i1)
+  const int* chunk_pix;        // [nchunks][16] pixel index or -1
+  const float* chunk_alpha;    // [nchunks][16]
+  const float* chunk_acut;     // [nchunks][16]
+  int nchunks, F, D;
+  float scale;
+  const float* dev_scale;      // optional device scalar multiplying C
+};
+cudaError_t launch_pf_depth(const PfDepthParams& p, int storage, int kernel_storage, cudaStream_t s);
+
+// Plan-time kernel build in float64:
+// K[i][f][d] = mod[f][d] * sum_j B[i][j] exp(i sigma_s kappa_f sqrt(r_j^2 + d^2))
+struct KrBuildParams {
+  const double* B;             // [n_rho][n_r] = q_j 2 pi r_j J0(2 pi r_j rho_i) (0 beyond cutoff)
+  const double* r;             // [n_r]
+  const double* kappa;         // [F]
+  const double* depth;         // [D]
+  int n_rho, n_r, F, D;
+  double sigma_s, sigma_t, delta;
+  double2* A;                  // scratch [n_r][F][D]
+  double2* K64;                // out [n_rho][F][D]
+};
+cudaError_t launch_kr_build(const KrBuildParams& p, cudaStream_t s);
+// Convert the float64 kernel to the stored type with a scale.
+cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int storage, double scale,
+                            cudaStream_t s);
+
+// Per-volume scale for reduced-precision storage: out[0] = target / ||u||_2,
+// out[1] = 1 / out[0], out[2] = 1 / out[0]^2, where u = H * (t % n) * t_scale (t_scale = 0: no ramp).
+cudaError_t launch_volume_scale(const void* H, long long count, int n, float t_scale, int storage,
+                                float target, float* partial, int npartial, float* out,
+                                cudaStream_t s);
+
+}  // namespace nlos

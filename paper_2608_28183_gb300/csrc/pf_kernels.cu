@@ -1,0 +1,351 @@
+// Phasor-field (radial RSD) kernels: temporal band transform, depth sum over
+// the radial kernel, plan-time float64 construction of the radial kernel, and
+// the per-volume scale used by reduced-precision storage.
+#include "nlos_fft.cuh"
+#include "nlos_internal.h"
+
+namespace nlos {
+
+// ---------------------------------------------------------------------------
+// PF1: P[x][y][f] = w(f) * sum_t H[x][y][t] exp(-2 pi i (k_lo + f) t / n)
+// (Sec. 3.1 phasor field; w(f) is the virtual wave's spectrum, folded here
+// instead of inside the depth sum.)
+// ---------------------------------------------------------------------------
+template <int L, class TR, class TS>
+struct PfBandCtx {
+  const TR* h;
+  TS* P;
+  float2* W;
+  const float2* tw;
+  const float* w;
+  int k_lo, F;
+  bool valid;
+  float ldmul, stmul;
+  __device__ __forceinline__ float2 load(int l) const {
+    if (!valid) return make_float2(0.f, 0.f);
+    return make_float2(Real<TR>::get(h + l) * ldmul, 0.f);
+  }
+  __device__ __forceinline__ float2& at(int l) const { return W[pad16(l)]; }
+  __device__ __forceinline__ void store(int l, float2 v) const {
+    const int f = l - k_lo;
+    if (valid && f >= 0 && f < F) Cpx<TS>::put(P + f, cscale(v, __ldg(w + f) * stmul));
+  }
+};
+
+template <int L> struct PfBandTile {
+  static constexpr int PPC = L <= 256 ? 8 : (L <= 1024 ? 4 : 2);
+  static constexpr int THREADS = PPC * (L / 16);
+  static constexpr size_t SMEM = (L > 16) ? sizeof(float2) * PPC * FftShape<L>::SMEM : 0;
+};
+
+template <int L, class TR, class TS>
+__global__ void __launch_bounds__(PfBandTile<L>::THREADS)
+pf_band_kernel(const PfBandParams p) {
+  using S = FftShape<L>;
+  constexpr int PPC = PfBandTile<L>::PPC;
+  extern __shared__ float2 pfb_sm[];
+  const int w = threadIdx.x / S::TPC;
+  const int j0 = threadIdx.x % S::TPC;
+  const long long pid = (long long)blockIdx.x * PPC + w;
+  const bool valid = pid < p.npencils;
+  const long long q = valid ? pid : 0;
+  const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
+  PfBandCtx<L, TR, TS> ctx{static_cast<const TR*>(p.H) + q * p.n, static_cast<TS*>(p.P) + q * p.F,
+                           pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale};
+  fft_run<L>(ctx, j0);
+}
+
+template <int L, class TR, class TS>
+static cudaError_t launch_band_one(const PfBandParams& p, cudaStream_t s) {
+  using T = PfBandTile<L>;
+  auto k = pf_band_kernel<L, TR, TS>;
+  if (T::SMEM > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  const long long blocks = (p.npencils + T::PPC - 1) / T::PPC;
+  k<<<(unsigned)blocks, T::THREADS, T::SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <class TR, class TS>
+static cudaError_t launch_band_typed(const PfBandParams& p, cudaStream_t s) {
+  switch (p.n) {
+    case 16: return launch_band_one<16, TR, TS>(p, s);
+    case 32: return launch_band_one<32, TR, TS>(p, s);
+    case 64: return launch_band_one<64, TR, TS>(p, s);
+    case 128: return launch_band_one<128, TR, TS>(p, s);
+    case 256: return launch_band_one<256, TR, TS>(p, s);
+    case 512: return launch_band_one<512, TR, TS>(p, s);
+    case 1024: return launch_band_one<1024, TR, TS>(p, s);
+    case 2048: return launch_band_one<2048, TR, TS>(p, s);
+    case 4096: return launch_band_one<4096, TR, TS>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s) {
+  if (p.npencils <= 0 || p.F <= 0) return cudaErrorInvalidValue;
+  switch (storage) {
+    case kF32: return launch_band_typed<float, float2>(p, s);
+    case kF16: return launch_band_typed<__half, __half2>(p, s);
+    case kBF16: return launch_band_typed<__nv_bfloat16, __nv_bfloat162>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PF3: depth sum (Alg. 4 inner loop; Sec. 4.3 propagation sum). One CTA owns a
+// chunk of up to 16 pixels that share the radial index pair (i0, i1) and 128
+// depths; each thread keeps 16 complex accumulators (one per pixel) for its
+// depth, so every radial-kernel sample read from memory feeds 16 pixels. The
+// lerp is K0 + alpha (K1 - K0) and the taper multiplies the finished sum.
+// Accumulation is float32 whatever the storage type.
+// ---------------------------------------------------------------------------
+constexpr int kDepthBlock = 128;
+
+template <class TS, class TK>
+__global__ void __launch_bounds__(kDepthBlock)
+pf_depth_kernel(const PfDepthParams p) {
+  extern __shared__ float2 ps[];   // [16][F] phasors of the chunk's pixels
+  __shared__ int pix[kPfChunk];
+  __shared__ float sal[kPfChunk], sac[kPfChunk];
+  const int ch = blockIdx.x;
+  const int d = blockIdx.y * kDepthBlock + threadIdx.x;
+  if (threadIdx.x < kPfChunk) {
+    pix[threadIdx.x] = p.chunk_pix[ch * kPfChunk + threadIdx.x];
+    sal[threadIdx.x] = p.chunk_alpha[ch * kPfChunk + threadIdx.x];
+    sac[threadIdx.x] = p.chunk_acut[ch * kPfChunk + threadIdx.x];
+  }
+  __syncthreads();
+  const int F = p.F;
+  const TS* Ph = static_cast<const TS*>(p.Phat);
+  for (int idx = threadIdx.x; idx < kPfChunk * F; idx += kDepthBlock) {
+    const int q = idx / F, f = idx - q * F;
+    const int px = pix[q];
+    ps[idx] = px >= 0 ? Cpx<TS>::get(Ph + (long long)px * F + f) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  if (d >= p.D) return;
+  float alpha[kPfChunk];
+#pragma unroll
+  for (int q = 0; q < kPfChunk; ++q) alpha[q] = sal[q];
+  float2 acc[kPfChunk];
+#pragma unroll
+  for (int q = 0; q < kPfChunk; ++q) acc[q] = make_float2(0.f, 0.f);
+  const int2 i01 = p.chunk_i01[ch];
+  const TK* K = static_cast<const TK*>(p.K);
+  const TK* K0 = K + (long long)i01.x * F * p.D + d;
+  const TK* K1 = K + (long long)i01.y * F * p.D + d;
+#pragma unroll 2
+  for (int f = 0; f < F; ++f) {
+    const float2 k0 = Cpx<TK>::get(K0 + (long long)f * p.D);
+    const float2 k1 = Cpx<TK>::get(K1 + (long long)f * p.D);
+    const float2 dk = csub(k1, k0);
+#pragma unroll
+    for (int q = 0; q < kPfChunk; ++q) {
+      const float2 kl = make_float2(fmaf(alpha[q], dk.x, k0.x), fmaf(alpha[q], dk.y, k0.y));
+      const float2 x = ps[q * F + f];
+      acc[q].x = fmaf(x.x, kl.x, fmaf(-x.y, kl.y, acc[q].x));
+      acc[q].y = fmaf(x.x, kl.y, fmaf(x.y, kl.x, acc[q].y));
+    }
+  }
+  const float sc = p.scale * (p.dev_scale ? *p.dev_scale : 1.0f);
+  TS* C = static_cast<TS*>(p.C);
+#pragma unroll
+  for (int q = 0; q < kPfChunk; ++q) {
+    const int px = pix[q];
+    if (px >= 0) Cpx<TS>::put(C + (long long)px * p.D + d, cscale(acc[q], sac[q] * sc));
+  }
+}
+
+template <class TS, class TK>
+static cudaError_t launch_depth_typed(const PfDepthParams& p, cudaStream_t s) {
+  auto k = pf_depth_kernel<TS, TK>;
+  const size_t smem = sizeof(float2) * kPfChunk * p.F;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)p.nchunks, (unsigned)((p.D + kDepthBlock - 1) / kDepthBlock));
+  k<<<grid, kDepthBlock, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pf_depth(const PfDepthParams& p, int storage, int kstorage, cudaStream_t s) {
+  if (p.nchunks <= 0) return cudaSuccess;
+  if (p.F <= 0 || p.D <= 0 || p.D > 65535 * kDepthBlock) return cudaErrorInvalidValue;
+  if (storage == kF32 && kstorage == kF32) return launch_depth_typed<float2, float2>(p, s);
+  if (storage == kF16 && kstorage == kF16) return launch_depth_typed<__half2, __half2>(p, s);
+  if (storage == kBF16 && kstorage == kBF16) return launch_depth_typed<__nv_bfloat162, __nv_bfloat162>(p, s);
+  if (storage == kF16 && kstorage == kF32) return launch_depth_typed<__half2, float2>(p, s);
+  if (storage == kBF16 && kstorage == kF32) return launch_depth_typed<__nv_bfloat162, float2>(p, s);
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Plan-time radial kernel (Eqs. 4-6) in float64.
+// ---------------------------------------------------------------------------
+__global__ void kr_phase_kernel(const KrBuildParams p) {
+  const long long total = (long long)p.n_r * p.F * p.D;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int dd = (int)(idx % p.D);
+    const long long rest = idx / p.D;
+    const int f = (int)(rest % p.F);
+    const int j = (int)(rest / p.F);
+    const double r = p.r[j], z = p.depth[dd];
+    const double ph = p.sigma_s * p.kappa[f] * sqrt(r * r + z * z);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    p.A[idx] = make_double2(cs, sn);
+  }
+}
+
+// K64[i][fd] = mod(f, d) * sum_j B[i][j] A[j][fd]; 64 x 64 output tile per
+// CTA, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) kr_gemm_kernel(const KrBuildParams p) {
+  __shared__ double Bs[16][64];
+  __shared__ double2 As[16][64];
+  const int NFD = p.F * p.D;
+  const int i_base = blockIdx.y * 64, fd_base = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double2 acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = make_double2(0.0, 0.0);
+  for (int j0 = 0; j0 < p.n_r; j0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      const int jj = e / 64, q = e % 64;
+      const int i = i_base + q, j = j0 + jj, fd = fd_base + q;
+      Bs[jj][q] = (i < p.n_rho && j < p.n_r) ? p.B[(long long)i * p.n_r + j] : 0.0;
+      As[jj][q] = (fd < NFD && j < p.n_r) ? p.A[(long long)j * NFD + fd] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int jj = 0; jj < 16; ++jj) {
+      double bv[4];
+      double2 av[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) bv[u] = Bs[jj][ty + 16 * u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) av[v] = As[jj][tx + 16 * v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          acc[u][v].x = fma(bv[u], av[v].x, acc[u][v].x);
+          acc[u][v].y = fma(bv[u], av[v].y, acc[u][v].y);
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = i_base + ty + 16 * u;
+    if (i >= p.n_rho) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int fd = fd_base + tx + 16 * v;
+      if (fd >= NFD) continue;
+      const int f = fd / p.D, dd = fd % p.D;
+      const double ph = p.kappa[f] * (p.sigma_t * p.depth[dd] + p.delta);
+      double sn, cs;
+      sincos(ph, &sn, &cs);
+      const double2 a = acc[u][v];
+      p.K64[(long long)i * NFD + fd] = make_double2(a.x * cs - a.y * sn, a.x * sn + a.y * cs);
+    }
+  }
+}
+
+cudaError_t launch_kr_build(const KrBuildParams& p, cudaStream_t s) {
+  kr_phase_kernel<<<1024, 256, 0, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int NFD = p.F * p.D;
+  dim3 grid((unsigned)((NFD + 63) / 64), (unsigned)((p.n_rho + 63) / 64));
+  kr_gemm_kernel<<<grid, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <class TK>
+__global__ void kr_store_kernel(const double2* K64, TK* K, long long count, double scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = K64[i];
+    Cpx<TK>::put(K + i, make_float2((float)(v.x * scale), (float)(v.y * scale)));
+  }
+}
+
+cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int storage, double scale,
+                            cudaStream_t s) {
+  switch (storage) {
+    case kF32: kr_store_kernel<float2><<<1024, 256, 0, s>>>(K64, static_cast<float2*>(K), count, scale); break;
+    case kF16: kr_store_kernel<__half2><<<1024, 256, 0, s>>>(K64, static_cast<__half2*>(K), count, scale); break;
+    case kBF16:
+      kr_store_kernel<__nv_bfloat162><<<1024, 256, 0, s>>>(K64, static_cast<__nv_bfloat162*>(K), count, scale);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-volume scale for reduced-precision storage (two-stage, deterministic).
+// ---------------------------------------------------------------------------
+template <class TR>
+__global__ void sumsq_partial_kernel(const TR* H, long long count, int n, float t_scale, float* partial) {
+  __shared__ float red[256];
+  float acc = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    float v = Real<TR>::get(H + i);
+    if (t_scale != 0.f) v *= (float)(int)(i % n) * t_scale;
+    acc = fmaf(v, v, acc);
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int sft = 128; sft > 0; sft >>= 1) {
+    if (threadIdx.x < sft) red[threadIdx.x] += red[threadIdx.x + sft];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void sumsq_final_kernel(const float* partial, int npartial, float target, float* out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < npartial; i += blockDim.x) acc += partial[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int sft = 128; sft > 0; sft >>= 1) {
+    if (threadIdx.x < sft) red[threadIdx.x] += red[threadIdx.x + sft];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(red[0]);
+    const float sc = nrm > 0.0 ? (float)(target / nrm) : 1.0f;
+    out[0] = sc;
+    out[1] = 1.0f / sc;
+    out[2] = (float)(1.0 / ((double)sc * (double)sc));
+  }
+}
+
+cudaError_t launch_volume_scale(const void* H, long long count, int n, float t_scale, int storage,
+                                float target, float* partial, int npartial, float* out, cudaStream_t s) {
+  switch (storage) {
+    case kF32: sumsq_partial_kernel<float><<<npartial, 256, 0, s>>>(static_cast<const float*>(H), count, n, t_scale, partial); break;
+    case kF16: sumsq_partial_kernel<__half><<<npartial, 256, 0, s>>>(static_cast<const __half*>(H), count, n, t_scale, partial); break;
+    case kBF16:
+      sumsq_partial_kernel<__nv_bfloat16><<<npartial, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(H), count, n, t_scale, partial);
+      break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sumsq_final_kernel<<<1, 256, 0, s>>>(partial, npartial, target, out);
+  return cudaGetLastError();
+}
+
+}  // namespace nlos

@@ -1,0 +1,233 @@
+"""Thin Python binding of the C ABI in include/nlos.h (argument marshalling only).
+
+Every step of a reconstruction runs in the CUDA library's kernels; this module
+only checks tensors, passes raw pointers and the current CUDA stream, and turns
+status codes into exceptions. If the library is missing it raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnlos_gb300.so")
+
+NLOS_FK, NLOS_PHASOR_RSD = 0, 1
+NLOS_F32, NLOS_F16, NLOS_BF16 = 0, 1, 2
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
+METHODS = {"fk": NLOS_FK, "pf": NLOS_PHASOR_RSD, "phasor": NLOS_PHASOR_RSD}
+STORAGES = {"f32": NLOS_F32, "f16": NLOS_F16, "bf16": NLOS_BF16}
+
+EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nlos_reconstruct",
+            "nlos_reconstruct_ws", "nlos_reconstruct_host", "nlos_reconstruct_batch",
+            "nlos_plan_set_profiling", "nlos_plan_stage_times", "nlos_plan_stage_name",
+            "nlos_plan_destroy", "nlos_last_error", "nlos_version"]
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nt", ctypes.c_int),
+        ("bin_width_s", ctypes.c_double),
+        ("wall_w_m", ctypes.c_double), ("wall_h_m", ctypes.c_double),
+        ("method", ctypes.c_int), ("storage", ctypes.c_int), ("pad_factor", ctypes.c_int),
+        ("wavelength_m", ctypes.c_double), ("cycles", ctypes.c_double),
+        ("n_depths", ctypes.c_int),
+        ("depth_min_m", ctypes.c_double), ("depth_max_m", ctypes.c_double),
+        ("sigma_s", ctypes.c_int), ("sigma_t", ctypes.c_int),
+        ("delta_m", ctypes.c_double),
+    ]
+
+
+class NlosError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnlos_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run paper_2608_28183_gb300/build.py)")
+    lib = ctypes.CDLL(path)
+    vp, sz = ctypes.c_void_p, ctypes.c_size_t
+    lib.nlos_plan_desc_default.argtypes = [ctypes.POINTER(PlanDesc)]
+    lib.nlos_plan_desc_default.restype = None
+    lib.nlos_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(vp)]
+    lib.nlos_plan_query.argtypes = [vp, ctypes.POINTER(sz * 3), ctypes.POINTER(sz), ctypes.POINTER(sz),
+                                    ctypes.POINTER(sz)]
+    lib.nlos_reconstruct.argtypes = [vp, vp, vp, vp]
+    lib.nlos_reconstruct_ws.argtypes = [vp, vp, vp, vp, sz, vp]
+    lib.nlos_reconstruct_host.argtypes = [vp, vp, vp, vp]
+    lib.nlos_reconstruct_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(vp), ctypes.c_int, vp]
+    lib.nlos_plan_destroy.argtypes = [vp]
+    lib.nlos_plan_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.nlos_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
+    lib.nlos_plan_stage_name.argtypes = [vp, ctypes.c_int]
+    lib.nlos_plan_stage_name.restype = ctypes.c_char_p
+    for name in ("nlos_plan_create", "nlos_plan_query", "nlos_reconstruct", "nlos_reconstruct_ws",
+                 "nlos_reconstruct_host", "nlos_reconstruct_batch", "nlos_plan_destroy",
+                 "nlos_plan_set_profiling", "nlos_plan_stage_times"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.nlos_last_error.argtypes = []
+    lib.nlos_last_error.restype = ctypes.c_char_p
+    lib.nlos_version.argtypes = []
+    lib.nlos_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise NlosError(status, _lib.nlos_last_error().decode())
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class Geometry:
+    nx: int
+    ny: int
+    nt: int
+    bin_width_s: float
+    wall_w_m: float
+    wall_h_m: float
+
+
+class Plan:
+    """A reconstruction plan (owns device tables and a default workspace)."""
+
+    def __init__(self, nx: int, ny: int, nt: int, bin_width_s: float, wall_w_m: float, wall_h_m: float,
+                 method: str = "fk", storage: str = "f32", pad_factor: int = 2, *,
+                 n_depths: int = 0, depth_min_m: float = 0.0, depth_max_m: float = 0.0,
+                 wavelength_m: float = 0.0, cycles: float = 5.0, sigma_s: int = 0, sigma_t: int = 0,
+                 delta_m: float = 0.0):
+        lib = load_library()
+        d = PlanDesc()
+        lib.nlos_plan_desc_default(ctypes.byref(d))
+        d.nx, d.ny, d.nt = nx, ny, nt
+        d.bin_width_s, d.wall_w_m, d.wall_h_m = bin_width_s, wall_w_m, wall_h_m
+        d.method = METHODS[method]
+        d.storage = STORAGES[storage]
+        d.pad_factor = pad_factor
+        d.wavelength_m, d.cycles = wavelength_m, cycles
+        d.n_depths, d.depth_min_m, d.depth_max_m = n_depths, depth_min_m, depth_max_m
+        d.sigma_s, d.sigma_t, d.delta_m = sigma_s, sigma_t, delta_m
+        self.desc = d
+        self.method = method
+        self.storage = storage
+        h = ctypes.c_void_p()
+        _check(lib.nlos_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        shape = (ctypes.c_size_t * 3)()
+        ws, ib, ob = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib.nlos_plan_query(h, ctypes.byref(shape), ctypes.byref(ws), ctypes.byref(ib), ctypes.byref(ob)))
+        self.out_shape = tuple(int(v) for v in shape)
+        self.workspace_bytes = ws.value
+        self.input_bytes = ib.value
+        self.output_bytes = ob.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def input_dtype(self):
+        import torch
+        return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
+
+    def _check_io(self, transient, volume):
+        import torch
+        d = self.desc
+        if not (transient.is_cuda and volume.is_cuda):
+            raise ValueError("transient and volume must be CUDA tensors")
+        if transient.dtype != self.input_dtype() or not transient.is_contiguous() \
+                or tuple(transient.shape) != (d.nx, d.ny, d.nt):
+            raise ValueError(f"transient must be contiguous {self.input_dtype()} [{d.nx},{d.ny},{d.nt}]")
+        if volume.dtype != torch.float32 or not volume.is_contiguous() or tuple(volume.shape) != self.out_shape:
+            raise ValueError(f"volume must be contiguous float32 {list(self.out_shape)}")
+
+    def empty_volume(self):
+        import torch
+        return torch.empty(self.out_shape, dtype=torch.float32, device="cuda")
+
+    def reconstruct(self, transient, volume=None, stream=None, workspace=None):
+        """Reconstruct on the device; returns the volume tensor (asynchronous)."""
+        if volume is None:
+            volume = self.empty_volume()
+        self._check_io(transient, volume)
+        if workspace is None:
+            _check(_lib.nlos_reconstruct(self._h, ctypes.c_void_p(transient.data_ptr()),
+                                         ctypes.c_void_p(volume.data_ptr()), _stream_ptr(stream)))
+        else:
+            _check(_lib.nlos_reconstruct_ws(self._h, ctypes.c_void_p(transient.data_ptr()),
+                                            ctypes.c_void_p(volume.data_ptr()),
+                                            ctypes.c_void_p(workspace.data_ptr()),
+                                            ctypes.c_size_t(workspace.numel() * workspace.element_size()),
+                                            _stream_ptr(stream)))
+        return volume
+
+    def reconstruct_host(self, transient_host, volume_host, stream=None):
+        """End-to-end call on host buffers (numpy arrays or CPU tensors); synchronous."""
+        def ptr(x):
+            return ctypes.c_void_p(x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data)
+        _check(_lib.nlos_reconstruct_host(self._h, ptr(transient_host), ptr(volume_host), _stream_ptr(stream)))
+        return volume_host
+
+    def set_profiling(self, enable: bool):
+        """Record a CUDA event after every stage of each reconstruction."""
+        _check(_lib.nlos_plan_set_profiling(self._h, int(bool(enable))))
+
+    def stage_times(self):
+        """{stage name: accumulated ms} over the profiled calls, and the call count (resets)."""
+        cap = 16
+        times = (ctypes.c_double * cap)()
+        ns, calls = ctypes.c_int(), ctypes.c_longlong()
+        _check(_lib.nlos_plan_stage_times(self._h, times, cap, ctypes.byref(ns), ctypes.byref(calls)))
+        names = [_lib.nlos_plan_stage_name(self._h, i).decode() for i in range(ns.value)]
+        return {nm: times[i] for i, nm in enumerate(names)}, calls.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(_lib.nlos_plan_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def reconstruct_batch(plans, transients, volumes, workspaces=None, stream=None):
+    """Reconstruct several captures forked over the library's streams (asynchronous)."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    T = (ctypes.c_void_p * n)(*[t.data_ptr() for t in transients])
+    V = (ctypes.c_void_p * n)(*[v.data_ptr() for v in volumes])
+    for p, t, v in zip(plans, transients, volumes):
+        p._check_io(t, v)
+    W = None if workspaces is None else (ctypes.c_void_p * n)(*[w.data_ptr() for w in workspaces])
+    _check(_lib.nlos_reconstruct_batch(P, T, V, W, n, _stream_ptr(stream)))
+    return volumes
+
+
+def plan_for_capture(geom, method="fk", storage="f32", **kw) -> Plan:
+    return Plan(geom.nx, geom.ny, geom.nt, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m,
+                method=method, storage=storage, **kw)
+
+
+def version() -> str:
+    return load_library().nlos_version().decode()

@@ -1,0 +1,83 @@
+"""GPU parity of radial phasor-field reconstruction through the C ABI against
+the FP64 oracle (FP32 storage: relative L2 <= 1e-5, identical peak voxel)."""
+import numpy as np
+import pytest
+
+from oracle import pf
+from paper_2608_28183_gb300 import synth
+from tests.gpu_util import exact_input, rel_l2, same_peak, to_device
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def library():
+    from paper_2608_28183_gb300 import build, nlos
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    return nlos.load_library()
+
+
+def _pair(geom, depths, storage="f32", **kw):
+    from paper_2608_28183_gb300 import nlos
+    D, dmin, dmax = depths
+    plan = nlos.plan_for_capture(geom, "pf", storage, n_depths=D, depth_min_m=dmin, depth_max_m=dmax, **kw)
+    oplan = pf.make_plan(geom.nx, geom.ny, geom.nt, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m,
+                         D, dmin, dmax, **{k: v for k, v in kw.items() if v})
+    return plan, oplan
+
+
+def _gpu(plan, H):
+    out = plan.reconstruct(to_device(H, plan.input_dtype()))
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+def _capture(geom, seed, zr):
+    rng = np.random.default_rng(seed)
+    pts = [(rng.uniform(-0.3, 0.3) * geom.wall_w_m, rng.uniform(-0.3, 0.3) * geom.wall_h_m,
+            rng.uniform(*zr), 1.0) for _ in range(3)]
+    return synth.render(geom, synth.Scene(points=np.array(pts)), peak=300.0, background=0.5, seed=seed)
+
+
+CASES = [
+    (synth.Geometry(8, 8, 256, 32e-12, 0.4, 0.4), (5, 0.3, 0.9), (0.4, 0.9)),
+    (synth.Geometry(16, 32, 512, 16e-12, 0.6, 1.0), (37, 0.4, 1.1), (0.5, 1.0)),
+    (synth.Geometry(32, 32, 512, 16e-12, 1.0, 1.0), (130, 0.4, 1.2), (0.5, 1.1)),
+    (synth.Geometry(64, 16, 1024, 16e-12, 2.0, 0.6), (64, 0.5, 2.0), (0.8, 1.8)),
+]
+
+
+@pytest.mark.parametrize("geom,depths,zr", CASES, ids=lambda v: getattr(v, "nx", None) and f"{v.nx}x{v.ny}x{v.nt}")
+def test_pf_parity_small(geom, depths, zr):
+    plan, oplan = _pair(geom, depths)
+    cap = _capture(geom, seed=geom.nx + geom.nt, zr=zr)
+    got = _gpu(plan, cap.counts)
+    ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float32), oplan)
+    err = rel_l2(got, ref)
+    assert err <= 1e-5, err
+    assert same_peak(got, ref)
+
+
+def test_pf_non_confocal_modality():
+    geom, depths, zr = CASES[2]
+    plan, oplan = _pair(geom, depths, sigma_s=1, sigma_t=1, delta_m=0.05)
+    cap = _capture(geom, seed=5, zr=zr)
+    got = _gpu(plan, cap.counts)
+    ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float32), oplan)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_pf_parity_workload_128x128x1024():
+    """Full-size phasor-field workload: 128 x 128 x 1024, 151 frequencies, 128 planes."""
+    cap = synth.make_capture("pf_128x128x1024", 0, device="cuda")
+    g = cap.geometry
+    plan, oplan = _pair(g, (128, 0.5, 2.5))
+    assert plan.out_shape == (128, 128, 128)
+    got = _gpu(plan, cap.counts)
+    ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float32), oplan)
+    err = rel_l2(got, ref)
+    assert err <= 1e-5, err
+    assert same_peak(got, ref)
