@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--grid", default=None,
+                    help="nx,ny,nt: same scene recipe on a smaller grid (profiling captures only)")
     return ap.parse_args()
 
 
@@ -170,7 +172,12 @@ def run_reference(args):
     import numpy as np
     from oracle import fk
     from paper_2608_28183_gb300 import synth
-    cap = synth.make_capture(WORKLOAD, 0, device=None)
+    try:
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else None
+    except Exception:
+        dev = None
+    cap = synth.make_capture(WORKLOAD, 0, device=dev)     # input rendering only, not timed
     g = cap.geometry
     H = cap.counts.astype(np.float32).astype(np.float64)
     fk.fk_reconstruct(H, g.bin_width_s, g.wall_w_m, g.wall_h_m)        # one warm-up volume
@@ -220,7 +227,11 @@ def main():
         if dist:
             dist.barrier()
 
-    cap = synth.make_capture(WORKLOAD, rank, device="cuda")
+    geom = None
+    if args.grid:
+        nx, ny, nt = (int(v) for v in args.grid.split(","))
+        geom = synth.Geometry(nx, ny, nt, 16e-12, 2.0, 2.0)
+    cap = synth.make_capture(WORKLOAD, rank, device="cuda", geom=geom)
     g = cap.geometry
     plan = nlos.plan_for_capture(g, "fk", args.storage)
     H = torch.as_tensor(cap.counts, dtype=torch.float32).to(plan.input_dtype()).cuda().contiguous()
@@ -304,7 +315,8 @@ def main():
         "vs_baseline": value * PAPER_SECONDS_PER_VOLUME,
         "vs_baseline_note": "paper: offline f-k 256x256x512 padded FP32, 0.143 s/volume on an RTX 4080 SUPER, incl. alloc/free",
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "method": "confocal f-k migration", "grid": [g.nx, g.ny, g.nt],
+        "config": {"workload": WORKLOAD if not args.grid else f"{WORKLOAD} scene on {args.grid}",
+                   "method": "confocal f-k migration", "grid": [g.nx, g.ny, g.nt],
                    "padded": [2 * g.nx, 2 * g.ny, 2 * g.nt], "bin_width_s": g.bin_width_s, "wall_m": [g.wall_w_m, g.wall_h_m],
                    "storage": args.storage, "scene": "10 points + 3 oriented patches, Poisson, peak log-uniform 1e2-1e4",
                    "l2": "no flush: each step moves >= 3.5 GB through a 2.2 GB workspace, far above the 129 MB L2",
