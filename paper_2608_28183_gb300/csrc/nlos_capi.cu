@@ -788,3 +788,13 @@ const char* nlos_last_error(void) { return g_err.c_str(); }
 const char* nlos_version(void) { return "nlos-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// Narrow accessors for entry points compiled in other files of the library.
+namespace nlos {
+size_t plan_workspace_bytes(const nlos_plan_s* p) { return p->ws_bytes; }
+bool plan_profiling(const nlos_plan_s* p) { return p->prof_on; }
+nlos_status_t plan_run(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaStream_t s) {
+  return run_plan(p, H, vol, ws, s);
+}
+nlos_status_t set_error(nlos_status_t st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace nlos

@@ -23,7 +23,7 @@ STORAGES = {"f32": NLOS_F32, "f16": NLOS_F16, "bf16": NLOS_BF16}
 EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nlos_reconstruct",
             "nlos_reconstruct_ws", "nlos_reconstruct_host", "nlos_reconstruct_batch",
             "nlos_plan_set_profiling", "nlos_plan_stage_times", "nlos_plan_stage_name",
-            "nlos_plan_destroy", "nlos_last_error", "nlos_version"]
+            "nlos_plan_destroy", "nlos_last_error", "nlos_version", "nlos_reconstruct_noalloc"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -69,6 +69,8 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_reconstruct_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                            ctypes.POINTER(vp), ctypes.c_int, vp]
     lib.nlos_plan_destroy.argtypes = [vp]
+    lib.nlos_reconstruct_noalloc.argtypes = [vp, vp, vp, vp]
+    lib.nlos_reconstruct_noalloc.restype = ctypes.c_int
     lib.nlos_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.nlos_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
