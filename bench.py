@@ -153,16 +153,40 @@ class ClockSampler:
 
 
 def cpu_baseline_oracle(counts, geom):
-    """The FP64 oracle as it stands, on this host's cores, one full volume."""
+    """The FP64 oracle as it stands, on this host's cores, one full volume.
+    Returns the baseline record and the oracle's volume."""
     from oracle import fk
     import numpy as np
     H = np.asarray(counts, dtype=np.float64)
     t = time.perf_counter()
-    fk.fk_reconstruct(H, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m, workers=os.cpu_count())
+    R = fk.fk_reconstruct(H, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m, workers=os.cpu_count())
     dt = time.perf_counter() - t
     return {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": "1 full 256x256x512 volume (scipy.fft with all host threads; numpy elementwise steps single-threaded)",
-            "seconds": dt}
+            "seconds": dt}, R
+
+
+def rel_l2(a, b):
+    import numpy as np
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def time_plan(plan, H, vol, steps, torch):
+    """CUDA-event time of `steps` back-to-back reconstructions: (total ms, sorted per-step ms)."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for i in range(steps):
+        starts[i].record()
+        plan.reconstruct(H, vol)
+        ends[i].record()
+    t1.record()
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1), sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
 
 
 def run_reference(args):
@@ -302,12 +326,35 @@ def main():
     step_mean_ms = total_ms / K
     pipe_achieved = pipe_bytes / (step_mean_ms * 1e-3) / 1e9
 
-    cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_oracle(H.float().cpu().numpy(), g)
+    def pct(q, xs=None):
+        xs = step_ms if xs is None else xs
+        return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
 
-    def pct(q):
-        return step_ms[min(len(step_ms) - 1, int(round(q * (len(step_ms) - 1))))]
+    # FP16-storage variant of the same workload (same timing protocol)
+    variants = {}
+    if args.storage == "f32":
+        p16 = nlos.plan_for_capture(g, "fk", "f16")
+        H16 = torch.as_tensor(cap.counts, dtype=torch.float32).to(torch.float16).cuda().contiguous()
+        v16 = p16.empty_volume()
+        for _ in range(5):
+            p16.reconstruct(H16, v16)
+        K16 = max(50, K // 4)
+        tot16, st16 = time_plan(p16, H16, v16, K16, torch)
+        variants["f16_storage"] = {"value": K16 / (tot16 / 1e3), "unit": UNIT, "steps": K16,
+                                   "ms_per_step": tot16 / K16, "latency_ms": {"p50": pct(0.5, st16), "p99": pct(0.99, st16)},
+                                   "bytes_model": "54 V", "pipeline_frac": pipeline_bytes(g.nx, g.ny, g.nt, "f16")
+                                   / (tot16 / K16 * 1e-3) / 1e9 / peak}
+
+    cpu = None
+    parity = {}
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, Rref = cpu_baseline_oracle(H.float().cpu().numpy(), g)
+        parity["f32_rel_l2_vs_oracle"] = rel_l2(vol.cpu().numpy(), Rref)
+        if "f16_storage" in variants:
+            from oracle import fk as ofk
+            H16d = H16.float().cpu().numpy().astype(np.float64)
+            R16 = ofk.fk_reconstruct(H16d, g.bin_width_s, g.wall_w_m, g.wall_h_m, workers=os.cpu_count())
+            variants["f16_storage"]["rel_l2_vs_oracle"] = rel_l2(v16.cpu().numpy(), R16)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
@@ -331,6 +378,8 @@ def main():
         "stages_ms_per_launch": per_launch_ms,
         "stage_bytes": sb,
         "cpu_baseline": cpu,
+        "parity": parity,
+        "variants": variants,
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": Ke,
                 "h2d_bytes_per_step": plan.input_bytes, "d2h_bytes_per_step": plan.output_bytes,
                 "path": "nlos_reconstruct_host, pinned host buffers"},

@@ -25,28 +25,31 @@ template <int L, int LD, int ST, class TS>
 struct AxisCtx {
   using TR = typename RealOf<TS>::T;
   static constexpr int IC = AxisTile<L>::IC;
+  static constexpr int SSTRIDE = IC;
   const void* in;
   void* out;
   const float2* tw;
-  float2* sm;
+  float2* smem;
   long long in_base, out_base;     // offsets of (outer, axis 0, inner column)
   long long in_axis, out_axis;
   int L_in, L_out, c, t_len, inverse;
   bool valid;
   float ldmul, stmul, tmul;
 
-  __device__ __forceinline__ float2 load(int l) const {
-    if (!valid || l >= L_in) return make_float2(0.f, 0.f);
+  __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
+    x[0] = make_float2(0.f, 0.f);
+    if (!valid || l >= L_in) return;
     if constexpr (LD == kLoadReal) {
       float v = Real<TR>::get(static_cast<const TR*>(in) + in_base + l * in_axis) * ldmul;
-      return make_float2(v * tmul, 0.f);
+      x[0] = make_float2(v * tmul, 0.f);
     } else {
       float2 v = cscale(Cpx<TS>::get(static_cast<const TS*>(in) + in_base + l * in_axis), ldmul);
-      return inverse ? cconj(v) : v;
+      x[0] = inverse ? cconj(v) : v;
     }
   }
-  __device__ __forceinline__ float2& at(int l) const { return sm[pad16(l) * IC + c]; }
-  __device__ __forceinline__ void store(int l, float2 v) const {
+  __device__ __forceinline__ float2* sm(int) const { return smem + c; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
+    float2 v = x[0];
     if (!valid || l >= L_out) return;
     const long long o = out_base + l * out_axis;
     if constexpr (ST == kStoreCpx) {
@@ -60,7 +63,7 @@ struct AxisCtx {
   }
 };
 
-template <int L, int LD, int ST, class TS>
+template <int L, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 __global__ void __launch_bounds__(AxisTile<L>::THREADS)
 axis_fft_kernel(const AxisParams p) {
   extern __shared__ float2 axis_sm[];
@@ -73,7 +76,7 @@ axis_fft_kernel(const AxisParams p) {
   ctx.in = p.in;
   ctx.out = p.out;
   ctx.tw = p.tw;
-  ctx.sm = axis_sm;
+  ctx.smem = axis_sm;
   ctx.c = c;
   ctx.valid = ii < p.inner;
   ctx.in_base = outer * p.in_outer + ii;
@@ -87,13 +90,13 @@ axis_fft_kernel(const AxisParams p) {
   ctx.ldmul = p.ld_dev_scale ? *p.ld_dev_scale : 1.0f;
   ctx.stmul = p.scale * (p.st_dev_scale ? *p.st_dev_scale : 1.0f);
   ctx.tmul = p.t_len > 0 ? (float)(int)(ii % p.t_len) * p.t_scale : 1.0f;
-  fft_run<L>(ctx, j0);
+  fftn_run<L, 1, kHalfIn, kHalfOut>(ctx, j0);
 }
 
-template <int L, int LD, int ST, class TS>
+template <int L, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
   using Tile = AxisTile<L>;
-  auto k = axis_fft_kernel<L, LD, ST, TS>;
+  auto k = axis_fft_kernel<L, LD, ST, TS, kHalfIn, kHalfOut>;
   if (Tile::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile::SMEM);
     if (e != cudaSuccess) return e;
@@ -103,28 +106,38 @@ cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int LD, int ST, class TS>
+template <int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_len(const AxisLaunch& l, cudaStream_t s) {
   switch (l.L) {
-    case 16: return launch_axis_one<16, LD, ST, TS>(l, s);
-    case 32: return launch_axis_one<32, LD, ST, TS>(l, s);
-    case 64: return launch_axis_one<64, LD, ST, TS>(l, s);
-    case 128: return launch_axis_one<128, LD, ST, TS>(l, s);
-    case 256: return launch_axis_one<256, LD, ST, TS>(l, s);
-    case 512: return launch_axis_one<512, LD, ST, TS>(l, s);
-    case 1024: return launch_axis_one<1024, LD, ST, TS>(l, s);
-    case 2048: return launch_axis_one<2048, LD, ST, TS>(l, s);
+    case 16: return launch_axis_one<16, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    case 32: return launch_axis_one<32, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    case 64: return launch_axis_one<64, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    case 128: return launch_axis_one<128, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    case 256: return launch_axis_one<256, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    case 512: return launch_axis_one<512, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    case 1024: return launch_axis_one<1024, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    case 2048: return launch_axis_one<2048, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
+// The sequences use five shapes: forward passes read a zero-padded upper half
+// (L_in = L/2) and keep every output, inverse passes read every input and keep
+// the lower half (L_out = L/2); the real-input x pass keeps kx in [0, L/2].
 template <class TS>
 cudaError_t launch_axis_typed(const AxisLaunch& l, cudaStream_t s) {
   if (l.n_outer <= 0 || l.n_outer > 65535 || l.p.inner <= 0) return cudaErrorInvalidValue;
-  if (l.load_mode == kLoadReal && l.store_mode == kStoreCpx) return launch_axis_len<kLoadReal, kStoreCpx, TS>(l, s);
-  if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx) return launch_axis_len<kLoadCpx, kStoreCpx, TS>(l, s);
-  if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs2) return launch_axis_len<kLoadCpx, kStoreAbs2, TS>(l, s);
-  if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs) return launch_axis_len<kLoadCpx, kStoreAbs, TS>(l, s);
+  const bool half_in = 2 * l.p.L_in == l.L, half_out = 2 * l.p.L_out <= l.L;
+  if (l.load_mode == kLoadReal && l.store_mode == kStoreCpx && half_in && !half_out)
+    return launch_axis_len<kLoadReal, kStoreCpx, TS, true, false>(l, s);
+  if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx && half_in && !half_out)
+    return launch_axis_len<kLoadCpx, kStoreCpx, TS, true, false>(l, s);
+  if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx && l.p.L_in == l.L && half_out)
+    return launch_axis_len<kLoadCpx, kStoreCpx, TS, false, true>(l, s);
+  if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs2 && l.p.L_in == l.L && half_out)
+    return launch_axis_len<kLoadCpx, kStoreAbs2, TS, false, true>(l, s);
+  if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs && l.p.L_in == l.L && half_out)
+    return launch_axis_len<kLoadCpx, kStoreAbs, TS, false, true>(l, s);
   return cudaErrorInvalidValue;
 }
 

@@ -38,13 +38,17 @@ struct StoltCoord {
   bool valid;
 };
 
+// mu = sqrt(A + m^2) to ~1e-11 absolute: y0 = S * rsqrt(S) is within a few
+// ulp of sqrt(S); one Newton step from the exact FMA residual S - y0^2 gives
+// mu = y0 + mlo. The weight m/mu uses the same reciprocal square root.
 __device__ __forceinline__ StoltCoord stolt_coord(float Ahi, float Alo, int m, int n) {
   StoltCoord c;
   float2 s = two_sum(Ahi, (float)(m * m));
   s = fast_two_sum(s.x, s.y + Alo);
-  const float y0 = sqrtf(s.x);
+  const float rs = rsqrtf(s.x);
+  const float y0 = s.x * rs;
   const float res = fmaf(-y0, y0, s.x) + s.y;     // (A + m^2) - y0^2
-  const float mlo = res * (0.5f / y0);            // mu = y0 + mlo
+  const float mlo = res * (0.5f * rs);            // mu = y0 + mlo
   int k0 = (int)floorf(y0);
   float al = (y0 - (float)k0) + mlo;
   if (al < 0.f) {
@@ -58,65 +62,67 @@ __device__ __forceinline__ StoltCoord stolt_coord(float Ahi, float Alo, int m, i
   c.k0 = k0;
   c.k1 = min(k0 + 1, n - 1);
   c.alpha = al;
-  c.jac = (float)m / y0;
+  c.jac = (float)m * rs;
   return c;
 }
 
+// forward transform of the stored pencil; its upper half is zero padding
 template <int L, class TS>
 struct FkFwdCtx {
+  static constexpr int SSTRIDE = 1;
   const TS* g;
   float2* U;
   float2* W;
   const float2* tw;
-  int n;
   bool valid;
   float ldmul;
-  __device__ __forceinline__ float2 load(int l) const {
-    if (!valid || l >= n) return make_float2(0.f, 0.f);
-    return cscale(Cpx<TS>::get(g + l), ldmul);
+  __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
+    x[0] = valid ? cscale(Cpx<TS>::get(g + l), ldmul) : make_float2(0.f, 0.f);
   }
-  __device__ __forceinline__ float2& at(int l) const { return W[pad16(l)]; }
-  __device__ __forceinline__ void store(int l, float2 v) const { U[pad16(l)] = v; }
+  __device__ __forceinline__ float2* sm(int) const { return W; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[pad16(l)] = x[0]; }
 };
 
-template <int L, class TS, bool kMirror>
+// both inverse transforms at once: t = 0 the stored pencil, t = 1 its
+// Hermitian partner; one Stolt coordinate per m feeds both
+template <int L, class TS>
 struct FkInvCtx {
+  static constexpr int SSTRIDE = 1;
   const float2* U;
-  float2* W;
+  float2* W0;
+  float2* W1;
   const float2* tw;
-  TS* out;
+  TS* out0;
+  TS* out1;
   int n;
   float Ahi, Alo;
-  bool do_store;
+  bool st0, st1;
   float stmul;
-  __device__ __forceinline__ float2 load(int m) const {
-    if (m < 1 || m > n - 1) return make_float2(0.f, 0.f);
+  __device__ __forceinline__ void load(int m, float2 (&x)[2]) const {
+    x[0] = x[1] = make_float2(0.f, 0.f);
+    if (m < 1) return;                                // m <= n-1 (upper half is pruned)
     const StoltCoord c = stolt_coord(Ahi, Alo, m, n);
-    if (!c.valid) return make_float2(0.f, 0.f);
-    float2 u0, u1;
-    if (!kMirror) {
-      u0 = U[pad16(c.k0)];
-      u1 = U[pad16(c.k1)];
-    } else {
-      u0 = U[pad16((L - c.k0) & (L - 1))];
-      u1 = U[pad16((L - c.k1) & (L - 1))];
-    }
-    float2 v = make_float2(fmaf(c.alpha, u1.x - u0.x, u0.x), fmaf(c.alpha, u1.y - u0.y, u0.y));
-    v = cscale(v, c.jac);
-    // inverse DFT as conj(DFT(conj(V))): the direct pencil loads conj(V); the
-    // partner's V is conj(lerp) * m/mu, whose conjugate is lerp * m/mu.
-    return kMirror ? v : cconj(v);
+    if (!c.valid) return;
+    const float2 u0 = U[pad16(c.k0)], u1 = U[pad16(c.k1)];
+    const float2 w0 = U[pad16((L - c.k0) & (L - 1))], w1 = U[pad16((L - c.k1) & (L - 1))];
+    const float2 d = make_float2(fmaf(c.alpha, u1.x - u0.x, u0.x), fmaf(c.alpha, u1.y - u0.y, u0.y));
+    const float2 e = make_float2(fmaf(c.alpha, w1.x - w0.x, w0.x), fmaf(c.alpha, w1.y - w0.y, w0.y));
+    // inverse DFT as conj(DFT(conj(V))): the pencil loads conj(V); the
+    // partner's V is conj(lerp) * m/mu, whose conjugate is lerp * m/mu
+    x[0] = cconj(cscale(d, c.jac));
+    x[1] = cscale(e, c.jac);
   }
-  __device__ __forceinline__ float2& at(int l) const { return W[pad16(l)]; }
-  __device__ __forceinline__ void store(int l, float2 v) const {
-    if (do_store && l < n) Cpx<TS>::put(out + l, cscale(cconj(v), stmul));
+  __device__ __forceinline__ float2* sm(int t) const { return t == 0 ? W0 : W1; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[2]) const {   // l < n (kHalfOut)
+    if (st0) Cpx<TS>::put(out0 + l, cscale(cconj(x[0]), stmul));
+    if (st1) Cpx<TS>::put(out1 + l, cscale(cconj(x[1]), stmul));
   }
 };
 
 template <int L> struct FkTile {
   static constexpr int PPC = L <= 256 ? 8 : (L <= 1024 ? 4 : 2);   // pencils per CTA
   static constexpr int THREADS = PPC * (L / 16);
-  static constexpr size_t SMEM = sizeof(float2) * 2 * PPC * FftShape<L>::SMEM;
+  static constexpr size_t SMEM = sizeof(float2) * 3 * PPC * FftShape<L>::SMEM;
 };
 
 template <int L, class TS>
@@ -133,11 +139,12 @@ fk_zstage_kernel(const FkZParams p) {
   const int kx = valid ? (int)(pid / twob) : 0;
   const int ky = valid ? (int)(pid % twob) : 0;
   float2* U = fk_sm + w * S::SMEM;
-  float2* W = fk_sm + (PPC + w) * S::SMEM;
+  float2* W0 = fk_sm + (PPC + w) * S::SMEM;
+  float2* W1 = fk_sm + (2 * PPC + w) * S::SMEM;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
-    FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W, p.tw, p.n, valid, ldmul};
-    fft_run<L>(ctx, j0);
+    FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul};
+    fftn_run<L, 1, true, false>(ctx, j0);
   }
   __syncthreads();
   const float2 ax = p.ax[kx];
@@ -149,18 +156,10 @@ fk_zstage_kernel(const FkZParams p) {
   const int mkx = (kx == 0) ? 0 : 2 * p.a - kx;
   const int mky = (twob - ky) & (twob - 1);
   const long long o_mirror = ((long long)mkx * twob + mky) * p.n;
-  {
-    FkInvCtx<L, TS, false> ctx{U, W, p.tw, psi + o_direct, p.n, A.x, A.y, valid, p.st_scale};
-    fft_run<L>(ctx, j0);
-  }
-  __syncthreads();
-  {
-    // run for every pencil so all threads meet the same barriers; stored only
-    // where the partner is not itself a stored pencil
-    FkInvCtx<L, TS, true> ctx{U, W, p.tw, psi + o_mirror, p.n, A.x, A.y,
-                              valid && kx > 0 && kx < p.a, p.st_scale};
-    fft_run<L>(ctx, j0);
-  }
+  // the partner is stored only where it is not itself a stored pencil
+  FkInvCtx<L, TS> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, p.n, A.x, A.y,
+                      valid, valid && kx > 0 && kx < p.a, p.st_scale};
+  fftn_run<L, 2, true, true>(ctx, j0);
 }
 
 template <int L, class TS>

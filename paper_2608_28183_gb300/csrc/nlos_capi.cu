@@ -484,7 +484,8 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_MARK(p, s, sid++);
   // FK4: x inverse (keep x < a), |psi|^2 with the 1/(8abn) normalisation
   const double N = 8.0 * a * b * n;
-  const double gprod = (double)g2a * g2b * g2n * g2n * g2b * g2a;
+  // pass scales applied to the data before this last pass (it applies none of its own)
+  const double gprod = (double)g2a * g2b * g2n * g2n * g2b;
   const float fscale = (float)(1.0 / (N * N * gprod * gprod));
   l = axis(st, 2 * a, 1, b0, vol, b * n, 0, b * n, 0, b * n, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a]);
   l.store_mode = kStoreAbs2;
@@ -514,7 +515,10 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     inv_s = scal + 1;
   }
   const float gn = pass_scale(st, n), g2a = pass_scale(st, 2 * a), g2b = pass_scale(st, 2 * b);
+  // depth-sum output scale: undoes the stored kernel's scale and, for 16-bit
+  // storage, divides by 16 so sums over the band stay inside the half range
   const float c3 = st == kF32 ? 1.0f : (float)(1.0 / (16.0 * p->kr_scale));
+  const double c3_data = st == kF32 ? 1.0 : 1.0 / 16.0;      // c3 * kr_scale
   // PF1: temporal band transform with w(f)
   PfBandParams bp{};
   bp.H = H;
@@ -557,7 +561,8 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   l = axis(st, 2 * b, 2 * a, b1, b0, D, 2 * b * D, D, b * D, D, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b]);
   NLOS_CU(launch_axis_fft(l, s), "pf y-inverse");
   NLOS_MARK(p, s, sid++);
-  const double gprod = (double)gn * g2b * g2a * c3 * g2b * g2a;
+  // scales the data carries into this last pass (it applies none of its own)
+  const double gprod = (double)gn * g2b * g2a * c3_data * g2b;
   const float fscale = (float)(1.0 / (4.0 * a * b * gprod));
   l = axis(st, 2 * a, 1, b0, vol, b * D, 0, b * D, 0, b * D, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a]);
   l.store_mode = kStoreAbs;

@@ -153,28 +153,82 @@ template <int L> struct FftShape {
 // (stride 16) and the contiguous gathers free of bank conflicts.
 __device__ __forceinline__ int pad16(int l) { return l + (l >> 4); }
 
-// Runs passes P..NPASS-1 of an L-point transform for one thread.
+// Radix-16 DFT whose inputs 8..15 are zero (first pass of a transform whose
+// upper half is zero padding): the first radix-4 stage sees (x0, x1, 0, 0).
+__device__ __forceinline__ void dft16_half(float2* v) {
+  float2 y[4][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+    const float2 x0 = v[n1], x1 = v[n1 + 4];
+    const float2 mi = cmul_mi(x1);
+    y[n1][0] = cadd(x0, x1);
+    y[n1][2] = csub(x0, x1);
+    y[n1][1] = cadd(x0, mi);
+    y[n1][3] = csub(x0, mi);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) y[n1][k2] = mul_w32(y[n1][k2], 2 * n1 * k2);
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 t[4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) t[n1] = y[n1][k2];
+    Dft<4>::run(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = t[k1];
+  }
+}
+
+// Runs passes P..NPASS-1 of NT L-point transforms that share one schedule
+// (same thread mapping and twiddles) for one thread.
+//   kHalfIn:  inputs l >= L/2 are zero (not loaded; pruned first butterfly)
+//   kHalfOut: only outputs l < L/2 are stored (dead outputs are not computed)
 // Ctx provides:
-//   float2 load(int l)           element l of the input (first pass only)
-//   void   store(int l, float2)  element l of the output (last pass only)
-//   float2& at(int l)            shared-memory slot of element l (middle passes)
-//   const float2* tw             twiddle table of the plan for length L
-template <int L, int P, class Ctx>
-__device__ __forceinline__ void fft_passes(Ctx& ctx, const int j0, float2 (&v)[16]) {
+//   void load(int l, float2 (&x)[NT])        input element l of every transform (first pass)
+//   void store(int l, const float2 (&x)[NT]) output element l of every transform (last pass)
+//   float2* sm(int t)                        shared-memory base of transform t; element l
+//                                            lives at sm(t)[pad16(l) * SSTRIDE]
+//   static constexpr int SSTRIDE
+//   const float2* tw                         twiddle table of the plan for length L
+template <int L, int NT, bool kHalfIn, bool kHalfOut, int P, class Ctx>
+__device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[NT][16]) {
   using S = FftShape<L>;
   constexpr int R = S::radix(P);
   constexpr int NS = S::span(P);
   constexpr int BPT = 16 / R;
+  constexpr int Q = L / R;
+  constexpr int SS = Ctx::SSTRIDE;
   constexpr bool kFirst = (P == 0);
   constexpr bool kLast = (P == S::NPASS - 1);
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int j = j0 + i * S::TPC;
+    if constexpr (kFirst) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int l = j + r * (L / R);
-      if constexpr (kFirst) v[i * R + r] = ctx.load(l);
-      else v[i * R + r] = ctx.at(l);
+      for (int r = 0; r < R; ++r) {
+        if (kHalfIn && 2 * r >= R) {
+#pragma unroll
+          for (int t = 0; t < NT; ++t) v[t][i * R + r] = make_float2(0.f, 0.f);
+        } else {
+          float2 x[NT];
+          ctx.load(j + r * Q, x);
+#pragma unroll
+          for (int t = 0; t < NT; ++t) v[t][i * R + r] = x[t];
+        }
+      }
+    } else if constexpr (Q % 16 == 0) {
+      const int pj = pad16(j) * SS;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const float2* s = ctx.sm(t) + pj;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[t][i * R + r] = s[r * (Q + Q / 16) * SS];
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[t][i * R + r] = ctx.sm(t)[pad16(j + r * Q) * SS];
     }
   }
   if constexpr (!kFirst) __syncthreads();
@@ -182,34 +236,66 @@ __device__ __forceinline__ void fft_passes(Ctx& ctx, const int j0, float2 (&v)[1
   for (int i = 0; i < BPT; ++i) {
     const int j = j0 + i * S::TPC;
     if constexpr (!kFirst) {
-      const int k = j & (NS - 1);
-      const float2* t = ctx.tw + S::twoff(P) + k;
+      const float2* tp = ctx.tw + S::twoff(P) + (j & (NS - 1));
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[i * R + r] = cmul(v[i * R + r], __ldg(t + r * NS));
+      for (int r = 1; r < R; ++r) {
+        const float2 w = __ldg(tp + r * NS);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) v[t][i * R + r] = cmul(v[t][i * R + r], w);
+      }
     }
-    Dft<R>::run(&v[i * R]);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      if constexpr (kFirst && kHalfIn && R == 16) dft16_half(&v[t][i * R]);
+      else Dft<R>::run(&v[t][i * R]);
+    }
   }
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int j = j0 + i * S::TPC;
     const int base = (j / NS) * NS * R + (j & (NS - 1));
+    if constexpr (kLast) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int l = base + r * NS;
-      if constexpr (kLast) ctx.store(l, v[i * R + r]);
-      else ctx.at(l) = v[i * R + r];
+      for (int r = 0; r < R; ++r) {
+        if (kHalfOut && 2 * r >= R) continue;
+        float2 x[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) x[t] = v[t][i * R + r];
+        ctx.store(base + r * NS, x);
+      }
+    } else if constexpr (NS == 1 && R == 16) {
+      const int pb = 17 * j * SS;          // pad16(16 j + r) = 17 j + r
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        float2* s = ctx.sm(t) + pb;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[r * SS] = v[t][i * R + r];
+      }
+    } else if constexpr (NS % 16 == 0) {
+      const int pb = pad16(base) * SS;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        float2* s = ctx.sm(t) + pb;
+#pragma unroll
+        for (int r = 0; r < R; ++r) s[r * (NS + NS / 16) * SS] = v[t][i * R + r];
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < NT; ++t)
+#pragma unroll
+        for (int r = 0; r < R; ++r) ctx.sm(t)[pad16(base + r * NS) * SS] = v[t][i * R + r];
     }
   }
   if constexpr (!kLast) {
     __syncthreads();
-    fft_passes<L, P + 1>(ctx, j0, v);
+    fftn_passes<L, NT, kHalfIn, kHalfOut, P + 1>(ctx, j0, v);
   }
 }
 
-template <int L, class Ctx>
-__device__ __forceinline__ void fft_run(Ctx& ctx, const int j0) {
-  float2 v[16];
-  fft_passes<L, 0>(ctx, j0, v);
+template <int L, int NT, bool kHalfIn, bool kHalfOut, class Ctx>
+__device__ __forceinline__ void fftn_run(Ctx& ctx, const int j0) {
+  float2 v[NT][16];
+  fftn_passes<L, NT, kHalfIn, kHalfOut, 0>(ctx, j0, v);
 }
 
 // ---------------------------------------------------------------------------

@@ -13,6 +13,7 @@ namespace nlos {
 // ---------------------------------------------------------------------------
 template <int L, class TR, class TS>
 struct PfBandCtx {
+  static constexpr int SSTRIDE = 1;
   const TR* h;
   TS* P;
   float2* W;
@@ -21,14 +22,13 @@ struct PfBandCtx {
   int k_lo, F;
   bool valid;
   float ldmul, stmul;
-  __device__ __forceinline__ float2 load(int l) const {
-    if (!valid) return make_float2(0.f, 0.f);
-    return make_float2(Real<TR>::get(h + l) * ldmul, 0.f);
+  __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
+    x[0] = valid ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f) : make_float2(0.f, 0.f);
   }
-  __device__ __forceinline__ float2& at(int l) const { return W[pad16(l)]; }
-  __device__ __forceinline__ void store(int l, float2 v) const {
+  __device__ __forceinline__ float2* sm(int) const { return W; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     const int f = l - k_lo;
-    if (valid && f >= 0 && f < F) Cpx<TS>::put(P + f, cscale(v, __ldg(w + f) * stmul));
+    if (valid && f >= 0 && f < F) Cpx<TS>::put(P + f, cscale(x[0], __ldg(w + f) * stmul));
   }
 };
 
@@ -52,7 +52,7 @@ pf_band_kernel(const PfBandParams p) {
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   PfBandCtx<L, TR, TS> ctx{static_cast<const TR*>(p.H) + q * p.n, static_cast<TS*>(p.P) + q * p.F,
                            pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale};
-  fft_run<L>(ctx, j0);
+  fftn_run<L, 1, false, false>(ctx, j0);
 }
 
 template <int L, class TR, class TS>
