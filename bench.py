@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--storage", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--no-extras", action="store_true", help="skip the batch and serving measurements")
     ap.add_argument("--grid", default=None,
                     help="nx,ny,nt: same scene recipe on a smaller grid (profiling captures only)")
     return ap.parse_args()
@@ -187,6 +188,152 @@ def time_plan(plan, H, vol, steps, torch):
     t1.record()
     torch.cuda.synchronize()
     return t0.elapsed_time(t1), sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+
+def _mixed_specs(rng, n, sides, bins, storage):
+    """n capture descriptions: sides x bins drawn uniformly, f-k / phasor-field alternating."""
+    from paper_2608_28183_gb300 import synth
+    out = []
+    for k in range(n):
+        side = int(rng.choice(sides))
+        nt = int(rng.choice(bins))
+        g = synth.Geometry(side, side, nt, 16e-12, 2.0, 2.0)
+        method = "fk" if k % 2 == 0 else "pf"
+        kw = {} if method == "fk" else dict(n_depths=128, depth_min_m=0.4, depth_max_m=nt * g.bin_depth_m)
+        out.append((g, method, storage, kw))
+    return out
+
+
+def _point_capture(synth, g, rng, seed):
+    import numpy as np
+    zmax = 0.9 * g.nt * g.bin_depth_m
+    pts = np.stack([rng.uniform(-0.4, 0.4, 10) * g.wall_w_m, rng.uniform(-0.4, 0.4, 10) * g.wall_h_m,
+                    rng.uniform(0.3, 1.0, 10) * zmax, rng.uniform(0.3, 1.0, 10)], axis=1)
+    return synth.render(g, synth.Scene(points=pts), peak=float(10 ** rng.uniform(2, 4)), background=0.5,
+                        seed=seed, device="cuda")
+
+
+def batch_bench(torch, nlos, synth, reps=20):
+    """32 captures (64/128/256 squared x 512/1024 bins, half f-k half phasor),
+    FP16 storage, autotuned plans, recorded once into a CUDA graph; compared
+    with the same captures reconstructed one at a time with FP32 plans."""
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(3000))
+    specs = _mixed_specs(rng, 32, [64, 128, 256], [512, 1024], "f16")
+    plans, ins, outs, plans32, ins32, outs32 = [], [], [], [], [], []
+    for k, (g, m, st, kw) in enumerate(specs):
+        cap = _point_capture(synth, g, rng, 3000 + k)
+        p = nlos.plan_for_capture(g, m, st, **kw)
+        p.autotune()
+        plans.append(p)
+        ins.append(torch.as_tensor(cap.counts, dtype=torch.float32).to(torch.float16).cuda())
+        outs.append(p.empty_volume())
+        p32 = nlos.plan_for_capture(g, m, "f32", **kw)
+        plans32.append(p32)
+        ins32.append(torch.as_tensor(cap.counts, dtype=torch.float32).cuda())
+        outs32.append(p32.empty_volume())
+    batch = nlos.Batch(plans, ins, outs)
+    for _ in range(3):
+        batch.launch()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        batch.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / reps
+    for p, x, o in zip(plans32, ins32, outs32):
+        p.reconstruct(x, o)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        for p, x, o in zip(plans32, ins32, outs32):
+            p.reconstruct(x, o)
+    e1.record()
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / reps
+    rel = max(float(torch.linalg.vector_norm((a - b).double()) / torch.linalg.vector_norm(b.double()))
+              for a, b in zip(outs, outs32))
+    batch.close()
+    return {"captures": 32, "mix": "64/128/256 squared x 512/1024 bins, 16 f-k + 16 phasor (128 planes)",
+            "graph_fp16_volumes_per_s": 32 / (t_batch * 1e-3), "graph_ms": t_batch,
+            "sequential_fp32_volumes_per_s": 32 / (t_seq * 1e-3), "sequential_ms": t_seq,
+            "max_rel_l2_fp16_vs_fp32": rel, "autotuned": True}
+
+
+def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000), seconds=2.0, budget_gb=120):
+    """Poisson arrivals at each rate; each request a capture of side 32..256
+    and 256/512/1024 bins, f-k or phasor at 50/50, FP16, through the
+    continuous-batching server (budget 120 GB, 8 slots); against the plain FP32
+    one-at-a-time path fed by the same arrivals."""
+    import threading
+    import numpy as np
+    rng = np.random.Generator(np.random.PCG64(4000))
+    specs = []
+    for side in (32, 64, 128, 256):
+        for nt in (256, 512, 1024):
+            for m in ("fk", "pf"):
+                g = synth.Geometry(side, side, nt, 16e-12, 2.0, 2.0)
+                kw = {} if m == "fk" else dict(n_depths=128, depth_min_m=0.4, depth_max_m=nt * g.bin_depth_m)
+                specs.append((g, m, kw))
+    server = nlos.Server(memory_budget_bytes=budget_gb << 30, n_slots=8)
+    pool = []
+    ring = 8
+    for k, (g, m, kw) in enumerate(specs):
+        cap = _point_capture(synth, g, rng, 4000 + k)
+        d16 = nlos.desc_for_capture(g, m, "f16", **kw)
+        server.preload(d16)
+        p32 = nlos.plan_for_capture(g, m, "f32", **kw)
+        x16 = torch.as_tensor(cap.counts, dtype=torch.float32).to(torch.float16).cuda()
+        x32 = torch.as_tensor(cap.counts, dtype=torch.float32).cuda()
+        outs = [p32.empty_volume() for _ in range(ring)]
+        pool.append((d16, x16, p32, x32, outs))
+    torch.cuda.synchronize()
+    results = []
+    for rate in rates:
+        n = max(5, int(rate * seconds))
+        arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        pick = rng.integers(0, len(pool), n)
+        # continuous-batching server
+        tickets = [None] * n
+        server.stats(reset=True)
+        t0 = time.perf_counter()
+        def waiter():
+            for i in range(n):
+                while tickets[i] is None:
+                    time.sleep(5e-5)
+                server.wait(tickets[i])
+        th = threading.Thread(target=waiter)
+        th.start()
+        for i in range(n):
+            dt = arr[i] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            d16, x16, _, _, outs = pool[pick[i]]
+            tickets[i] = server.submit(d16, x16, outs[i % ring])
+        th.join()
+        st = server.stats(reset=True)
+        span = time.perf_counter() - t0
+        # plain FP32 one-at-a-time path, same arrivals (latency includes queueing)
+        lat = []
+        t0 = time.perf_counter()
+        for i in range(n):
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            _, _, p32, x32, outs = pool[pick[i]]
+            p32.reconstruct(x32, outs[i % ring])
+            torch.cuda.synchronize()
+            lat.append((time.perf_counter() - t0 - arr[i]) * 1e3)
+        span32 = time.perf_counter() - t0
+        lat.sort()
+        results.append({"rate_rps": rate, "requests": n,
+                        "served_fp16": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "volumes_per_s": n / span},
+                        "serial_fp32": {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(n - 1, int(0.99 * (n - 1) + 0.5))],
+                                        "volumes_per_s": n / span32}})
+    server.close()
+    return {"budget_gb": budget_gb, "slots": 8, "shapes": len(specs), "sweep": results}
 
 
 def run_reference(args):
@@ -345,6 +492,14 @@ def main():
                                    "bytes_model": "54 V", "pipeline_frac": pipeline_bytes(g.nx, g.ny, g.nt, "f16")
                                    / (tot16 / K16 * 1e-3) / 1e9 / peak}
 
+    extras = {}
+    if world == 1 and not args.no_extras and not args.grid:
+        for name, fn in (("batch", batch_bench), ("serving", serving_bench)):
+            try:
+                extras[name] = fn(torch, nlos, synth)
+            except Exception as exc:     # report, do not lose the headline line
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+
     cpu = None
     parity = {}
     if world == 1 and not args.no_cpu_baseline:
@@ -380,6 +535,8 @@ def main():
         "cpu_baseline": cpu,
         "parity": parity,
         "variants": variants,
+        "batch": extras.get("batch"),
+        "serving": extras.get("serving"),
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": Ke,
                 "h2d_bytes_per_step": plan.input_bytes, "d2h_bytes_per_step": plan.output_bytes,
                 "path": "nlos_reconstruct_host, pinned host buffers"},

@@ -45,6 +45,8 @@ typedef enum {
 } nlos_status_t;
 
 typedef struct nlos_plan_s* nlos_plan_t;
+typedef struct nlos_batch_s* nlos_batch_t;
+typedef struct nlos_server_s* nlos_server_t;
 
 /*
  * Capture and method description (problem statement of Sec. 3: confocal
@@ -94,6 +96,12 @@ void nlos_plan_desc_default(nlos_plan_desc_t* desc);
  * UNSUPPORTED (pad_factor 1, non-power-of-two sizes), OUT_OF_MEMORY, CUDA.
  */
 nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out);
+
+/* nlos_plan_create with flags. NLOS_PLAN_NO_WORKSPACE: do not allocate the
+ * default workspace (the plan is then used only through nlos_reconstruct_ws,
+ * batches or a server, which provide their own). */
+#define NLOS_PLAN_NO_WORKSPACE 1
+nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_plan_t* out);
 
 /*
  * Shape and byte counts of a plan: out_shape = {nx, ny, nz}; workspace_bytes
@@ -154,6 +162,89 @@ nlos_status_t nlos_reconstruct_batch(const nlos_plan_t* plans, const void* const
  * and must be serialised by the caller. Asynchronous on stream.
  */
 nlos_status_t nlos_reconstruct_noalloc(nlos_plan_t plan, const void* transient, void* volume, void* stream);
+
+/*
+ * Autotune the plan's launch shapes: for every stage with more than one
+ * kernel variant (column tiles of the x/y transforms, pencils per CTA of the
+ * f-k temporal stage) time the whole reconstruction with each variant on a
+ * scratch input (coordinate descent, CUDA events on `stream`) and keep the
+ * fastest. Results are cached per plan shape for the process and, when the
+ * environment variable NLOS_AUTOTUNE_CACHE names a file, in that JSON file
+ * (read on first use, rewritten after tuning). Synchronous; allocates a
+ * scratch transient and volume for the duration of the call. Numerics do not
+ * depend on the variant. Errors: INVALID_ARG (NULL plan, tracing enabled),
+ * OUT_OF_MEMORY, CUDA.
+ */
+nlos_status_t nlos_plan_autotune(nlos_plan_t plan, void* stream);
+
+/* Current variant index of each stage (tiles[i], i < min(capacity, *n_stages)). */
+nlos_status_t nlos_plan_get_tiles(nlos_plan_t plan, int* tiles, int capacity, int* n_stages);
+
+/* Set every stage's variant explicitly (n must equal the stage count; each index in range). */
+nlos_status_t nlos_plan_set_tiles(nlos_plan_t plan, const int* tiles, int n);
+
+/*
+ * Record a batch of n reconstructions into one CUDA graph (the batching of
+ * Sec. 4.1's graph replay, extended to many captures of uneven size): item i
+ * reconstructs transients[i] into volumes[i] (caller-owned device buffers,
+ * fixed for the batch's life) with plans[i]. Items are assigned longest
+ * first to the least-loaded of up to max_streams side streams (0 -> 8) that
+ * fork from and join to the launching stream inside the graph, so independent
+ * captures overlap on the device; each side stream owns one workspace sized
+ * for its largest item (owned by the batch). Creation runs the batch once
+ * eagerly (loading kernels) and then records it; synchronous.
+ * Errors: INVALID_ARG (NULL arrays/items, tracing enabled), OUT_OF_MEMORY, CUDA.
+ */
+nlos_status_t nlos_batch_create(const nlos_plan_t* plans, const void* const* transients, void* const* volumes,
+                                int n, int max_streams, nlos_batch_t* out);
+
+/* Launch the recorded graph on stream (asynchronous); reads the batch's inputs, writes its outputs. */
+nlos_status_t nlos_batch_launch(nlos_batch_t batch, void* stream);
+
+/* Release the graph, its streams and workspaces (synchronises the device). */
+nlos_status_t nlos_batch_destroy(nlos_batch_t batch);
+
+/*
+ * Continuous-batching server (Sec. 4.1's producer-consumer front end, served
+ * from many clients). Requests of any description are queued by any thread
+ * and served by one scheduler thread: plans are created once per distinct
+ * description and stay resident; a request is admitted in arrival order as
+ * soon as one of n_slots streams is free and its workspace (the padded
+ * volume's footprint) fits in memory_budget_bytes next to the requests
+ * already running; admitted requests overlap on the device. Workspaces come
+ * from the stream-ordered allocator. Each result equals that of a standalone
+ * nlos_reconstruct with the same description.
+ * Errors: INVALID_ARG (budget 0, slots outside [1, 64]), CUDA.
+ */
+nlos_status_t nlos_server_create(size_t memory_budget_bytes, int n_slots, nlos_server_t* out);
+
+/* Create (and keep) the plan for desc ahead of the first request. Synchronous. */
+nlos_status_t nlos_server_preload(nlos_server_t server, const nlos_plan_desc_t* desc);
+
+/*
+ * Queue one request: transient/volume are caller-owned device buffers (input
+ * ready when this is called, output valid once nlos_server_wait returns).
+ * Creates the plan if the description is new (synchronous, stalls the
+ * device). *ticket identifies the request. Errors: INVALID_ARG (NULL
+ * arguments, invalid description), OUT_OF_MEMORY (workspace larger than the
+ * whole budget), UNSUPPORTED, CUDA.
+ */
+nlos_status_t nlos_server_submit(nlos_server_t server, const nlos_plan_desc_t* desc, const void* transient,
+                                 void* volume, uint64_t* ticket);
+
+/*
+ * Block until the request finished (or timeout_s elapsed, <= 0: one hour);
+ * returns its latency (submission to observed completion) and forgets the
+ * ticket. Errors: INVALID_ARG (unknown ticket), TIMEOUT, CUDA.
+ */
+nlos_status_t nlos_server_wait(nlos_server_t server, uint64_t ticket, double timeout_s, double* latency_ms);
+
+/* Latency percentiles and throughput of the completed requests (optionally reset). */
+nlos_status_t nlos_server_stats(nlos_server_t server, double* p50_ms, double* p99_ms, double* volumes_per_s,
+                                unsigned long long* completed, int reset);
+
+/* Finish queued work, stop the scheduler, release plans and streams. */
+nlos_status_t nlos_server_destroy(nlos_server_t server);
 
 /*
  * Stage tracing. While enabled, every reconstruction with this plan records a

@@ -54,6 +54,10 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     """Compile csrc/*.cu for sm_103a and link libnlos_gb300.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = _sources()
+    keep = {os.path.basename(x)[:-3] + ".o" for x in srcs}
+    for stale in glob.glob(os.path.join(BUILD, "*.o")):
+        if os.path.basename(stale) not in keep:
+            os.remove(stale)
     hdr_time = _newest(_headers())
     flags = CFLAGS + list(extra_flags or [])
     jobs = []

@@ -15,16 +15,27 @@ template <> struct RealOf<float2> { using T = float; };
 template <> struct RealOf<__half2> { using T = __half; };
 template <> struct RealOf<__nv_bfloat162> { using T = __nv_bfloat16; };
 
-template <int L> struct AxisTile {
-  static constexpr int IC = L <= 64 ? 32 : (L <= 256 ? 16 : (L <= 1024 ? 8 : 4));
+// Column-tile variants per length (selected by AxisLaunch::tile; index 0 is
+// the default, the autotuner may pick another).
+__host__ __device__ constexpr int axis_ic(int L, int v) {
+  return L <= 32 ? (v == 0 ? 32 : 64)
+       : L <= 64 ? (v == 0 ? 32 : 16)
+       : L <= 256 ? (v == 0 ? 16 : (v == 1 ? 8 : 32))
+       : L <= 512 ? (v == 0 ? 8 : (v == 1 ? 4 : 16))
+       : L <= 1024 ? (v == 0 ? 8 : 4)
+       : (v == 0 ? 4 : 2);
+}
+
+template <int L, int IC_> struct AxisTile {
+  static constexpr int IC = IC_;
   static constexpr int THREADS = IC * (L / 16);
   static constexpr size_t SMEM = (L > 16) ? sizeof(float2) * FftShape<L>::SMEM * IC : 0;
 };
 
-template <int L, int LD, int ST, class TS>
+template <int L, int IC_, int LD, int ST, class TS>
 struct AxisCtx {
   using TR = typename RealOf<TS>::T;
-  static constexpr int IC = AxisTile<L>::IC;
+  static constexpr int IC = IC_;
   static constexpr int SSTRIDE = IC;
   const void* in;
   void* out;
@@ -63,12 +74,11 @@ struct AxisCtx {
   }
 };
 
-template <int L, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
-__global__ void __launch_bounds__(AxisTile<L>::THREADS)
+template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
+__global__ void __launch_bounds__(AxisTile<L, IC>::THREADS)
 axis_fft_kernel(const AxisParams p) {
   extern __shared__ float2 axis_sm[];
-  constexpr int IC = AxisTile<L>::IC;
-  AxisCtx<L, LD, ST, TS> ctx;
+  AxisCtx<L, IC, LD, ST, TS> ctx;
   const int c = threadIdx.x % IC;
   const int j0 = threadIdx.x / IC;
   const long long ii = (long long)blockIdx.x * IC + c;
@@ -93,10 +103,10 @@ axis_fft_kernel(const AxisParams p) {
   fftn_run<L, 1, kHalfIn, kHalfOut>(ctx, j0);
 }
 
-template <int L, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
-cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
-  using Tile = AxisTile<L>;
-  auto k = axis_fft_kernel<L, LD, ST, TS, kHalfIn, kHalfOut>;
+template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
+cudaError_t launch_axis_ic(const AxisLaunch& l, cudaStream_t s) {
+  using Tile = AxisTile<L, IC>;
+  auto k = axis_fft_kernel<L, IC, LD, ST, TS, kHalfIn, kHalfOut>;
   if (Tile::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Tile::SMEM);
     if (e != cudaSuccess) return e;
@@ -106,17 +116,31 @@ cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int L, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
+cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
+  const int v = (l.tile >= 0 && l.tile < axis_tile_count(L)) ? l.tile : 0;
+  if (v == 0) return launch_axis_ic<L, axis_ic(L, 0), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+  if (v == 1) return launch_axis_ic<L, axis_ic(L, 1), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+  return launch_axis_ic<L, axis_ic(L, 2), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+}
+
+// AXIS_SMALL / AXIS_LARGE select the length range a translation unit
+// instantiates (lengths <= 256 and >= 512), so the builds run in parallel.
 template <int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_len(const AxisLaunch& l, cudaStream_t s) {
   switch (l.L) {
+#if defined(AXIS_SMALL)
     case 16: return launch_axis_one<16, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 32: return launch_axis_one<32, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 64: return launch_axis_one<64, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 128: return launch_axis_one<128, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 256: return launch_axis_one<256, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+#endif
+#if defined(AXIS_LARGE)
     case 512: return launch_axis_one<512, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 1024: return launch_axis_one<1024, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 2048: return launch_axis_one<2048, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+#endif
     default: return cudaErrorInvalidValue;
   }
 }

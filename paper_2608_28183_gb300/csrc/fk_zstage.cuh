@@ -17,6 +17,7 @@
 // into (hi, lo) floats, m^2 is exact, and the square root gets one Newton
 // correction from an exact FMA residual. Plain float would put the
 // interpolation weight off by up to 6e-5 near m ~ 1000.
+#pragma once
 #include "nlos_fft.cuh"
 #include "nlos_internal.h"
 
@@ -119,17 +120,24 @@ struct FkInvCtx {
   }
 };
 
-template <int L> struct FkTile {
-  static constexpr int PPC = L <= 256 ? 8 : (L <= 1024 ? 4 : 2);   // pencils per CTA
+// pencils-per-CTA variants per length (index 0 is the default)
+__host__ __device__ constexpr int fk_ppc(int L, int v) {
+  return L <= 128 ? (v == 0 ? 16 : 32)
+       : L <= 256 ? (v == 0 ? 8 : 16)
+       : L <= 512 ? (v == 0 ? 4 : 8)
+       : (L <= 1024 ? (v == 0 ? 4 : 2) : (v == 0 ? 2 : 1));
+}
+
+template <int L, int PPC_> struct FkTile {
+  static constexpr int PPC = PPC_;   // pencils per CTA
   static constexpr int THREADS = PPC * (L / 16);
   static constexpr size_t SMEM = sizeof(float2) * 3 * PPC * FftShape<L>::SMEM;
 };
 
-template <int L, class TS>
-__global__ void __launch_bounds__(FkTile<L>::THREADS)
+template <int L, int PPC, class TS>
+__global__ void __launch_bounds__(FkTile<L, PPC>::THREADS)
 fk_zstage_kernel(const FkZParams p) {
   using S = FftShape<L>;
-  constexpr int PPC = FkTile<L>::PPC;
   extern __shared__ float2 fk_sm[];
   const int w = threadIdx.x / S::TPC;
   const int j0 = threadIdx.x % S::TPC;
@@ -162,10 +170,10 @@ fk_zstage_kernel(const FkZParams p) {
   fftn_run<L, 2, true, true>(ctx, j0);
 }
 
-template <int L, class TS>
-static cudaError_t launch_fk_one(const FkZParams& p, cudaStream_t s) {
-  using T = FkTile<L>;
-  auto k = fk_zstage_kernel<L, TS>;
+template <int L, int PPC, class TS>
+cudaError_t launch_fk_ppc(const FkZParams& p, cudaStream_t s) {
+  using T = FkTile<L, PPC>;
+  auto k = fk_zstage_kernel<L, PPC, TS>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -175,27 +183,24 @@ static cudaError_t launch_fk_one(const FkZParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <class TS>
-static cudaError_t launch_fk_typed(const FkZParams& p, cudaStream_t s) {
-  switch (2 * p.n) {
-    case 32: return launch_fk_one<32, TS>(p, s);
-    case 64: return launch_fk_one<64, TS>(p, s);
-    case 128: return launch_fk_one<128, TS>(p, s);
-    case 256: return launch_fk_one<256, TS>(p, s);
-    case 512: return launch_fk_one<512, TS>(p, s);
-    case 1024: return launch_fk_one<1024, TS>(p, s);
-    case 2048: return launch_fk_one<2048, TS>(p, s);
-    case 4096: return launch_fk_one<4096, TS>(p, s);
-    default: return cudaErrorInvalidValue;
-  }
+template <int L, class TS>
+cudaError_t launch_fk_one(const FkZParams& p, int tile, cudaStream_t s) {
+  if (tile == 1) return launch_fk_ppc<L, fk_ppc(L, 1), TS>(p, s);
+  return launch_fk_ppc<L, fk_ppc(L, 0), TS>(p, s);
 }
 
-cudaError_t launch_fk_zstage(const FkZParams& p, int storage, cudaStream_t s) {
+template <class TS>
+cudaError_t launch_fk_typed(const FkZParams& p, int tile, cudaStream_t s) {
   if (p.npencils <= 0) return cudaErrorInvalidValue;
-  switch (storage) {
-    case kF32: return launch_fk_typed<float2>(p, s);
-    case kF16: return launch_fk_typed<__half2>(p, s);
-    case kBF16: return launch_fk_typed<__nv_bfloat162>(p, s);
+  switch (2 * p.n) {
+    case 32: return launch_fk_one<32, TS>(p, tile, s);
+    case 64: return launch_fk_one<64, TS>(p, tile, s);
+    case 128: return launch_fk_one<128, TS>(p, tile, s);
+    case 256: return launch_fk_one<256, TS>(p, tile, s);
+    case 512: return launch_fk_one<512, TS>(p, tile, s);
+    case 1024: return launch_fk_one<1024, TS>(p, tile, s);
+    case 2048: return launch_fk_one<2048, TS>(p, tile, s);
+    case 4096: return launch_fk_one<4096, TS>(p, tile, s);
     default: return cudaErrorInvalidValue;
   }
 }

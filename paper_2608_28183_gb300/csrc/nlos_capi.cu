@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -16,15 +17,31 @@
 #include "nlos_internal.h"
 
 namespace nlos {
-cudaError_t launch_axis_fft_f32(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_axis_fft_f16(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_axis_fft_bf16(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f32_small(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f32_large(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f16_small(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f16_large(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_bf16_small(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_bf16_large(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_fk_zstage_f32(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_f16(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_bf16(const FkZParams& p, int tile, cudaStream_t s);
 
 cudaError_t launch_axis_fft(const AxisLaunch& l, cudaStream_t s) {
+  const bool small = l.L <= 256;
   switch (l.storage) {
-    case kF32: return launch_axis_fft_f32(l, s);
-    case kF16: return launch_axis_fft_f16(l, s);
-    case kBF16: return launch_axis_fft_bf16(l, s);
+    case kF32: return small ? launch_axis_fft_f32_small(l, s) : launch_axis_fft_f32_large(l, s);
+    case kF16: return small ? launch_axis_fft_f16_small(l, s) : launch_axis_fft_f16_large(l, s);
+    case kBF16: return small ? launch_axis_fft_bf16_small(l, s) : launch_axis_fft_bf16_large(l, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s) {
+  switch (storage) {
+    case kF32: return launch_fk_zstage_f32(p, tile, s);
+    case kF16: return launch_fk_zstage_f16(p, tile, s);
+    case kBF16: return launch_fk_zstage_bf16(p, tile, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -110,6 +127,11 @@ struct nlos_plan_s {
   void* d_in = nullptr;
   void* d_out = nullptr;
   std::vector<void*> allocs;
+  // per-stage tile variant (autotuner) and the transform length it applies to
+  std::vector<int> tiles;
+  std::vector<int> stage_len;     // 0: stage has no variants
+  std::vector<int> stage_kind;    // 1: strided-axis transform, 2: f-k temporal stage
+  bool tuned = false;
   // stage tracing
   std::vector<std::string> stage_names;
   bool prof_on = false;
@@ -409,8 +431,9 @@ nlos_status_t mark(nlos_plan_s* p, cudaStream_t s, int stage) {
 
 AxisLaunch axis(int storage, int L, long long n_outer, const void* in, void* out, long long inner,
                 long long in_outer, long long in_axis, long long out_outer, long long out_axis, int L_in,
-                int L_out, int inverse, float scale, const float2* tw) {
+                int L_out, int inverse, float scale, const float2* tw, int tile) {
   AxisLaunch l{};
+  l.tile = tile;
   l.storage = storage;
   l.L = L;
   l.n_outer = n_outer;
@@ -452,7 +475,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   }
   const float g2a = pass_scale(st, 2 * a), g2b = pass_scale(st, 2 * b), g2n = pass_scale(st, 2 * n);
   // FK1: x forward (real input, scaled by t/(n-1), zero-padded to 2a, kx in [0, a])
-  AxisLaunch l = axis(st, 2 * a, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)a + 1, 0, g2a, p->tw[2 * a]);
+  AxisLaunch l = axis(st, 2 * a, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)a + 1, 0, g2a, p->tw[2 * a], p->tiles[sid]);
   l.load_mode = kLoadReal;
   l.p.t_len = (int)n;
   l.p.t_scale = 1.0f / (float)(n - 1);
@@ -460,7 +483,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_CU(launch_axis_fft(l, s), "fk x-forward");
   NLOS_MARK(p, s, sid++);
   // FK1: y forward (zero-padded to 2b)
-  l = axis(st, 2 * b, a + 1, b0, b1, n, b * n, n, 2 * b * n, n, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b]);
+  l = axis(st, 2 * b, a + 1, b0, b1, n, b * n, n, 2 * b * n, n, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
   NLOS_CU(launch_axis_fft(l, s), "fk y-forward");
   NLOS_MARK(p, s, sid++);
   // FK3: t forward + Stolt + inverse along z for both Hermitian partners
@@ -476,10 +499,10 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   z.npencils = (a + 1) * 2 * b;
   z.ld_scale = g2n;
   z.st_scale = g2n;
-  NLOS_CU(launch_fk_zstage(z, st, s), "fk stolt stage");
+  NLOS_CU(launch_fk_zstage(z, st, p->tiles[sid], s), "fk stolt stage");
   NLOS_MARK(p, s, sid++);
   // FK4: y inverse (keep y < b)
-  l = axis(st, 2 * b, 2 * a, b2, b0, n, 2 * b * n, n, b * n, n, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b]);
+  l = axis(st, 2 * b, 2 * a, b2, b0, n, 2 * b * n, n, b * n, n, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b], p->tiles[sid]);
   NLOS_CU(launch_axis_fft(l, s), "fk y-inverse");
   NLOS_MARK(p, s, sid++);
   // FK4: x inverse (keep x < a), |psi|^2 with the 1/(8abn) normalisation
@@ -487,7 +510,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   // pass scales applied to the data before this last pass (it applies none of its own)
   const double gprod = (double)g2a * g2b * g2n * g2n * g2b;
   const float fscale = (float)(1.0 / (N * N * gprod * gprod));
-  l = axis(st, 2 * a, 1, b0, vol, b * n, 0, b * n, 0, b * n, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a]);
+  l = axis(st, 2 * a, 1, b0, vol, b * n, 0, b * n, 0, b * n, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a], p->tiles[sid]);
   l.store_mode = kStoreAbs2;
   l.p.st_dev_scale = inv_s2;
   NLOS_CU(launch_axis_fft(l, s), "fk x-inverse");
@@ -535,10 +558,10 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_CU(launch_pf_band(bp, st, s), "pf band transform");
   NLOS_MARK(p, s, sid++);
   // PF2: top-left padding and 2D forward transform (y then x) of every band slice
-  AxisLaunch l = axis(st, 2 * b, a, b0, b1, F, b * F, F, 2 * b * F, F, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b]);
+  AxisLaunch l = axis(st, 2 * b, a, b0, b1, F, b * F, F, 2 * b * F, F, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
   NLOS_CU(launch_axis_fft(l, s), "pf y-forward");
   NLOS_MARK(p, s, sid++);
-  l = axis(st, 2 * a, 1, b1, b2, 2 * b * F, 0, 2 * b * F, 0, 2 * b * F, (int)a, 2 * (int)a, 0, g2a, p->tw[2 * a]);
+  l = axis(st, 2 * a, 1, b1, b2, 2 * b * F, 0, 2 * b * F, 0, 2 * b * F, (int)a, 2 * (int)a, 0, g2a, p->tw[2 * a], p->tiles[sid]);
   NLOS_CU(launch_axis_fft(l, s), "pf x-forward");
   NLOS_MARK(p, s, sid++);
   // PF3: depth sum (pixels beyond the cutoff stay zero)
@@ -558,13 +581,13 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_CU(launch_pf_depth(dp, st, p->kr_storage, s), "pf depth sum");
   NLOS_MARK(p, s, sid++);
   // PF4: 2D inverse transform per depth (y then x), crop, |.| with 1/(4ab)
-  l = axis(st, 2 * b, 2 * a, b1, b0, D, 2 * b * D, D, b * D, D, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b]);
+  l = axis(st, 2 * b, 2 * a, b1, b0, D, 2 * b * D, D, b * D, D, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b], p->tiles[sid]);
   NLOS_CU(launch_axis_fft(l, s), "pf y-inverse");
   NLOS_MARK(p, s, sid++);
   // scales the data carries into this last pass (it applies none of its own)
   const double gprod = (double)gn * g2b * g2a * c3_data * g2b;
   const float fscale = (float)(1.0 / (4.0 * a * b * gprod));
-  l = axis(st, 2 * a, 1, b0, vol, b * D, 0, b * D, 0, b * D, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a]);
+  l = axis(st, 2 * a, 1, b0, vol, b * D, 0, b * D, 0, b * D, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a], p->tiles[sid]);
   l.store_mode = kStoreAbs;
   l.p.st_dev_scale = inv_s;
   NLOS_CU(launch_axis_fft(l, s), "pf x-inverse");
@@ -636,6 +659,10 @@ void nlos_plan_desc_default(nlos_plan_desc_t* d) {
 }
 
 nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out) {
+  return nlos_plan_create_ex(desc, 0, out);
+}
+
+nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_plan_t* out) {
   g_err.clear();
   if (!out) return fail(NLOS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -653,9 +680,16 @@ nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out) {
                             "pf_x_inverse"};
   if (desc->method == NLOS_FK) for (const char* nm : fk_names) p->stage_names.push_back(nm);
   else for (const char* nm : pf_names) p->stage_names.push_back(nm);
+  for (const std::string& nm : p->stage_names) {
+    const bool xs = nm.find("_x_") != std::string::npos, ys = nm.find("_y_") != std::string::npos;
+    p->stage_kind.push_back(xs || ys ? 1 : (nm == "fk_stolt_z" ? 2 : 0));
+    p->stage_len.push_back(xs ? 2 * p->a : ys ? 2 * p->b : nm == "fk_stolt_z" ? 2 * p->n : 0);
+  }
+  p->tiles.assign(p->stage_names.size(), 0);
   st = desc->method == NLOS_FK ? build_fk(p) : build_pf(p);
-  if (st == NLOS_OK) st = dalloc(p, &p->ws, p->ws_bytes, "workspace");
-  if (st == NLOS_OK) {
+  const bool own_ws = !(flags & NLOS_PLAN_NO_WORKSPACE);
+  if (st == NLOS_OK && own_ws) st = dalloc(p, &p->ws, p->ws_bytes, "workspace");
+  if (st == NLOS_OK && own_ws) {
     cudaError_t e = cudaMemset(p->ws, 0, p->ws_bytes);
     if (e != cudaSuccess) st = cuda_fail(e, "workspace clear");
   }
@@ -694,12 +728,14 @@ nlos_status_t nlos_reconstruct_ws(nlos_plan_t p, const void* transient, void* vo
 
 nlos_status_t nlos_reconstruct(nlos_plan_t p, const void* transient, void* volume, void* stream) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace; use nlos_reconstruct_ws");
   return nlos_reconstruct_ws(p, transient, volume, p->ws, p->ws_bytes, stream);
 }
 
 nlos_status_t nlos_reconstruct_host(nlos_plan_t p, const void* th, void* vh, void* stream) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
   if (!th || !vh) return fail(NLOS_ERR_INVALID_ARG, "host buffer is NULL");
+  if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace");
   size_t ib = 0, ob = 0;
   nlos_plan_query(p, nullptr, nullptr, &ib, &ob);
   nlos_status_t st;
@@ -720,6 +756,8 @@ nlos_status_t nlos_reconstruct_batch(const nlos_plan_t* plans, const void* const
   if (n == 0) return NLOS_OK;
   for (int i = 0; i < n; ++i) {
     if (!plans[i] || !transients[i] || !volumes[i]) return fail(NLOS_ERR_INVALID_ARG, "batch item %d is NULL", i);
+    if (!workspaces && !plans[i]->ws)
+      return fail(NLOS_ERR_INVALID_ARG, "batch item %d: plan has no workspace and none was given", i);
     if (!workspaces)
       for (int j = 0; j < i; ++j)
         if (plans[j] == plans[i]) return fail(NLOS_ERR_INVALID_ARG, "plan repeated in batch without workspaces");
@@ -741,6 +779,297 @@ nlos_status_t nlos_reconstruct_batch(const nlos_plan_t* plans, const void* const
     NLOS_CU(cudaEventRecord(g_join[k], g_streams[k]), "batch join");
     NLOS_CU(cudaStreamWaitEvent(s, g_join[k], 0), "batch join");
   }
+  return NLOS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: coordinate descent over each stage's tile variants, timing the
+// whole sequence with CUDA events; results cached per plan shape (and in a
+// JSON file named by NLOS_AUTOTUNE_CACHE, if set)
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int>> g_tune_cache;
+bool g_tune_loaded = false;
+
+std::string tune_key(const nlos_plan_s* p) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "m%d_s%d_%dx%dx%d_F%d_D%d", p->d.method, p->storage, p->a, p->b, p->n, p->F, p->D);
+  return buf;
+}
+
+void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char* path = getenv("NLOS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  std::string txt;
+  char buf[4096];
+  size_t k;
+  while ((k = fread(buf, 1, sizeof buf, f)) > 0) txt.append(buf, k);
+  fclose(f);
+  // flat JSON object: {"key": [v, v, ...], ...}
+  size_t i = 0;
+  while ((i = txt.find('"', i)) != std::string::npos) {
+    const size_t e = txt.find('"', i + 1);
+    if (e == std::string::npos) break;
+    const std::string key = txt.substr(i + 1, e - i - 1);
+    const size_t lb = txt.find('[', e), rb = txt.find(']', e);
+    if (lb == std::string::npos || rb == std::string::npos || rb < lb) break;
+    std::vector<int> v;
+    const char* c = txt.c_str() + lb + 1;
+    while (c < txt.c_str() + rb) {
+      char* endp = nullptr;
+      const long x = strtol(c, &endp, 10);
+      if (endp == c) { ++c; continue; }
+      v.push_back((int)x);
+      c = endp;
+    }
+    g_tune_cache[key] = v;
+    i = rb + 1;
+  }
+}
+
+void tune_cache_save() {
+  const char* path = getenv("NLOS_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = fopen(path, "w");
+  if (!f) return;
+  fprintf(f, "{\n");
+  size_t n = 0;
+  for (const auto& kv : g_tune_cache) {
+    fprintf(f, "  \"%s\": [", kv.first.c_str());
+    for (size_t j = 0; j < kv.second.size(); ++j) fprintf(f, "%s%d", j ? ", " : "", kv.second[j]);
+    fprintf(f, "]%s\n", ++n < g_tune_cache.size() ? "," : "");
+  }
+  fprintf(f, "}\n");
+  fclose(f);
+}
+
+int stage_variants(const nlos_plan_s* p, size_t i) {
+  if (p->stage_kind[i] == 1) return axis_tile_count(p->stage_len[i]);
+  if (p->stage_kind[i] == 2) return fk_tile_count(p->stage_len[i]);
+  return 1;
+}
+}  // namespace
+
+extern "C" {
+
+nlos_status_t nlos_plan_autotune(nlos_plan_t p, void* stream) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (p->prof_on) return fail(NLOS_ERR_INVALID_ARG, "disable stage tracing before autotuning");
+  const std::string key = tune_key(p);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_cache_load();
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end() && it->second.size() == p->tiles.size()) {
+      p->tiles = it->second;
+      p->tuned = true;
+      return NLOS_OK;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  size_t ib = 0, ob = 0;
+  nlos_plan_query(p, nullptr, nullptr, &ib, &ob);
+  void *din = nullptr, *dout = nullptr, *tws = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&din, ib);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, ob);
+  if (e == cudaSuccess && !p->ws) e = cudaMalloc(&tws, p->ws_bytes);
+  void* ws = p->ws ? p->ws : tws;
+  if (e == cudaSuccess) e = cudaMemsetAsync(din, 0, ib, s);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  nlos_status_t st = e == cudaSuccess ? NLOS_OK : cuda_fail(e, "autotune buffers");
+  auto time_seq = [&](float* ms) -> nlos_status_t {
+    nlos_status_t r = run_plan(p, din, dout, ws, s);
+    if (r != NLOS_OK) return r;
+    NLOS_CU(cudaEventRecord(e0, s), "autotune timing");
+    for (int k = 0; k < 3; ++k) {
+      r = run_plan(p, din, dout, ws, s);
+      if (r != NLOS_OK) return r;
+    }
+    NLOS_CU(cudaEventRecord(e1, s), "autotune timing");
+    NLOS_CU(cudaEventSynchronize(e1), "autotune timing");
+    NLOS_CU(cudaEventElapsedTime(ms, e0, e1), "autotune timing");
+    return NLOS_OK;
+  };
+  for (size_t i = 0; st == NLOS_OK && i < p->tiles.size(); ++i) {
+    const int nv = stage_variants(p, i);
+    if (nv < 2) continue;
+    int best = p->tiles[i];
+    float best_ms = 1e30f;
+    for (int v = 0; v < nv && st == NLOS_OK; ++v) {
+      p->tiles[i] = v;
+      float ms = 0.f;
+      st = time_seq(&ms);
+      if (st == NLOS_OK && ms < best_ms) {
+        best_ms = ms;
+        best = v;
+      }
+    }
+    p->tiles[i] = best;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(s);
+  if (din) cudaFree(din);
+  if (dout) cudaFree(dout);
+  if (tws) cudaFree(tws);
+  if (st != NLOS_OK) return st;
+  p->tuned = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = p->tiles;
+  tune_cache_save();
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_plan_get_tiles(nlos_plan_t p, int* tiles, int capacity, int* n_stages) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (n_stages) *n_stages = (int)p->tiles.size();
+  for (int i = 0; tiles && i < capacity && i < (int)p->tiles.size(); ++i) tiles[i] = p->tiles[i];
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_plan_set_tiles(nlos_plan_t p, const int* tiles, int n) {
+  if (!p || !tiles || n != (int)p->tiles.size()) return fail(NLOS_ERR_INVALID_ARG, "bad tile vector");
+  for (int i = 0; i < n; ++i)
+    if (tiles[i] < 0 || tiles[i] >= stage_variants(p, i)) return fail(NLOS_ERR_INVALID_ARG, "tile %d out of range", i);
+  for (int i = 0; i < n; ++i) p->tiles[i] = tiles[i];
+  return NLOS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// graph batches: many captures recorded once into a CUDA graph, items
+// spread over side streams (longest first, onto the least-loaded stream) so
+// independent captures overlap; one workspace per side stream
+// ---------------------------------------------------------------------------
+struct nlos_batch_s {
+  int n = 0;
+  std::vector<void*> ws;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> stream_of;
+};
+
+namespace {
+void batch_free(nlos_batch_s* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaStream_t t : b->side) cudaStreamDestroy(t);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (void* w : b->ws) cudaFree(w);
+  delete b;
+}
+}  // namespace
+
+extern "C" {
+
+nlos_status_t nlos_batch_create(const nlos_plan_t* plans, const void* const* transients, void* const* volumes, int n,
+                                int max_streams, nlos_batch_t* out) {
+  if (!out) return fail(NLOS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n <= 0 || !plans || !transients || !volumes) return fail(NLOS_ERR_INVALID_ARG, "bad batch arrays");
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !transients[i] || !volumes[i]) return fail(NLOS_ERR_INVALID_ARG, "batch item %d is NULL", i);
+    if (plans[i]->prof_on) return fail(NLOS_ERR_INVALID_ARG, "disable stage tracing before recording a batch");
+  }
+  const int ns = std::max(1, std::min(n, max_streams > 0 ? max_streams : kBatchStreams));
+  nlos_batch_s* b = new nlos_batch_s();
+  b->n = n;
+  // longest-processing-time-first assignment by workspace size (a proxy for the padded volume)
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int u, int v) { return plans[u]->ws_bytes > plans[v]->ws_bytes; });
+  std::vector<double> load(ns, 0.0);
+  std::vector<size_t> need(ns, 0);
+  b->stream_of.assign(n, 0);
+  for (int i : order) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->stream_of[i] = k;
+    load[k] += (double)plans[i]->ws_bytes;
+    need[k] = std::max(need[k], plans[i]->ws_bytes);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; k < ns && e == cudaSuccess; ++k) {
+    cudaStream_t t;
+    cudaEvent_t ev;
+    void* w = nullptr;
+    e = cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking);
+    if (e != cudaSuccess) break;
+    b->side.push_back(t);
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) break;
+    b->join.push_back(ev);
+    e = cudaMalloc(&w, std::max<size_t>(need[k], 256));
+    if (e != cudaSuccess) break;
+    b->ws.push_back(w);
+  }
+  if (e != cudaSuccess) {
+    nlos_status_t r = cuda_fail(e, "batch resources");
+    batch_free(b);
+    return r;
+  }
+  // one eager pass loads every kernel and sets attributes outside the capture
+  nlos_status_t st = NLOS_OK;
+  for (int i = 0; i < n && st == NLOS_OK; ++i)
+    st = run_plan(plans[i], transients[i], volumes[i], b->ws[b->stream_of[i]], b->cap);
+  if (st == NLOS_OK) {
+    e = cudaStreamSynchronize(b->cap);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch warm-up");
+  }
+  if (st == NLOS_OK) {
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch capture");
+  }
+  if (st == NLOS_OK) {
+    bool ok = cudaEventRecord(b->fork, b->cap) == cudaSuccess;
+    for (int k = 0; ok && k < ns; ++k) ok = cudaStreamWaitEvent(b->side[k], b->fork, 0) == cudaSuccess;
+    for (int i = 0; ok && i < n; ++i)
+      ok = run_plan(plans[i], transients[i], volumes[i], b->ws[b->stream_of[i]], b->side[b->stream_of[i]]) == NLOS_OK;
+    for (int k = 0; ok && k < ns; ++k) {
+      ok = cudaEventRecord(b->join[k], b->side[k]) == cudaSuccess;
+      if (ok) ok = cudaStreamWaitEvent(b->cap, b->join[k], 0) == cudaSuccess;
+    }
+    e = cudaStreamEndCapture(b->cap, &b->graph);
+    if (!ok || e != cudaSuccess) st = fail(NLOS_ERR_CUDA, "batch capture failed: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  if (st == NLOS_OK) {
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) st = cuda_fail(e, "batch graph instantiate");
+  }
+  if (st != NLOS_OK) {
+    batch_free(b);
+    return st;
+  }
+  *out = b;
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_batch_launch(nlos_batch_t b, void* stream) {
+  if (!b) return fail(NLOS_ERR_INVALID_ARG, "batch is NULL");
+  NLOS_CU(cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)), "batch launch");
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_batch_destroy(nlos_batch_t b) {
+  if (!b) return fail(NLOS_ERR_INVALID_ARG, "batch is NULL");
+  cudaDeviceSynchronize();
+  batch_free(b);
   return NLOS_OK;
 }
 
@@ -802,4 +1131,5 @@ nlos_status_t plan_run(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaS
   return run_plan(p, H, vol, ws, s);
 }
 nlos_status_t set_error(nlos_status_t st, const char* msg) { return fail(st, "%s", msg); }
+const nlos_plan_desc_t* plan_desc(const nlos_plan_s* p) { return &p->d; }
 }  // namespace nlos

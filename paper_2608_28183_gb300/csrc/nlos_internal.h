@@ -36,6 +36,7 @@ struct AxisParams {
 
 struct AxisLaunch {
   AxisParams p;
+  int tile;                    // column-tile variant (0 = default)
   int L;
   long long n_outer;
   int storage;                 // element type of complex arrays (and of real input)
@@ -43,6 +44,10 @@ struct AxisLaunch {
   int store_mode;              // AxisStore
 };
 cudaError_t launch_axis_fft(const AxisLaunch& l, cudaStream_t s);
+// number of column-tile variants of the axis transform of length L
+__host__ __device__ constexpr int axis_tile_count(int L) { return (L >= 128 && L <= 512) ? 3 : 2; }
+// number of pencils-per-CTA variants of the f-k temporal stage of length L = 2n
+__host__ __device__ constexpr int fk_tile_count(int L) { return 2; }
 
 // f-k temporal-frequency stage: forward length-2n FFT of each stored pencil
 // G[kx][ky][0..n) (kx in [0, a], ky in [0, 2b)), Stolt resampling with the
@@ -61,7 +66,7 @@ struct FkZParams {
   const float* ld_dev_scale;   // optional device scalar multiplying forward loads
   float st_scale;              // multiplies stored values
 };
-cudaError_t launch_fk_zstage(const FkZParams& p, int storage, cudaStream_t s);
+cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s);
 
 // Phasor-field temporal band transform: per wall pencil H[x][y][0..n) (real),
 // length-n DFT, keep bins k_lo..k_lo+F-1, multiply by w(f): P[x][y][f].

@@ -23,7 +23,11 @@ STORAGES = {"f32": NLOS_F32, "f16": NLOS_F16, "bf16": NLOS_BF16}
 EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nlos_reconstruct",
             "nlos_reconstruct_ws", "nlos_reconstruct_host", "nlos_reconstruct_batch",
             "nlos_plan_set_profiling", "nlos_plan_stage_times", "nlos_plan_stage_name",
-            "nlos_plan_destroy", "nlos_last_error", "nlos_version", "nlos_reconstruct_noalloc"]
+            "nlos_plan_destroy", "nlos_last_error", "nlos_version", "nlos_reconstruct_noalloc",
+            "nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles",
+            "nlos_batch_create", "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex",
+            "nlos_server_create", "nlos_server_preload", "nlos_server_submit", "nlos_server_wait",
+            "nlos_server_stats", "nlos_server_destroy"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -71,6 +75,26 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_plan_destroy.argtypes = [vp]
     lib.nlos_reconstruct_noalloc.argtypes = [vp, vp, vp, vp]
     lib.nlos_reconstruct_noalloc.restype = ctypes.c_int
+    lib.nlos_plan_autotune.argtypes = [vp, vp]
+    lib.nlos_plan_get_tiles.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.nlos_plan_set_tiles.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    lib.nlos_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int,
+                                      ctypes.c_int, ctypes.POINTER(vp)]
+    lib.nlos_batch_launch.argtypes = [vp, vp]
+    lib.nlos_batch_destroy.argtypes = [vp]
+    lib.nlos_plan_create_ex.argtypes = [ctypes.POINTER(PlanDesc), ctypes.c_int, ctypes.POINTER(vp)]
+    lib.nlos_server_create.argtypes = [sz, ctypes.c_int, ctypes.POINTER(vp)]
+    lib.nlos_server_preload.argtypes = [vp, ctypes.POINTER(PlanDesc)]
+    lib.nlos_server_submit.argtypes = [vp, ctypes.POINTER(PlanDesc), vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.nlos_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.nlos_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
+    lib.nlos_server_destroy.argtypes = [vp]
+    for name in ("nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles", "nlos_batch_create",
+                 "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex", "nlos_server_create",
+                 "nlos_server_preload", "nlos_server_submit", "nlos_server_wait", "nlos_server_stats",
+                 "nlos_server_destroy"):
+        getattr(lib, name).restype = ctypes.c_int
     lib.nlos_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.nlos_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
@@ -109,25 +133,32 @@ class Geometry:
     wall_h_m: float
 
 
+def make_desc(nx: int, ny: int, nt: int, bin_width_s: float, wall_w_m: float, wall_h_m: float,
+              method: str = "fk", storage: str = "f32", pad_factor: int = 2, *,
+              n_depths: int = 0, depth_min_m: float = 0.0, depth_max_m: float = 0.0,
+              wavelength_m: float = 0.0, cycles: float = 5.0, sigma_s: int = 0, sigma_t: int = 0,
+              delta_m: float = 0.0) -> PlanDesc:
+    lib = load_library()
+    d = PlanDesc()
+    lib.nlos_plan_desc_default(ctypes.byref(d))
+    d.nx, d.ny, d.nt = nx, ny, nt
+    d.bin_width_s, d.wall_w_m, d.wall_h_m = bin_width_s, wall_w_m, wall_h_m
+    d.method = METHODS[method]
+    d.storage = STORAGES[storage]
+    d.pad_factor = pad_factor
+    d.wavelength_m, d.cycles = wavelength_m, cycles
+    d.n_depths, d.depth_min_m, d.depth_max_m = n_depths, depth_min_m, depth_max_m
+    d.sigma_s, d.sigma_t, d.delta_m = sigma_s, sigma_t, delta_m
+    return d
+
+
 class Plan:
     """A reconstruction plan (owns device tables and a default workspace)."""
 
     def __init__(self, nx: int, ny: int, nt: int, bin_width_s: float, wall_w_m: float, wall_h_m: float,
-                 method: str = "fk", storage: str = "f32", pad_factor: int = 2, *,
-                 n_depths: int = 0, depth_min_m: float = 0.0, depth_max_m: float = 0.0,
-                 wavelength_m: float = 0.0, cycles: float = 5.0, sigma_s: int = 0, sigma_t: int = 0,
-                 delta_m: float = 0.0):
+                 method: str = "fk", storage: str = "f32", pad_factor: int = 2, **kw):
         lib = load_library()
-        d = PlanDesc()
-        lib.nlos_plan_desc_default(ctypes.byref(d))
-        d.nx, d.ny, d.nt = nx, ny, nt
-        d.bin_width_s, d.wall_w_m, d.wall_h_m = bin_width_s, wall_w_m, wall_h_m
-        d.method = METHODS[method]
-        d.storage = STORAGES[storage]
-        d.pad_factor = pad_factor
-        d.wavelength_m, d.cycles = wavelength_m, cycles
-        d.n_depths, d.depth_min_m, d.depth_max_m = n_depths, depth_min_m, depth_max_m
-        d.sigma_s, d.sigma_t, d.delta_m = sigma_s, sigma_t, delta_m
+        d = make_desc(nx, ny, nt, bin_width_s, wall_w_m, wall_h_m, method, storage, pad_factor, **kw)
         self.desc = d
         self.method = method
         self.storage = storage
@@ -201,6 +232,23 @@ class Plan:
         names = [_lib.nlos_plan_stage_name(self._h, i).decode() for i in range(ns.value)]
         return {nm: times[i] for i, nm in enumerate(names)}, calls.value
 
+    def autotune(self, stream=None):
+        """Pick each stage's fastest launch shape (cached per plan shape)."""
+        _check(_lib.nlos_plan_autotune(self._h, _stream_ptr(stream)))
+        return self.tiles
+
+    @property
+    def tiles(self):
+        buf = (ctypes.c_int * 16)()
+        n = ctypes.c_int()
+        _check(_lib.nlos_plan_get_tiles(self._h, buf, 16, ctypes.byref(n)))
+        return [buf[i] for i in range(n.value)]
+
+    @tiles.setter
+    def tiles(self, values):
+        arr = (ctypes.c_int * len(values))(*values)
+        _check(_lib.nlos_plan_set_tiles(self._h, arr, len(values)))
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
             _check(_lib.nlos_plan_destroy(self._h))
@@ -224,6 +272,87 @@ def reconstruct_batch(plans, transients, volumes, workspaces=None, stream=None):
     W = None if workspaces is None else (ctypes.c_void_p * n)(*[w.data_ptr() for w in workspaces])
     _check(_lib.nlos_reconstruct_batch(P, T, V, W, n, _stream_ptr(stream)))
     return volumes
+
+
+class Batch:
+    """Many reconstructions recorded once into a CUDA graph and replayed.
+
+    The device buffers given here are the batch's inputs and outputs for its
+    whole life; launch() replays the graph on the current stream."""
+
+    def __init__(self, plans, transients, volumes, max_streams: int = 0):
+        load_library()
+        n = len(plans)
+        for p, t, v in zip(plans, transients, volumes):
+            p._check_io(t, v)
+        self._keep = (list(plans), list(transients), list(volumes))
+        P = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+        T = (ctypes.c_void_p * n)(*[t.data_ptr() for t in transients])
+        V = (ctypes.c_void_p * n)(*[v.data_ptr() for v in volumes])
+        h = ctypes.c_void_p()
+        _check(_lib.nlos_batch_create(P, T, V, n, max_streams, ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.nlos_batch_launch(self._h, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(_lib.nlos_batch_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server: queue requests from any thread, wait for tickets."""
+
+    def __init__(self, memory_budget_bytes: int, n_slots: int = 8):
+        load_library()
+        h = ctypes.c_void_p()
+        _check(_lib.nlos_server_create(ctypes.c_size_t(memory_budget_bytes), n_slots, ctypes.byref(h)))
+        self._h = h
+
+    def preload(self, desc: PlanDesc):
+        _check(_lib.nlos_server_preload(self._h, ctypes.byref(desc)))
+
+    def submit(self, desc: PlanDesc, transient, volume) -> int:
+        t = ctypes.c_uint64()
+        _check(_lib.nlos_server_submit(self._h, ctypes.byref(desc), ctypes.c_void_p(transient.data_ptr()),
+                                       ctypes.c_void_p(volume.data_ptr()), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_s: float = 60.0) -> float:
+        lat = ctypes.c_double()
+        _check(_lib.nlos_server_wait(self._h, ctypes.c_uint64(ticket), timeout_s, ctypes.byref(lat)))
+        return lat.value
+
+    def stats(self, reset: bool = False) -> dict:
+        p50, p99, vps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_ulonglong()
+        _check(_lib.nlos_server_stats(self._h, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(vps),
+                                      ctypes.byref(n), int(reset)))
+        return {"p50_ms": p50.value, "p99_ms": p99.value, "volumes_per_s": vps.value, "completed": n.value}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(_lib.nlos_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def desc_for_capture(geom, method="fk", storage="f32", **kw) -> PlanDesc:
+    return make_desc(geom.nx, geom.ny, geom.nt, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m,
+                     method=method, storage=storage, **kw)
 
 
 def plan_for_capture(geom, method="fk", storage="f32", **kw) -> Plan:
