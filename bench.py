@@ -56,6 +56,26 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def reduce_max(value, dist, device):
+    """Maximum of a per-rank scalar over all ranks (the value itself without a process group)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(world, units_per_rank, max_seconds):
+    """Units processed by all ranks divided by the slowest rank's time."""
+    return world * units_per_rank / max_seconds
+
+
+def capture_index_for(rank, step=0):
+    """Each rank reconstructs its own seeded captures (replicas, no data exchange)."""
+    return rank + 1000 * step
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -336,6 +356,49 @@ def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000), seconds=2.0, b
     return {"budget_gb": budget_gb, "slots": 8, "shapes": len(specs), "sweep": results}
 
 
+def pf_bench(torch, nlos, synth, steps=200, with_oracle=True):
+    """Phasor-field workload: 128 x 128 x 1024 over 2 m, 16 ps, 128 planes
+    0.5-2.5 m (151 band frequencies), FP32 and FP16 storage."""
+    import numpy as np
+    cap = synth.make_capture("pf_128x128x1024", 0, device="cuda")
+    g = cap.geometry
+    out = {"workload": "pf_128x128x1024", "planes": 128}
+    vol32 = None
+    for storage in ("f32", "f16"):
+        plan = nlos.plan_for_capture(g, "pf", storage, n_depths=128, depth_min_m=0.5, depth_max_m=2.5)
+        plan.autotune()
+        x = torch.as_tensor(cap.counts, dtype=torch.float32).to(plan.input_dtype()).cuda()
+        v = plan.empty_volume()
+        for _ in range(5):
+            plan.reconstruct(x, v)
+        plan.set_profiling(True)
+        tot, st = time_plan(plan, x, v, steps, torch)
+        stages, calls = plan.stage_times()
+        plan.set_profiling(False)
+        rec = {"volumes_per_s": steps / (tot / 1e3), "ms_per_volume": tot / steps,
+               "p50_ms": st[len(st) // 2], "p99_ms": st[min(len(st) - 1, int(0.99 * (len(st) - 1) + 0.5))],
+               "stages_ms": {k: val / calls for k, val in stages.items()}}
+        if storage == "f32":
+            vol32 = v.cpu().numpy()
+            band = 151
+            npix = 4 * g.nx * g.ny
+            flops = npix * band * 128 * 12          # per (pixel, f, d): lerp 2 FMA + complex MAC 4 FMA
+            ms = rec["stages_ms"]["pf_depth_sum"]
+            rec["depth_sum_alu"] = {"bound": "alu", "flops": flops, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
+                                    "peak_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
+                                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz max clock"}
+            rec["depth_sum_alu"]["frac"] = rec["depth_sum_alu"]["achieved_tflops"] / rec["depth_sum_alu"]["peak_tflops"]
+        else:
+            rec["rel_l2_vs_f32"] = float(np.linalg.norm(v.cpu().numpy() - vol32) / np.linalg.norm(vol32))
+        out[storage] = rec
+    if with_oracle:
+        from oracle import pf as opf
+        op = opf.make_plan(g.nx, g.ny, g.nt, g.bin_width_s, g.wall_w_m, g.wall_h_m, 128, 0.5, 2.5)
+        ref = opf.pf_reconstruct(np.asarray(torch.as_tensor(cap.counts, dtype=torch.float32).numpy(), dtype=np.float64), op)
+        out["f32"]["rel_l2_vs_oracle"] = rel_l2(vol32, ref)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -402,9 +465,10 @@ def main():
     if args.grid:
         nx, ny, nt = (int(v) for v in args.grid.split(","))
         geom = synth.Geometry(nx, ny, nt, 16e-12, 2.0, 2.0)
-    cap = synth.make_capture(WORKLOAD, rank, device="cuda", geom=geom)
+    cap = synth.make_capture(WORKLOAD, capture_index_for(rank), device="cuda", geom=geom)
     g = cap.geometry
     plan = nlos.plan_for_capture(g, "fk", args.storage)
+    tiles = plan.autotune()                       # the project's launch-shape autotuner (cached per shape)
     H = torch.as_tensor(cap.counts, dtype=torch.float32).to(plan.input_dtype()).cuda().contiguous()
     vol = plan.empty_volume()
     for _ in range(max(3, args.warmup)):
@@ -434,11 +498,8 @@ def main():
     total_ms = t0.elapsed_time(t1)
     step_ms = sorted(s.elapsed_time(e) for s, e in zip(starts, ends))
     stages, calls = plan.stage_times()
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * K / (total_ms / 1e3)
+    total_ms = reduce_max(total_ms, dist, "cuda")
+    value = whole_job_throughput(world, K, total_ms / 1e3)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
     Ke = max(1, min(args.e2e_steps, K))
@@ -450,12 +511,8 @@ def main():
     te = time.perf_counter()
     for _ in range(Ke):
         plan.reconstruct_host(h_in, h_out)
-    e2e_s = time.perf_counter() - te
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = world * Ke / e2e_s
+    e2e_s = reduce_max(time.perf_counter() - te, dist, "cuda")
+    e2e_value = whole_job_throughput(world, Ke, e2e_s)
 
     if rank != 0:
         if dist:
@@ -481,6 +538,7 @@ def main():
     variants = {}
     if args.storage == "f32":
         p16 = nlos.plan_for_capture(g, "fk", "f16")
+        p16.autotune()
         H16 = torch.as_tensor(cap.counts, dtype=torch.float32).to(torch.float16).cuda().contiguous()
         v16 = p16.empty_volume()
         for _ in range(5):
@@ -494,7 +552,8 @@ def main():
 
     extras = {}
     if world == 1 and not args.no_extras and not args.grid:
-        for name, fn in (("batch", batch_bench), ("serving", serving_bench)):
+        for name, fn in (("batch", batch_bench), ("serving", serving_bench),
+                         ("phasor_field", lambda t, n, sy: pf_bench(t, n, sy, with_oracle=not args.no_cpu_baseline))):
             try:
                 extras[name] = fn(torch, nlos, synth)
             except Exception as exc:     # report, do not lose the headline line
@@ -531,12 +590,14 @@ def main():
                               "bytes": pipe_bytes, "achieved": pipe_achieved, "peak": peak, "unit": "GB/s",
                               "frac": pipe_achieved / peak},
         "stages_ms_per_launch": per_launch_ms,
+        "autotuned_tiles": tiles,
         "stage_bytes": sb,
         "cpu_baseline": cpu,
         "parity": parity,
         "variants": variants,
         "batch": extras.get("batch"),
         "serving": extras.get("serving"),
+        "phasor_field": extras.get("phasor_field"),
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": Ke,
                 "h2d_bytes_per_step": plan.input_bytes, "d2h_bytes_per_step": plan.output_bytes,
                 "path": "nlos_reconstruct_host, pinned host buffers"},

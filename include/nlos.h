@@ -247,6 +247,22 @@ nlos_status_t nlos_server_stats(nlos_server_t server, double* p50_ms, double* p9
 nlos_status_t nlos_server_destroy(nlos_server_t server);
 
 /*
+ * Read and clear the device error word of a workspace (NULL: the plan's
+ * default one). Kernels that stage tiles with TMA wait on barriers with an
+ * iteration limit; a wait that runs out records a timeout there and the
+ * kernel returns instead of hanging. Synchronous.
+ * Returns OK (code 0), TIMEOUT (code 1) or CUDA.
+ */
+nlos_status_t nlos_workspace_check(nlos_plan_t plan, const void* workspace, int* code);
+
+/*
+ * Self-test of that bounded wait: one CTA waits at most `limit` polls on a
+ * barrier that nothing arrives on. Returns TIMEOUT with *code = 1 when the
+ * wait gave up as it should (the context stays usable). Synchronous.
+ */
+nlos_status_t nlos_selftest_bounded_wait(int limit, int* code);
+
+/*
  * Stage tracing. While enabled, every reconstruction with this plan records a
  * CUDA event before its first stage and after each stage, on the call's
  * stream (use one stream per plan while profiling).

@@ -5,26 +5,34 @@
 // TPC = L/16 threads each, exchanging through shared memory laid out as
 // [padded row][IC].
 #pragma once
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+
 #include "nlos_fft.cuh"
 #include "nlos_internal.h"
+#include "nlos_tma.cuh"
 
 namespace nlos {
+
+// NLOS_DEBUG=1: print each axis launch's path and CUDA result to stderr
+inline bool axis_debug() {
+  static int on = -1;
+  if (on < 0) on = getenv("NLOS_DEBUG") ? 1 : 0;
+  return on == 1;
+}
+inline cudaError_t axis_report(const char* path, int L, int ic, int threads, size_t smem, long long gx, long long gy,
+                               cudaError_t e) {
+  if (axis_debug())
+    fprintf(stderr, "[nlos axis] %s L=%d IC=%d threads=%d smem=%zu grid=(%lld,%lld) -> %s\n", path, L, ic, threads,
+            smem, gx, gy, cudaGetErrorString(e));
+  return e;
+}
 
 template <class TS> struct RealOf;
 template <> struct RealOf<float2> { using T = float; };
 template <> struct RealOf<__half2> { using T = __half; };
 template <> struct RealOf<__nv_bfloat162> { using T = __nv_bfloat16; };
-
-// Column-tile variants per length (selected by AxisLaunch::tile; index 0 is
-// the default, the autotuner may pick another).
-__host__ __device__ constexpr int axis_ic(int L, int v) {
-  return L <= 32 ? (v == 0 ? 32 : 64)
-       : L <= 64 ? (v == 0 ? 32 : 16)
-       : L <= 256 ? (v == 0 ? 16 : (v == 1 ? 8 : 32))
-       : L <= 512 ? (v == 0 ? 8 : (v == 1 ? 4 : 16))
-       : L <= 1024 ? (v == 0 ? 8 : 4)
-       : (v == 0 ? 4 : 2);
-}
 
 template <int L, int IC_> struct AxisTile {
   static constexpr int IC = IC_;
@@ -37,6 +45,7 @@ struct AxisCtx {
   using TR = typename RealOf<TS>::T;
   static constexpr int IC = IC_;
   static constexpr int SSTRIDE = IC;
+  static constexpr bool kSmemInput = false;
   const void* in;
   void* out;
   const float2* tw;
@@ -74,6 +83,95 @@ struct AxisCtx {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Real input, two columns per transform: the tile covers 2*IC inner columns;
+// column c and column c + IC ride as the real and imaginary parts of one
+// complex transform. The spectrum stays in shared memory, and the two real
+// columns' spectra are split from Z[k] and Z[L-k]:
+//   X_c[k] = (Z[k] + conj Z[L-k]) / 2,  X_{c+IC}[k] = (Z[k] - conj Z[L-k]) / (2i).
+// ---------------------------------------------------------------------------
+template <int L, int IC, class TS>
+struct AxisPairCtx {
+  using TR = typename RealOf<TS>::T;
+  static constexpr int SSTRIDE = IC;
+  static constexpr bool kSmemInput = false;
+  const TR* in;
+  float2* smem;
+  const float2* tw;
+  long long base0, base1, in_axis;
+  int L_in, c;
+  bool v0, v1;
+  float m0, m1;
+  __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
+    x[0] = make_float2(0.f, 0.f);
+    if (l >= L_in) return;
+    if (v0) x[0].x = Real<TR>::get(in + base0 + l * in_axis) * m0;
+    if (v1) x[0].y = Real<TR>::get(in + base1 + l * in_axis) * m1;
+  }
+  __device__ __forceinline__ float2* sm(int) const { return smem + c; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { smem[pad16(l) * IC + c] = x[0]; }
+};
+
+template <int L, int IC, class TS>
+__global__ void __launch_bounds__(AxisTile<L, IC>::THREADS)
+axis_fft_realpair_kernel(const AxisParams p) {
+  extern __shared__ float2 pair_sm[];
+  constexpr int TPC = L / 16;
+  const int c = threadIdx.x % IC;
+  const int j0 = threadIdx.x / IC;
+  const long long ii0 = (long long)blockIdx.x * (2 * IC) + c;
+  const long long ii1 = ii0 + IC;
+  const long long outer = blockIdx.y;
+  const float ldmul = p.ld_dev_scale ? *p.ld_dev_scale : 1.0f;
+  AxisPairCtx<L, IC, TS> ctx;
+  ctx.in = static_cast<const typename RealOf<TS>::T*>(p.in);
+  ctx.smem = pair_sm;
+  ctx.tw = p.tw;
+  ctx.base0 = outer * p.in_outer + ii0;
+  ctx.base1 = outer * p.in_outer + ii1;
+  ctx.in_axis = p.in_axis;
+  ctx.L_in = p.L_in;
+  ctx.c = c;
+  ctx.v0 = ii0 < p.inner;
+  ctx.v1 = ii1 < p.inner;
+  ctx.m0 = ldmul * (p.t_len > 0 ? (float)(int)(ii0 % p.t_len) * p.t_scale : 1.0f);
+  ctx.m1 = ldmul * (p.t_len > 0 ? (float)(int)(ii1 % p.t_len) * p.t_scale : 1.0f);
+  fftn_run<L, 1, true, false>(ctx, j0);
+  __syncthreads();
+  const float h = 0.5f * p.scale * (p.st_dev_scale ? *p.st_dev_scale : 1.0f);
+  TS* out = static_cast<TS*>(p.out);
+  for (int k = j0; k < p.L_out; k += TPC) {
+    const float2 zk = pair_sm[pad16(k) * IC + c];
+    const float2 zm = pair_sm[pad16((L - k) & (L - 1)) * IC + c];
+    if (ctx.v0)
+      Cpx<TS>::put(out + outer * p.out_outer + ii0 + k * p.out_axis, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
+    if (ctx.v1)
+      Cpx<TS>::put(out + outer * p.out_outer + ii1 + k * p.out_axis, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
+  }
+}
+
+template <int L, int IC, class TS>
+cudaError_t launch_axis_pair_ic(const AxisLaunch& l, cudaStream_t s) {
+  using Tile = AxisTile<L, IC>;
+  constexpr size_t smem = sizeof(float2) * FftShape<L>::SMEM * IC;
+  auto k = axis_fft_realpair_kernel<L, IC, TS>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)((l.p.inner + 2 * IC - 1) / (2 * IC)), (unsigned)l.n_outer);
+  k<<<grid, Tile::THREADS, smem, s>>>(l.p);
+  return axis_report("realpair", L, IC, Tile::THREADS, smem, grid.x, grid.y, cudaGetLastError());
+}
+
+template <int L, class TS>
+cudaError_t launch_axis_pair(const AxisLaunch& l, cudaStream_t s) {
+  const int v = (l.tile >= 0 && l.tile < axis_tile_count(L)) ? l.tile % axis_ic_count(L) : 0;
+  if (v == 0) return launch_axis_pair_ic<L, axis_ic(L, 0), TS>(l, s);
+  if (v == 1) return launch_axis_pair_ic<L, axis_ic(L, 1), TS>(l, s);
+  return launch_axis_pair_ic<L, axis_ic(L, 2), TS>(l, s);
+}
+
 template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 __global__ void __launch_bounds__(AxisTile<L, IC>::THREADS)
 axis_fft_kernel(const AxisParams p) {
@@ -103,8 +201,134 @@ axis_fft_kernel(const AxisParams p) {
   fftn_run<L, 1, kHalfIn, kHalfOut>(ctx, j0);
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged variant: persistent CTAs walk the tiles; while one tile is
+// transformed in shared memory, the TMA engine fetches the next one into the
+// other buffer (double buffering on two mbarriers). The first pass reads the
+// dense staged tile; the transform then continues in place in the same buffer.
+// ---------------------------------------------------------------------------
+template <int L, int IC, int LD, int ST, class TS>
+struct AxisTmaCtx : AxisCtx<L, IC, LD, ST, TS> {
+  using Base = AxisCtx<L, IC, LD, ST, TS>;
+  using TR = typename Base::TR;
+  static constexpr bool kSmemInput = true;
+  const void* tile;     // staged tile, [row][IC] of the input element type
+  __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
+    x[0] = make_float2(0.f, 0.f);
+    if (l >= this->L_in) return;
+    if constexpr (LD == kLoadReal) {
+      const float v = Real<TR>::get(static_cast<const TR*>(tile) + l * IC + this->c) * this->ldmul;
+      x[0] = make_float2(v * this->tmul, 0.f);
+    } else {
+      const float2 v = cscale(Cpx<TS>::get(static_cast<const TS*>(tile) + l * IC + this->c), this->ldmul);
+      x[0] = this->inverse ? cconj(v) : v;
+    }
+  }
+};
+
+template <int L, int IC, int LD, class TS> struct AxisTmaTile {
+  using TR = typename RealOf<TS>::T;
+  static constexpr size_t ELEM = LD == kLoadReal ? sizeof(TR) : sizeof(TS);
+  static constexpr size_t BUF = sizeof(float2) * FftShape<L>::SMEM * IC;   // bytes per buffer (multiple of 128)
+  static constexpr size_t SMEM = 2 * BUF + 2 * sizeof(uint64_t);
+  static constexpr int THREADS = IC * (L / 16);
+};
+
+constexpr int kTmaWaitLimit = 1 << 21;   // polls; each may suspend briefly, ~1 s in all
+
+template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
+__global__ void __launch_bounds__(AxisTile<L, IC>::THREADS)
+axis_fft_tma_kernel(const __grid_constant__ CUtensorMap tmap, const AxisParams p, const int tiles_inner,
+                    const long long ntiles, int* err) {
+  using T = AxisTmaTile<L, IC, LD, TS>;
+  extern __shared__ __align__(128) unsigned char tma_sm[];
+  auto buf = [&](int slot) { return reinterpret_cast<float2*>(tma_sm + slot * T::BUF); };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tma_sm + 2 * T::BUF);
+  const int c = threadIdx.x % IC;
+  const int j0 = threadIdx.x / IC;
+  const int rows = p.L_in;
+  const uint32_t tile_bytes = (uint32_t)(rows * IC * T::ELEM);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long tile, int slot) {
+    const int ti = (int)(tile % tiles_inner);
+    const int to = (int)(tile / tiles_inner);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[slot], tile_bytes);
+    for (int r0 = 0; r0 < rows; r0 += 256)
+      tma_load_3d(reinterpret_cast<unsigned char*>(buf(slot)) + (size_t)r0 * IC * T::ELEM, &tmap, &bar[slot],
+                  ti * IC, r0, to);
+  };
+  long long tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  const float ldmul = p.ld_dev_scale ? *p.ld_dev_scale : 1.0f;
+  const float stmul = p.scale * (p.st_dev_scale ? *p.st_dev_scale : 1.0f);
+  for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    const int slot = k & 1;
+    const long long next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) issue(next, slot ^ 1);
+    if (!mbar_wait_bounded(&bar[slot], (k >> 1) & 1, kTmaWaitLimit)) {
+      if (err) atomicExch(err, kDevErrTmaTimeout);
+      return;
+    }
+    const int ti = (int)(tile % tiles_inner);
+    const long long outer = tile / tiles_inner;
+    const long long ii = (long long)ti * IC + c;
+    AxisTmaCtx<L, IC, LD, ST, TS> ctx;
+    ctx.tile = buf(slot);
+    ctx.in = p.in;
+    ctx.out = p.out;
+    ctx.tw = p.tw;
+    ctx.smem = buf(slot);
+    ctx.c = c;
+    ctx.valid = ii < p.inner;
+    ctx.in_base = outer * p.in_outer + ii;
+    ctx.out_base = outer * p.out_outer + ii;
+    ctx.in_axis = p.in_axis;
+    ctx.out_axis = p.out_axis;
+    ctx.L_in = p.L_in;
+    ctx.L_out = p.L_out;
+    ctx.inverse = p.inverse;
+    ctx.t_len = p.t_len;
+    ctx.ldmul = ldmul;
+    ctx.stmul = stmul;
+    ctx.tmul = p.t_len > 0 ? (float)(int)(ii % p.t_len) * p.t_scale : 1.0f;
+    fftn_run<L, 1, kHalfIn, kHalfOut>(ctx, j0);
+    __syncthreads();   // the buffer is free before the next issue into it
+  }
+}
+
+template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
+cudaError_t launch_axis_tma(const AxisLaunch& l, cudaStream_t s) {
+  using T = AxisTmaTile<L, IC, LD, TS>;
+  auto k = axis_fft_tma_kernel<L, IC, LD, ST, TS, kHalfIn, kHalfOut>;
+  static int blocks_per_sm = 0;
+  static int sms = 0;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, T::THREADS, T::SMEM);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int tiles_inner = (int)((l.p.inner + IC - 1) / IC);
+  const long long ntiles = (long long)tiles_inner * l.n_outer;
+  const long long grid = std::min<long long>(ntiles, (long long)sms * blocks_per_sm);
+  k<<<(unsigned)grid, T::THREADS, T::SMEM, s>>>(l.tmap, l.p, tiles_inner, ntiles, l.err);
+  return axis_report("tma", L, IC, T::THREADS, T::SMEM, grid, ntiles, cudaGetLastError());
+}
+
 template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_ic(const AxisLaunch& l, cudaStream_t s) {
+  const bool tma = l.has_tmap && l.tile >= axis_ic_count(L);
+  if (tma) return launch_axis_tma<L, IC, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
   using Tile = AxisTile<L, IC>;
   auto k = axis_fft_kernel<L, IC, LD, ST, TS, kHalfIn, kHalfOut>;
   if (Tile::SMEM > 48 * 1024) {
@@ -113,20 +337,28 @@ cudaError_t launch_axis_ic(const AxisLaunch& l, cudaStream_t s) {
   }
   dim3 grid((unsigned)((l.p.inner + Tile::IC - 1) / Tile::IC), (unsigned)l.n_outer);
   k<<<grid, Tile::THREADS, Tile::SMEM, s>>>(l.p);
-  return cudaGetLastError();
+  return axis_report("direct", L, IC, Tile::THREADS, Tile::SMEM, grid.x, grid.y, cudaGetLastError());
 }
 
 template <int L, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
-  const int v = (l.tile >= 0 && l.tile < axis_tile_count(L)) ? l.tile : 0;
-  if (v == 0) return launch_axis_ic<L, axis_ic(L, 0), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
-  if (v == 1) return launch_axis_ic<L, axis_ic(L, 1), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
-  return launch_axis_ic<L, axis_ic(L, 2), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+  if constexpr (LD == kLoadRealPair) {
+    return launch_axis_pair<L, TS>(l, s);
+  } else {
+    const int v = (l.tile >= 0 && l.tile < axis_tile_count(L)) ? l.tile % axis_ic_count(L) : 0;
+    if (v == 0) return launch_axis_ic<L, axis_ic(L, 0), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    if (v == 1) return launch_axis_ic<L, axis_ic(L, 1), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+    return launch_axis_ic<L, axis_ic(L, 2), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+  }
 }
 
-// AXIS_SMALL / AXIS_LARGE select the length range a translation unit
-// instantiates (lengths <= 256 and >= 512), so the builds run in parallel.
-template <int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
+// Each translation unit instantiates one length range (kAxisSmall: lengths
+// <= 256, kAxisLarge: >= 512) so the builds run in parallel. The range is a
+// template parameter, so the two units' dispatchers are distinct functions
+// (a macro alone would give two different bodies to one symbol).
+constexpr int kAxisSmall = 0, kAxisLarge = 1;
+
+template <int RANGE, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_len(const AxisLaunch& l, cudaStream_t s) {
   switch (l.L) {
 #if defined(AXIS_SMALL)
@@ -141,28 +373,34 @@ cudaError_t launch_axis_len(const AxisLaunch& l, cudaStream_t s) {
     case 1024: return launch_axis_one<1024, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 2048: return launch_axis_one<2048, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
 #endif
-    default: return cudaErrorInvalidValue;
+    default: return axis_report("no-length", l.L, 0, 0, 0, 0, 0, cudaErrorInvalidValue);
   }
 }
 
 // The sequences use five shapes: forward passes read a zero-padded upper half
 // (L_in = L/2) and keep every output, inverse passes read every input and keep
 // the lower half (L_out = L/2); the real-input x pass keeps kx in [0, L/2].
-template <class TS>
+template <class TS, int RANGE>
 cudaError_t launch_axis_typed(const AxisLaunch& l, cudaStream_t s) {
-  if (l.n_outer <= 0 || l.n_outer > 65535 || l.p.inner <= 0) return cudaErrorInvalidValue;
+  if (l.n_outer <= 0 || l.n_outer > 65535 || l.p.inner <= 0)
+    return axis_report("bad-shape", l.L, 0, 0, 0, l.p.inner, l.n_outer, cudaErrorInvalidValue);
   const bool half_in = 2 * l.p.L_in == l.L, half_out = 2 * l.p.L_out <= l.L;
+  if (axis_debug())
+    fprintf(stderr, "[nlos axis] dispatch L=%d load=%d store=%d L_in=%d L_out=%d tile=%d tmap=%d\n", l.L, l.load_mode,
+            l.store_mode, l.p.L_in, l.p.L_out, l.tile, l.has_tmap);
   if (l.load_mode == kLoadReal && l.store_mode == kStoreCpx && half_in && !half_out)
-    return launch_axis_len<kLoadReal, kStoreCpx, TS, true, false>(l, s);
+    return launch_axis_len<RANGE, kLoadReal, kStoreCpx, TS, true, false>(l, s);
+  if (l.load_mode == kLoadRealPair && l.store_mode == kStoreCpx && half_in && 2 * l.p.L_out <= l.L + 2)
+    return launch_axis_len<RANGE, kLoadRealPair, kStoreCpx, TS, true, false>(l, s);
   if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx && half_in && !half_out)
-    return launch_axis_len<kLoadCpx, kStoreCpx, TS, true, false>(l, s);
+    return launch_axis_len<RANGE, kLoadCpx, kStoreCpx, TS, true, false>(l, s);
   if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx && l.p.L_in == l.L && half_out)
-    return launch_axis_len<kLoadCpx, kStoreCpx, TS, false, true>(l, s);
+    return launch_axis_len<RANGE, kLoadCpx, kStoreCpx, TS, false, true>(l, s);
   if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs2 && l.p.L_in == l.L && half_out)
-    return launch_axis_len<kLoadCpx, kStoreAbs2, TS, false, true>(l, s);
+    return launch_axis_len<RANGE, kLoadCpx, kStoreAbs2, TS, false, true>(l, s);
   if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs && l.p.L_in == l.L && half_out)
-    return launch_axis_len<kLoadCpx, kStoreAbs, TS, false, true>(l, s);
-  return cudaErrorInvalidValue;
+    return launch_axis_len<RANGE, kLoadCpx, kStoreAbs, TS, false, true>(l, s);
+  return axis_report("no-variant", l.L, 0, 0, 0, l.load_mode, l.store_mode, cudaErrorInvalidValue);
 }
 
 }  // namespace nlos

@@ -2,5 +2,5 @@
 #define AXIS_SMALL
 #include "axis_fft.cuh"
 namespace nlos {
-cudaError_t launch_axis_fft_bf16_small(const AxisLaunch& l, cudaStream_t s) { return launch_axis_typed<__nv_bfloat162>(l, s); }
+cudaError_t launch_axis_fft_bf16_small(const AxisLaunch& l, cudaStream_t s) { return launch_axis_typed<__nv_bfloat162, kAxisSmall>(l, s); }
 }  // namespace nlos

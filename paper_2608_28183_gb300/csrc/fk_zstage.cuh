@@ -71,6 +71,7 @@ __device__ __forceinline__ StoltCoord stolt_coord(float Ahi, float Alo, int m, i
 template <int L, class TS>
 struct FkFwdCtx {
   static constexpr int SSTRIDE = 1;
+  static constexpr bool kSmemInput = false;
   const TS* g;
   float2* U;
   float2* W;
@@ -89,6 +90,7 @@ struct FkFwdCtx {
 template <int L, class TS>
 struct FkInvCtx {
   static constexpr int SSTRIDE = 1;
+  static constexpr bool kSmemInput = false;
   const float2* U;
   float2* W0;
   float2* W1;
@@ -125,7 +127,7 @@ __host__ __device__ constexpr int fk_ppc(int L, int v) {
   return L <= 128 ? (v == 0 ? 16 : 32)
        : L <= 256 ? (v == 0 ? 8 : 16)
        : L <= 512 ? (v == 0 ? 4 : 8)
-       : (L <= 1024 ? (v == 0 ? 4 : 2) : (v == 0 ? 2 : 1));
+       : (L <= 1024 ? (v == 0 ? 2 : 4) : (v == 0 ? 2 : 1));
 }
 
 template <int L, int PPC_> struct FkTile {

@@ -55,8 +55,9 @@ constexpr double kC = 299792458.0;   // speed of light, m/s
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTaperBins = 8.0;   // smoothstep width below the radial cutoff
 constexpr float kVolumeTarget = 4096.0f;   // ||scaled input||_2 for reduced-precision storage
-constexpr int kScalePartials = 512;
+constexpr int kScalePartials = 2048;
 constexpr int kBatchStreams = 8;
+constexpr size_t kErrOffset = 64;    // device error word inside the workspace's scalar area
 
 thread_local std::string g_err;
 
@@ -429,6 +430,58 @@ nlos_status_t mark(nlos_plan_s* p, cudaStream_t s, int stage) {
     if (m_ != NLOS_OK) return m_;                  \
   } while (0)
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+    else
+      cudaGetLastError();   // do not leave a failed lookup as the thread's pending error
+  }
+  return fn;
+}
+
+// Prepare TMA staging for an axis launch whose variant asks for it: a 3D map
+// (inner, axis rows, outer) over the input with a box of one column tile by
+// min(L_in, 256) rows. Leaves the launch on direct loads when the layout does
+// not meet TMA's 16-byte rules (e.g. an odd number of band frequencies).
+void attach_tmap(AxisLaunch& l) {
+  l.has_tmap = 0;
+  const int nic = axis_ic_count(l.L);
+  if (l.tile < nic) return;
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return;
+  const size_t elem = l.load_mode == kLoadReal ? real_bytes(l.storage) : complex_bytes(l.storage);
+  const int IC = axis_ic(l.L, l.tile % nic);
+  const unsigned long long s1 = (unsigned long long)l.p.in_axis * elem;
+  const unsigned long long s2 =
+      l.n_outer > 1 ? (unsigned long long)l.p.in_outer * elem : (unsigned long long)l.p.L_in * s1;
+  if (s1 % 16 || s2 % 16 || (IC * elem) % 16 || (reinterpret_cast<uintptr_t>(l.p.in) % 16)) return;
+  if (l.p.L_in > 256 && l.p.L_in % 256) return;
+  const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                               : elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  const cuuint64_t dims[3] = {(cuuint64_t)l.p.inner, (cuuint64_t)l.p.L_in, (cuuint64_t)l.n_outer};
+  const cuuint64_t strides[2] = {s1, s2};
+  const cuuint32_t box[3] = {(cuuint32_t)IC, (cuuint32_t)std::min(l.p.L_in, 256), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  if (fn(&l.tmap, dt, 3, const_cast<void*>(l.p.in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+      CUDA_SUCCESS)
+    l.has_tmap = 1;
+}
+
 AxisLaunch axis(int storage, int L, long long n_outer, const void* in, void* out, long long inner,
                 long long in_outer, long long in_axis, long long out_outer, long long out_axis, int L_in,
                 int L_out, int inverse, float scale, const float2* tw, int tile) {
@@ -461,6 +514,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   void* b1 = ws + p->off[1];
   void* b2 = ws + p->off[2];
   float* scal = reinterpret_cast<float*>(ws + p->off_scal);
+  int* err = reinterpret_cast<int*>(ws + p->off_scal + kErrOffset);
   const float* s_in = nullptr;
   const float* inv_s2 = nullptr;
   int sid = 0;
@@ -476,14 +530,20 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   const float g2a = pass_scale(st, 2 * a), g2b = pass_scale(st, 2 * b), g2n = pass_scale(st, 2 * n);
   // FK1: x forward (real input, scaled by t/(n-1), zero-padded to 2a, kx in [0, a])
   AxisLaunch l = axis(st, 2 * a, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)a + 1, 0, g2a, p->tw[2 * a], p->tiles[sid]);
-  l.load_mode = kLoadReal;
+  // direct variants pack two real columns per complex transform; TMA-staged
+  // variants transform each real column on its own
+  l.load_mode = l.tile < axis_ic_count(2 * (int)a) ? kLoadRealPair : kLoadReal;
   l.p.t_len = (int)n;
   l.p.t_scale = 1.0f / (float)(n - 1);
   l.p.ld_dev_scale = s_in;
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk x-forward");
   NLOS_MARK(p, s, sid++);
   // FK1: y forward (zero-padded to 2b)
   l = axis(st, 2 * b, a + 1, b0, b1, n, b * n, n, 2 * b * n, n, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk y-forward");
   NLOS_MARK(p, s, sid++);
   // FK3: t forward + Stolt + inverse along z for both Hermitian partners
@@ -503,6 +563,8 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_MARK(p, s, sid++);
   // FK4: y inverse (keep y < b)
   l = axis(st, 2 * b, 2 * a, b2, b0, n, 2 * b * n, n, b * n, n, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b], p->tiles[sid]);
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk y-inverse");
   NLOS_MARK(p, s, sid++);
   // FK4: x inverse (keep x < a), |psi|^2 with the 1/(8abn) normalisation
@@ -513,6 +575,8 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   l = axis(st, 2 * a, 1, b0, vol, b * n, 0, b * n, 0, b * n, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a], p->tiles[sid]);
   l.store_mode = kStoreAbs2;
   l.p.st_dev_scale = inv_s2;
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk x-inverse");
   NLOS_MARK(p, s, sid++);
   return NLOS_OK;
@@ -525,6 +589,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   void* b1 = ws + p->off[1];
   void* b2 = ws + p->off[2];
   float* scal = reinterpret_cast<float*>(ws + p->off_scal);
+  int* err = reinterpret_cast<int*>(ws + p->off_scal + kErrOffset);
   const float* s_in = nullptr;
   const float* inv_s = nullptr;
   int sid = 0;
@@ -559,9 +624,13 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_MARK(p, s, sid++);
   // PF2: top-left padding and 2D forward transform (y then x) of every band slice
   AxisLaunch l = axis(st, 2 * b, a, b0, b1, F, b * F, F, 2 * b * F, F, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf y-forward");
   NLOS_MARK(p, s, sid++);
   l = axis(st, 2 * a, 1, b1, b2, 2 * b * F, 0, 2 * b * F, 0, 2 * b * F, (int)a, 2 * (int)a, 0, g2a, p->tw[2 * a], p->tiles[sid]);
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf x-forward");
   NLOS_MARK(p, s, sid++);
   // PF3: depth sum (pixels beyond the cutoff stay zero)
@@ -582,6 +651,8 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_MARK(p, s, sid++);
   // PF4: 2D inverse transform per depth (y then x), crop, |.| with 1/(4ab)
   l = axis(st, 2 * b, 2 * a, b1, b0, D, 2 * b * D, D, b * D, D, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b], p->tiles[sid]);
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf y-inverse");
   NLOS_MARK(p, s, sid++);
   // scales the data carries into this last pass (it applies none of its own)
@@ -590,6 +661,8 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   l = axis(st, 2 * a, 1, b0, vol, b * D, 0, b * D, 0, b * D, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a], p->tiles[sid]);
   l.store_mode = kStoreAbs;
   l.p.st_dev_scale = inv_s;
+  l.err = err;
+  attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf x-inverse");
   NLOS_MARK(p, s, sid++);
   return NLOS_OK;
@@ -597,6 +670,10 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
 
 nlos_status_t run_plan(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaStream_t s) {
   char* w = static_cast<char*>(ws);
+  // errors left pending by earlier, unrelated runtime calls of this thread
+  // (the runtime is shared with the host application) must not be reported
+  // against this sequence's launches
+  cudaGetLastError();
   return p->d.method == NLOS_FK ? run_fk(p, H, vol, w, s) : run_pf(p, H, vol, w, s);
 }
 
@@ -685,7 +762,12 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
     p->stage_kind.push_back(xs || ys ? 1 : (nm == "fk_stolt_z" ? 2 : 0));
     p->stage_len.push_back(xs ? 2 * p->a : ys ? 2 * p->b : nm == "fk_stolt_z" ? 2 * p->n : 0);
   }
+  // default launch shapes: TMA-staged axis transforms (each falls back to
+  // direct loads where the layout does not allow TMA); the autotuner may
+  // choose others
   p->tiles.assign(p->stage_names.size(), 0);
+  for (size_t i = 0; i < p->tiles.size(); ++i)
+    if (p->stage_kind[i] == 1) p->tiles[i] = axis_ic_count(p->stage_len[i]);
   st = desc->method == NLOS_FK ? build_fk(p) : build_pf(p);
   const bool own_ws = !(flags & NLOS_PLAN_NO_WORKSPACE);
   if (st == NLOS_OK && own_ws) st = dalloc(p, &p->ws, p->ws_bytes, "workspace");
@@ -1070,6 +1152,19 @@ nlos_status_t nlos_batch_destroy(nlos_batch_t b) {
   if (!b) return fail(NLOS_ERR_INVALID_ARG, "batch is NULL");
   cudaDeviceSynchronize();
   batch_free(b);
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_workspace_check(nlos_plan_t p, const void* workspace, int* code) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  const char* ws = static_cast<const char*>(workspace ? workspace : p->ws);
+  if (!ws) return fail(NLOS_ERR_INVALID_ARG, "no workspace");
+  int v = 0;
+  NLOS_CU(cudaMemcpy(&v, ws + p->off_scal + kErrOffset, sizeof v, cudaMemcpyDeviceToHost), "error word read");
+  if (v != 0) NLOS_CU(cudaMemset(const_cast<char*>(ws) + p->off_scal + kErrOffset, 0, sizeof v), "error word reset");
+  if (code) *code = v;
+  if (v == kDevErrTmaTimeout) return fail(NLOS_ERR_TIMEOUT, "a staged-load wait ran out of its iteration limit");
+  if (v != 0) return fail(NLOS_ERR_CUDA, "device error word %d", v);
   return NLOS_OK;
 }
 

@@ -189,6 +189,7 @@ __device__ __forceinline__ void dft16_half(float2* v) {
 //   float2* sm(int t)                        shared-memory base of transform t; element l
 //                                            lives at sm(t)[pad16(l) * SSTRIDE]
 //   static constexpr int SSTRIDE
+//   static constexpr bool kSmemInput         load() reads the shared buffer the passes reuse
 //   const float2* tw                         twiddle table of the plan for length L
 template <int L, int NT, bool kHalfIn, bool kHalfOut, int P, class Ctx>
 __device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[NT][16]) {
@@ -231,7 +232,9 @@ __device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[
         for (int r = 0; r < R; ++r) v[t][i * R + r] = ctx.sm(t)[pad16(j + r * Q) * SS];
     }
   }
-  if constexpr (!kFirst) __syncthreads();
+  // in-place: every read of this pass completes before the first write (a
+  // first pass whose input was staged in the same shared buffer needs it too)
+  if constexpr (!kFirst || Ctx::kSmemInput) __syncthreads();
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int j = j0 + i * S::TPC;

@@ -1,6 +1,7 @@
 // Internal interfaces between the host plan code and the kernel files.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -11,7 +12,7 @@ namespace nlos {
 enum Storage : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
 
 // Load/store modes of the strided-axis FFT.
-enum AxisLoad : int { kLoadReal = 0, kLoadCpx = 1 };
+enum AxisLoad : int { kLoadReal = 0, kLoadCpx = 1, kLoadRealPair = 2 };
 enum AxisStore : int { kStoreCpx = 0, kStoreAbs2 = 1, kStoreAbs = 2 };
 
 // FFT of length L along one axis of a [outer][L][inner] array (inner
@@ -36,7 +37,10 @@ struct AxisParams {
 
 struct AxisLaunch {
   AxisParams p;
-  int tile;                    // column-tile variant (0 = default)
+  int tile;                    // launch-shape variant: column tile = tile % n, TMA staging = tile / n
+  CUtensorMap tmap;            // input tensor map for TMA staging (valid if has_tmap)
+  int has_tmap;
+  int* err;                    // device error word (bounded-wait timeouts), may be null
   int L;
   long long n_outer;
   int storage;                 // element type of complex arrays (and of real input)
@@ -44,8 +48,23 @@ struct AxisLaunch {
   int store_mode;              // AxisStore
 };
 cudaError_t launch_axis_fft(const AxisLaunch& l, cudaStream_t s);
-// number of column-tile variants of the axis transform of length L
-__host__ __device__ constexpr int axis_tile_count(int L) { return (L >= 128 && L <= 512) ? 3 : 2; }
+// Column-tile variants per length (selected by AxisLaunch::tile; index 0 is
+// the default, the autotuner may pick another).
+__host__ __device__ constexpr int axis_ic(int L, int v) {
+  return L <= 32 ? (v == 0 ? 32 : 64)
+       : L <= 64 ? (v == 0 ? 32 : 16)
+       : L <= 256 ? (v == 0 ? 16 : (v == 1 ? 8 : 32))
+       : L <= 512 ? (v == 0 ? 8 : (v == 1 ? 4 : 16))
+       : L <= 1024 ? (v == 0 ? 8 : 4)
+       : (v == 0 ? 4 : 2);
+}
+
+// number of column-tile widths of the axis transform of length L; the launch
+// shape variants are these widths, each with direct loads or TMA staging
+__host__ __device__ constexpr int axis_ic_count(int L) { return (L >= 128 && L <= 512) ? 3 : 2; }
+__host__ __device__ constexpr int axis_tile_count(int L) { return 2 * axis_ic_count(L); }
+// error codes written to the device error word
+constexpr int kDevErrTmaTimeout = 1;
 // number of pencils-per-CTA variants of the f-k temporal stage of length L = 2n
 __host__ __device__ constexpr int fk_tile_count(int L) { return 2; }
 

@@ -14,6 +14,7 @@ namespace nlos {
 template <int L, class TR, class TS>
 struct PfBandCtx {
   static constexpr int SSTRIDE = 1;
+  static constexpr bool kSmemInput = false;
   const TR* h;
   TS* P;
   float2* W;
@@ -102,16 +103,18 @@ cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s) {
 // lerp is K0 + alpha (K1 - K0) and the taper multiplies the finished sum.
 // Accumulation is float32 whatever the storage type.
 // ---------------------------------------------------------------------------
-constexpr int kDepthBlock = 128;
+constexpr int kDepthThreads = 64;                 // threads per CTA
+constexpr int kDepthPerThread = 2;                // depths per thread (d and d + 64)
+constexpr int kDepthBlock = kDepthThreads * kDepthPerThread;
 
 template <class TS, class TK>
-__global__ void __launch_bounds__(kDepthBlock)
+__global__ void __launch_bounds__(kDepthThreads)
 pf_depth_kernel(const PfDepthParams p) {
-  extern __shared__ float2 ps[];   // [16][F] phasors of the chunk's pixels
+  extern __shared__ float4 ps4[];   // [F][kPfChunk / 2] pairs of the chunk's phasors
   __shared__ int pix[kPfChunk];
   __shared__ float sal[kPfChunk], sac[kPfChunk];
   const int ch = blockIdx.x;
-  const int d = blockIdx.y * kDepthBlock + threadIdx.x;
+  const int d0 = blockIdx.y * kDepthBlock + threadIdx.x;
   if (threadIdx.x < kPfChunk) {
     pix[threadIdx.x] = p.chunk_pix[ch * kPfChunk + threadIdx.x];
     sal[threadIdx.x] = p.chunk_alpha[ch * kPfChunk + threadIdx.x];
@@ -120,34 +123,56 @@ pf_depth_kernel(const PfDepthParams p) {
   __syncthreads();
   const int F = p.F;
   const TS* Ph = static_cast<const TS*>(p.Phat);
-  for (int idx = threadIdx.x; idx < kPfChunk * F; idx += kDepthBlock) {
+  float2* ps = reinterpret_cast<float2*>(ps4);
+  for (int idx = threadIdx.x; idx < kPfChunk * F; idx += kDepthThreads) {
     const int q = idx / F, f = idx - q * F;
     const int px = pix[q];
-    ps[idx] = px >= 0 ? Cpx<TS>::get(Ph + (long long)px * F + f) : make_float2(0.f, 0.f);
+    ps[f * kPfChunk + q] = px >= 0 ? Cpx<TS>::get(Ph + (long long)px * F + f) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  if (d >= p.D) return;
   float alpha[kPfChunk];
 #pragma unroll
   for (int q = 0; q < kPfChunk; ++q) alpha[q] = sal[q];
-  float2 acc[kPfChunk];
+  float2 acc[kDepthPerThread][kPfChunk];
 #pragma unroll
-  for (int q = 0; q < kPfChunk; ++q) acc[q] = make_float2(0.f, 0.f);
+  for (int e = 0; e < kDepthPerThread; ++e)
+#pragma unroll
+    for (int q = 0; q < kPfChunk; ++q) acc[e][q] = make_float2(0.f, 0.f);
   const int2 i01 = p.chunk_i01[ch];
   const TK* K = static_cast<const TK*>(p.K);
-  const TK* K0 = K + (long long)i01.x * F * p.D + d;
-  const TK* K1 = K + (long long)i01.y * F * p.D + d;
+  const long long row0 = (long long)i01.x * F * p.D, row1 = (long long)i01.y * F * p.D;
+  bool dv[kDepthPerThread];
+  int dd[kDepthPerThread];
+#pragma unroll
+  for (int e = 0; e < kDepthPerThread; ++e) {
+    dd[e] = d0 + e * kDepthThreads;
+    dv[e] = dd[e] < p.D;
+  }
 #pragma unroll 2
   for (int f = 0; f < F; ++f) {
-    const float2 k0 = Cpx<TK>::get(K0 + (long long)f * p.D);
-    const float2 k1 = Cpx<TK>::get(K1 + (long long)f * p.D);
-    const float2 dk = csub(k1, k0);
+    float2 k0[kDepthPerThread], dk[kDepthPerThread];
 #pragma unroll
-    for (int q = 0; q < kPfChunk; ++q) {
-      const float2 kl = make_float2(fmaf(alpha[q], dk.x, k0.x), fmaf(alpha[q], dk.y, k0.y));
-      const float2 x = ps[q * F + f];
-      acc[q].x = fmaf(x.x, kl.x, fmaf(-x.y, kl.y, acc[q].x));
-      acc[q].y = fmaf(x.x, kl.y, fmaf(x.y, kl.x, acc[q].y));
+    for (int e = 0; e < kDepthPerThread; ++e) {
+      const long long o = (long long)f * p.D + (dv[e] ? dd[e] : 0);
+      const float2 a = Cpx<TK>::get(K + row0 + o), b = Cpx<TK>::get(K + row1 + o);
+      k0[e] = a;
+      dk[e] = csub(b, a);
+    }
+    const float4* pf = ps4 + f * (kPfChunk / 2);
+#pragma unroll
+    for (int q2 = 0; q2 < kPfChunk / 2; ++q2) {
+      const float4 xx = pf[q2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int q = 2 * q2 + h;
+        const float2 x = h == 0 ? make_float2(xx.x, xx.y) : make_float2(xx.z, xx.w);
+#pragma unroll
+        for (int e = 0; e < kDepthPerThread; ++e) {
+          const float2 kl = make_float2(fmaf(alpha[q], dk[e].x, k0[e].x), fmaf(alpha[q], dk[e].y, k0[e].y));
+          acc[e][q].x = fmaf(x.x, kl.x, fmaf(-x.y, kl.y, acc[e][q].x));
+          acc[e][q].y = fmaf(x.x, kl.y, fmaf(x.y, kl.x, acc[e][q].y));
+        }
+      }
     }
   }
   const float sc = p.scale * (p.dev_scale ? *p.dev_scale : 1.0f);
@@ -155,7 +180,10 @@ pf_depth_kernel(const PfDepthParams p) {
 #pragma unroll
   for (int q = 0; q < kPfChunk; ++q) {
     const int px = pix[q];
-    if (px >= 0) Cpx<TS>::put(C + (long long)px * p.D + d, cscale(acc[q], sac[q] * sc));
+    if (px < 0) continue;
+#pragma unroll
+    for (int e = 0; e < kDepthPerThread; ++e)
+      if (dv[e]) Cpx<TS>::put(C + (long long)px * p.D + dd[e], cscale(acc[e][q], sac[q] * sc));
   }
 }
 
@@ -168,7 +196,7 @@ static cudaError_t launch_depth_typed(const PfDepthParams& p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)p.nchunks, (unsigned)((p.D + kDepthBlock - 1) / kDepthBlock));
-  k<<<grid, kDepthBlock, smem, s>>>(p);
+  k<<<grid, kDepthThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -294,15 +322,23 @@ cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int st
 // ---------------------------------------------------------------------------
 // Per-volume scale for reduced-precision storage (two-stage, deterministic).
 // ---------------------------------------------------------------------------
+// eight consecutive elements per thread and iteration (n is a multiple of 8,
+// so they share one pencil and their ramp is t0 .. t0 + 7)
 template <class TR>
 __global__ void sumsq_partial_kernel(const TR* H, long long count, int n, float t_scale, float* partial) {
   __shared__ float red[256];
   float acc = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-       i += (long long)gridDim.x * blockDim.x) {
-    float v = Real<TR>::get(H + i);
-    if (t_scale != 0.f) v *= (float)(int)(i % n) * t_scale;
-    acc = fmaf(v, v, acc);
+  const long long chunks = count / 8;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < chunks;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long i0 = q * 8;
+    const int t0 = (int)(i0 % n);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float v = Real<TR>::get(H + i0 + k);
+      if (t_scale != 0.f) v *= (float)(t0 + k) * t_scale;
+      acc = fmaf(v, v, acc);
+    }
   }
   red[threadIdx.x] = acc;
   __syncthreads();

@@ -27,7 +27,7 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles",
             "nlos_batch_create", "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex",
             "nlos_server_create", "nlos_server_preload", "nlos_server_submit", "nlos_server_wait",
-            "nlos_server_stats", "nlos_server_destroy"]
+            "nlos_server_stats", "nlos_server_destroy", "nlos_workspace_check", "nlos_selftest_bounded_wait"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -90,6 +90,10 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_server_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int]
     lib.nlos_server_destroy.argtypes = [vp]
+    lib.nlos_workspace_check.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.nlos_workspace_check.restype = ctypes.c_int
+    lib.nlos_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    lib.nlos_selftest_bounded_wait.restype = ctypes.c_int
     for name in ("nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles", "nlos_batch_create",
                  "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex", "nlos_server_create",
                  "nlos_server_preload", "nlos_server_submit", "nlos_server_wait", "nlos_server_stats",

@@ -1,7 +1,7 @@
 """Batched execution: a CUDA-graph batch of captures of uneven size (f-k and
 phasor fields, FP32 and FP16 storage) reproduces the single-capture results
 bit for bit, replays read the buffers' current contents, and every launch
-shape the autotuner may choose gives bit-identical volumes."""
+shape the autotuner may choose gives the same volumes (to rounding)."""
 import os
 
 import numpy as np
@@ -79,14 +79,18 @@ def test_every_launch_shape_gives_identical_volumes():
         base = plan.reconstruct(x).clone()
         n = len(plan.tiles)
         for stage in range(n):
-            for v in range(1, 3):
+            for v in range(1, 6):
                 tiles = [0] * n
                 tiles[stage] = v
                 try:
                     plan.tiles = tiles
                 except Exception:
                     continue          # stage has fewer variants
-                assert torch.equal(plan.reconstruct(x), base), (stage, v)
+                got = plan.reconstruct(x)
+                # same arithmetic up to rounding order (packing two real columns
+                # per transform in the x pass rounds differently)
+                err = float(torch.linalg.vector_norm((got - base).double()) / torch.linalg.vector_norm(base.double()))
+                assert err <= 1e-6, (stage, v, err)
 
 
 def test_autotune_picks_valid_shapes_and_caches():
@@ -99,6 +103,7 @@ def test_autotune_picks_valid_shapes_and_caches():
     x = to_device(cap.counts, torch.float32)
     tuned = plan.reconstruct(x).clone()
     plan.tiles = [0] * 5
-    assert torch.equal(plan.reconstruct(x), tuned)
+    other = plan.reconstruct(x)
+    assert float(torch.linalg.vector_norm((other - tuned).double()) / torch.linalg.vector_norm(tuned.double())) <= 1e-6
     plan2 = nlos.plan_for_capture(g, "fk", "f32")
     assert plan2.autotune() == tiles          # served from the process cache
