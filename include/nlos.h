@@ -35,6 +35,7 @@ extern "C" {
 
 typedef enum { NLOS_FK = 0, NLOS_PHASOR_RSD = 1 } nlos_method_t;
 typedef enum { NLOS_F32 = 0, NLOS_F16 = 1, NLOS_BF16 = 2 } nlos_storage_t;
+typedef enum { NLOS_OUT_MAGNITUDE = 0, NLOS_OUT_COMPLEX = 1 } nlos_output_t;
 typedef enum {
   NLOS_OK = 0,
   NLOS_ERR_INVALID_ARG = 1,
@@ -59,7 +60,13 @@ typedef struct nlos_server_s* nlos_server_t;
  *   method        nlos_method_t
  *   storage       nlos_storage_t of the input and of stored intermediates;
  *                 reduced precision uses a per-volume scale, arithmetic is float32
- *   pad_factor    2 (zero padding x2 on every axis, Sec. 4.2); 1 -> NLOS_ERR_UNSUPPORTED
+ *   pad_factor    2: zero padding x2 on every axis (Sec. 4.2); 1: unpadded f-k
+ *                 (Sec. 4.2's Pad x1 variant; nx, ny >= 16); other values INVALID_ARG
+ *   output        NLOS_OUT_MAGNITUDE: float32 volume, |Psi|^2 for f-k (Alg. 1)
+ *                 and |I| for phasor fields (Alg. 4); NLOS_OUT_COMPLEX: the
+ *                 complex field itself (Psi, or I) as interleaved float32
+ *                 (re, im) pairs, twice the bytes, the input of the coherence
+ *                 merge of Eqs. 8-9
  * Phasor-field only (Sec. 4.3, Eqs. 4-7):
  *   wavelength_m  virtual wavelength (0 -> 4 * wall_w_m / nx)
  *   cycles        Gaussian virtual-wave width in periods (0 -> 5)
@@ -80,6 +87,7 @@ typedef struct {
   double depth_min_m, depth_max_m;
   int sigma_s, sigma_t;
   double delta_m;
+  int output;
 } nlos_plan_desc_t;
 
 /* Fill *desc with defaults (f-k, float32, pad 2, cycles 5, confocal). */
@@ -93,7 +101,7 @@ void nlos_plan_desc_default(nlos_plan_desc_t* desc);
  * allocates the default workspace. Synchronous. *out receives an opaque
  * handle owned by the caller until nlos_plan_destroy.
  * Errors: INVALID_ARG (null pointer, sizes, extents <= 0, empty band),
- * UNSUPPORTED (pad_factor 1, non-power-of-two sizes), OUT_OF_MEMORY, CUDA.
+ * UNSUPPORTED (unpadded phasor fields, non-power-of-two sizes), OUT_OF_MEMORY, CUDA.
  */
 nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out);
 
@@ -279,6 +287,48 @@ nlos_status_t nlos_plan_stage_times(nlos_plan_t plan, double* times_ms, int capa
 
 /* Name of stage i of the plan's sequence (NULL if out of range). */
 const char* nlos_plan_stage_name(nlos_plan_t plan, int stage);
+
+/*
+ * Post-processing of reconstructed volumes. All pointers are device memory
+ * owned by the caller; volumes are [nx][ny][nz] with depth innermost; every
+ * call is asynchronous on stream and allocates nothing. Errors: INVALID_ARG
+ * (NULL pointers, non-positive sizes, N_w outside [1, 16]), CUDA (launch).
+ *
+ * nlos_max_image: the display reduction of Alg. 1 / Sec. 4.2,
+ *   image[x][y] = max_z volume[x][y][z] (its square root if take_sqrt, which
+ *   turns an f-k |Psi|^2 volume into an |Psi| image). image is float32 [nx][ny].
+ */
+nlos_status_t nlos_max_image(const float* volume, int nx, int ny, int nz, int take_sqrt, float* image, void* stream);
+
+/*
+ * nlos_moe_mix: the mixture of experts of Eq. 10 (Sec. 4.4) on two float32
+ * images of `count` pixels: both are divided by their own maximum, mixed as
+ * f = f_fk * (f_rsd + eps)^beta, and the result divided by its maximum.
+ * One thread block; out may alias neither input.
+ */
+nlos_status_t nlos_moe_mix(const float* img_fk, const float* img_rsd, long long count, float beta, float eps,
+                           float* out, void* stream);
+
+/*
+ * nlos_coherence_merge: the coherence factor of Eq. 8 and the merged
+ * magnitude of Eq. 9 over a window of N_w = nw complex volumes (interleaved
+ * float32 (re, im), `count` voxels each; frames[] is a host array of nw device
+ * pointers, e.g. NLOS_OUT_COMPLEX reconstructions):
+ *   C = |sum_j f_j| / (eps + sum_j |f_j|),  merged = C |sum_j f_j| / N_w.
+ * coherence may be NULL; eps must be > 0.
+ */
+nlos_status_t nlos_coherence_merge(const void* const* frames, int nw, long long count, float eps, float* merged,
+                                   float* coherence, void* stream);
+
+/*
+ * nlos_dda: depth-dependent averaging of the last N_w = nw float32 volumes
+ * (Sec. 4.4; the paper does not fix the weights). frames[0] is the newest
+ * frame; plane z averages the newest N(z) = min(N_w, 1 + floor(N_w z / nz))
+ * frames, so near planes keep their temporal detail and far, weak planes are
+ * averaged over the whole window. frames[] is a host array of device pointers
+ * to [nxy][nz] volumes.
+ */
+nlos_status_t nlos_dda(const float* const* frames, int nw, long long nxy, int nz, float* out, void* stream);
 
 /* Release the plan's tables, workspace and staging buffers (synchronises the device). */
 nlos_status_t nlos_plan_destroy(nlos_plan_t plan);

@@ -75,6 +75,9 @@ struct AxisCtx {
     if constexpr (ST == kStoreCpx) {
       if (inverse) v = cconj(v);
       Cpx<TS>::put(static_cast<TS*>(out) + o, cscale(v, stmul));
+    } else if constexpr (ST == kStoreCpx32) {
+      if (inverse) v = cconj(v);
+      static_cast<float2*>(out)[o] = cscale(v, stmul);
     } else if constexpr (ST == kStoreAbs2) {
       static_cast<float*>(out)[o] = fmaf(v.x, v.x, v.y * v.y) * stmul;
     } else {
@@ -112,7 +115,7 @@ struct AxisPairCtx {
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { smem[pad16(l) * IC + c] = x[0]; }
 };
 
-template <int L, int IC, class TS>
+template <int L, int IC, class TS, bool kHalfIn>
 __global__ void __launch_bounds__(AxisTile<L, IC>::THREADS)
 axis_fft_realpair_kernel(const AxisParams p) {
   extern __shared__ float2 pair_sm[];
@@ -136,7 +139,7 @@ axis_fft_realpair_kernel(const AxisParams p) {
   ctx.v1 = ii1 < p.inner;
   ctx.m0 = ldmul * (p.t_len > 0 ? (float)(int)(ii0 % p.t_len) * p.t_scale : 1.0f);
   ctx.m1 = ldmul * (p.t_len > 0 ? (float)(int)(ii1 % p.t_len) * p.t_scale : 1.0f);
-  fftn_run<L, 1, true, false>(ctx, j0);
+  fftn_run<L, 1, kHalfIn, false>(ctx, j0);
   __syncthreads();
   const float h = 0.5f * p.scale * (p.st_dev_scale ? *p.st_dev_scale : 1.0f);
   TS* out = static_cast<TS*>(p.out);
@@ -150,11 +153,11 @@ axis_fft_realpair_kernel(const AxisParams p) {
   }
 }
 
-template <int L, int IC, class TS>
+template <int L, int IC, class TS, bool kHalfIn>
 cudaError_t launch_axis_pair_ic(const AxisLaunch& l, cudaStream_t s) {
   using Tile = AxisTile<L, IC>;
   constexpr size_t smem = sizeof(float2) * FftShape<L>::SMEM * IC;
-  auto k = axis_fft_realpair_kernel<L, IC, TS>;
+  auto k = axis_fft_realpair_kernel<L, IC, TS, kHalfIn>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -164,12 +167,12 @@ cudaError_t launch_axis_pair_ic(const AxisLaunch& l, cudaStream_t s) {
   return axis_report("realpair", L, IC, Tile::THREADS, smem, grid.x, grid.y, cudaGetLastError());
 }
 
-template <int L, class TS>
+template <int L, class TS, bool kHalfIn>
 cudaError_t launch_axis_pair(const AxisLaunch& l, cudaStream_t s) {
   const int v = (l.tile >= 0 && l.tile < axis_tile_count(L)) ? l.tile % axis_ic_count(L) : 0;
-  if (v == 0) return launch_axis_pair_ic<L, axis_ic(L, 0), TS>(l, s);
-  if (v == 1) return launch_axis_pair_ic<L, axis_ic(L, 1), TS>(l, s);
-  return launch_axis_pair_ic<L, axis_ic(L, 2), TS>(l, s);
+  if (v == 0) return launch_axis_pair_ic<L, axis_ic(L, 0), TS, kHalfIn>(l, s);
+  if (v == 1) return launch_axis_pair_ic<L, axis_ic(L, 1), TS, kHalfIn>(l, s);
+  return launch_axis_pair_ic<L, axis_ic(L, 2), TS, kHalfIn>(l, s);
 }
 
 template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
@@ -343,7 +346,7 @@ cudaError_t launch_axis_ic(const AxisLaunch& l, cudaStream_t s) {
 template <int L, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
   if constexpr (LD == kLoadRealPair) {
-    return launch_axis_pair<L, TS>(l, s);
+    return launch_axis_pair<L, TS, kHalfIn>(l, s);
   } else {
     const int v = (l.tile >= 0 && l.tile < axis_tile_count(L)) ? l.tile % axis_ic_count(L) : 0;
     if (v == 0) return launch_axis_ic<L, axis_ic(L, 0), LD, ST, TS, kHalfIn, kHalfOut>(l, s);
@@ -392,6 +395,17 @@ cudaError_t launch_axis_typed(const AxisLaunch& l, cudaStream_t s) {
     return launch_axis_len<RANGE, kLoadReal, kStoreCpx, TS, true, false>(l, s);
   if (l.load_mode == kLoadRealPair && l.store_mode == kStoreCpx && half_in && 2 * l.p.L_out <= l.L + 2)
     return launch_axis_len<RANGE, kLoadRealPair, kStoreCpx, TS, true, false>(l, s);
+  // unpadded transforms: every input present, every output kept (the real
+  // x pass keeps the L/2 + 1 non-redundant outputs)
+  const bool full_in = l.p.L_in == l.L;
+  if (l.load_mode == kLoadReal && l.store_mode == kStoreCpx && full_in && 2 * l.p.L_out <= l.L + 2)
+    return launch_axis_len<RANGE, kLoadReal, kStoreCpx, TS, false, false>(l, s);
+  if (l.load_mode == kLoadRealPair && l.store_mode == kStoreCpx && full_in && 2 * l.p.L_out <= l.L + 2)
+    return launch_axis_len<RANGE, kLoadRealPair, kStoreCpx, TS, false, false>(l, s);
+  if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx && full_in && l.p.L_out == l.L)
+    return launch_axis_len<RANGE, kLoadCpx, kStoreCpx, TS, false, false>(l, s);
+  if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs2 && full_in && l.p.L_out == l.L)
+    return launch_axis_len<RANGE, kLoadCpx, kStoreAbs2, TS, false, false>(l, s);
   if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx && half_in && !half_out)
     return launch_axis_len<RANGE, kLoadCpx, kStoreCpx, TS, true, false>(l, s);
   if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx && l.p.L_in == l.L && half_out)
@@ -400,6 +414,8 @@ cudaError_t launch_axis_typed(const AxisLaunch& l, cudaStream_t s) {
     return launch_axis_len<RANGE, kLoadCpx, kStoreAbs2, TS, false, true>(l, s);
   if (l.load_mode == kLoadCpx && l.store_mode == kStoreAbs && l.p.L_in == l.L && half_out)
     return launch_axis_len<RANGE, kLoadCpx, kStoreAbs, TS, false, true>(l, s);
+  if (l.load_mode == kLoadCpx && l.store_mode == kStoreCpx32 && l.p.L_in == l.L && half_out)
+    return launch_axis_len<RANGE, kLoadCpx, kStoreCpx32, TS, false, true>(l, s);
   return axis_report("no-variant", l.L, 0, 0, 0, l.load_mode, l.store_mode, cudaErrorInvalidValue);
 }
 

@@ -103,7 +103,7 @@ struct FkInvCtx {
   float stmul;
   __device__ __forceinline__ void load(int m, float2 (&x)[2]) const {
     x[0] = x[1] = make_float2(0.f, 0.f);
-    if (m < 1) return;                                // m <= n-1 (upper half is pruned)
+    if (m < 1) return;                                // m < L/2 (upper half is pruned)
     const StoltCoord c = stolt_coord(Ahi, Alo, m, n);
     if (!c.valid) return;
     const float2 u0 = U[pad16(c.k0)], u1 = U[pad16(c.k1)];
@@ -116,7 +116,7 @@ struct FkInvCtx {
     x[1] = cscale(e, c.jac);
   }
   __device__ __forceinline__ float2* sm(int t) const { return t == 0 ? W0 : W1; }
-  __device__ __forceinline__ void store(int l, const float2 (&x)[2]) const {   // l < n (kHalfOut)
+  __device__ __forceinline__ void store(int l, const float2 (&x)[2]) const {   // every l the schedule keeps
     if (st0) Cpx<TS>::put(out0 + l, cscale(cconj(x[0]), stmul));
     if (st1) Cpx<TS>::put(out1 + l, cscale(cconj(x[1]), stmul));
   }
@@ -136,7 +136,10 @@ template <int L, int PPC_> struct FkTile {
   static constexpr size_t SMEM = sizeof(float2) * 3 * PPC * FftShape<L>::SMEM;
 };
 
-template <int L, int PPC, class TS>
+// kPad2: the temporal axis is zero-padded to L = 2n (the forward input's upper
+// half is zero and only z < n is kept); otherwise L = n and every output is
+// kept. Either way the Stolt source must stay below L/2.
+template <int L, int PPC, class TS, bool kPad2>
 __global__ void __launch_bounds__(FkTile<L, PPC>::THREADS)
 fk_zstage_kernel(const FkZParams p) {
   using S = FftShape<L>;
@@ -145,7 +148,7 @@ fk_zstage_kernel(const FkZParams p) {
   const int j0 = threadIdx.x % S::TPC;
   const long long pid = (long long)blockIdx.x * PPC + w;
   const bool valid = pid < p.npencils;
-  const int twob = 2 * p.b;
+  const int twob = p.b_pad;
   const int kx = valid ? (int)(pid / twob) : 0;
   const int ky = valid ? (int)(pid % twob) : 0;
   float2* U = fk_sm + w * S::SMEM;
@@ -154,7 +157,7 @@ fk_zstage_kernel(const FkZParams p) {
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
     FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul};
-    fftn_run<L, 1, true, false>(ctx, j0);
+    fftn_run<L, 1, kPad2, false>(ctx, j0);
   }
   __syncthreads();
   const float2 ax = p.ax[kx];
@@ -163,19 +166,19 @@ fk_zstage_kernel(const FkZParams p) {
   A = fast_two_sum(A.x, A.y + (ax.y + ay.y));
   TS* psi = static_cast<TS*>(p.psi);
   const long long o_direct = ((long long)kx * twob + ky) * p.n;
-  const int mkx = (kx == 0) ? 0 : 2 * p.a - kx;
+  const int mkx = (kx == 0) ? 0 : p.a_pad - kx;
   const int mky = (twob - ky) & (twob - 1);
   const long long o_mirror = ((long long)mkx * twob + mky) * p.n;
   // the partner is stored only where it is not itself a stored pencil
-  FkInvCtx<L, TS> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, p.n, A.x, A.y,
-                      valid, valid && kx > 0 && kx < p.a, p.st_scale};
-  fftn_run<L, 2, true, true>(ctx, j0);
+  FkInvCtx<L, TS> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, L / 2, A.x, A.y,
+                      valid, valid && kx > 0 && 2 * kx < p.a_pad, p.st_scale};
+  fftn_run<L, 2, true, kPad2>(ctx, j0);
 }
 
 template <int L, int PPC, class TS>
 cudaError_t launch_fk_ppc(const FkZParams& p, cudaStream_t s) {
   using T = FkTile<L, PPC>;
-  auto k = fk_zstage_kernel<L, PPC, TS>;
+  auto k = p.pad == 2 ? fk_zstage_kernel<L, PPC, TS, true> : fk_zstage_kernel<L, PPC, TS, false>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -194,7 +197,8 @@ cudaError_t launch_fk_one(const FkZParams& p, int tile, cudaStream_t s) {
 template <class TS>
 cudaError_t launch_fk_typed(const FkZParams& p, int tile, cudaStream_t s) {
   if (p.npencils <= 0) return cudaErrorInvalidValue;
-  switch (2 * p.n) {
+  switch (p.pad * p.n) {
+    case 16: return launch_fk_one<16, TS>(p, tile, s);
     case 32: return launch_fk_one<32, TS>(p, tile, s);
     case 64: return launch_fk_one<64, TS>(p, tile, s);
     case 128: return launch_fk_one<128, TS>(p, tile, s);

@@ -206,31 +206,35 @@ float2 split_ff(double v) {
 // ---------------------------------------------------------------------------
 nlos_status_t build_fk(nlos_plan_s* p) {
   const auto& d = p->d;
+  const int pf = d.pad_factor;
+  const int Lx = pf * p->a, Ly = pf * p->b, Lt = pf * p->n;
   const double dx = d.wall_w_m / d.nx, dy = d.wall_h_m / d.ny;
   const double sx = kC * d.bin_width_s / (2.0 * dx);
   const double sy = kC * d.bin_width_s / (2.0 * dy);
-  std::vector<float2> ax(2 * p->a), ay(2 * p->b);
-  for (int i = 0; i < 2 * p->a; ++i) {
-    const int pt = i < p->a ? i : i - 2 * p->a;
+  // signed index p~ of the Lx-point axis; mu^2 = A + m^2 with A = (n s_x p~ / a)^2 + (n s_y q~ / b)^2
+  // for either padding (the padded and unpadded grids give the same constant)
+  std::vector<float2> ax(Lx), ay(Ly);
+  for (int i = 0; i < Lx; ++i) {
+    const int pt = i < Lx / 2 ? i : i - Lx;
     const double v = (double)p->n * sx * pt / p->a;
     ax[i] = split_ff(v * v);
   }
-  for (int i = 0; i < 2 * p->b; ++i) {
-    const int qt = i < p->b ? i : i - 2 * p->b;
+  for (int i = 0; i < Ly; ++i) {
+    const int qt = i < Ly / 2 ? i : i - Ly;
     const double v = (double)p->n * sy * qt / p->b;
     ay[i] = split_ff(v * v);
   }
   nlos_status_t st;
   if ((st = upload(p, &p->ax, ax, "stolt table")) != NLOS_OK) return st;
   if ((st = upload(p, &p->ay, ay, "stolt table")) != NLOS_OK) return st;
-  if ((st = ensure_twiddles(p, 2 * p->a)) != NLOS_OK) return st;
-  if ((st = ensure_twiddles(p, 2 * p->b)) != NLOS_OK) return st;
-  if ((st = ensure_twiddles(p, 2 * p->n)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, Lx)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, Ly)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, Lt)) != NLOS_OK) return st;
   const size_t cb = complex_bytes(p->storage);
-  const long long a = p->a, b = p->b, n = p->n;
-  const size_t b0 = std::max((a + 1) * b * n, 2 * a * b * n) * cb;   // G1, then the y-inverse output
-  const size_t b1 = (a + 1) * 2 * b * n * cb;                         // G (kx <= a)
-  const size_t b2 = 2 * a * 2 * b * n * cb;                           // psi_z
+  const long long b = p->b, n = p->n, hx = Lx / 2 + 1;
+  const size_t b0 = std::max(hx * b * n, (long long)Lx * b * n) * cb;   // G1, then the y-inverse output
+  const size_t b1 = hx * Ly * n * cb;                                    // G (kx <= Lx/2)
+  const size_t b2 = (size_t)Lx * Ly * n * cb;                             // psi_z
   p->off[0] = 0;
   p->off[1] = align256(b0);
   p->off[2] = p->off[1] + align256(b1);
@@ -516,6 +520,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   float* scal = reinterpret_cast<float*>(ws + p->off_scal);
   int* err = reinterpret_cast<int*>(ws + p->off_scal + kErrOffset);
   const float* s_in = nullptr;
+  const float* inv_s = nullptr;
   const float* inv_s2 = nullptr;
   int sid = 0;
   NLOS_MARK(p, s, -1);
@@ -525,14 +530,16 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
             "volume scale");
     NLOS_MARK(p, s, sid++);
     s_in = scal;
+    inv_s = scal + 1;
     inv_s2 = scal + 2;
   }
-  const float g2a = pass_scale(st, 2 * a), g2b = pass_scale(st, 2 * b), g2n = pass_scale(st, 2 * n);
-  // FK1: x forward (real input, scaled by t/(n-1), zero-padded to 2a, kx in [0, a])
-  AxisLaunch l = axis(st, 2 * a, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)a + 1, 0, g2a, p->tw[2 * a], p->tiles[sid]);
+  const long long pf = p->d.pad_factor, Lx = pf * a, Ly = pf * b, Lt = pf * n, hx = Lx / 2 + 1;
+  const float g2a = pass_scale(st, (int)Lx), g2b = pass_scale(st, (int)Ly), g2n = pass_scale(st, (int)Lt);
+  // FK1: x forward (real input, scaled by t/(n-1), zero-padded to Lx, kx in [0, Lx/2])
+  AxisLaunch l = axis(st, (int)Lx, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)hx, 0, g2a, p->tw[(int)Lx], p->tiles[sid]);
   // direct variants pack two real columns per complex transform; TMA-staged
   // variants transform each real column on its own
-  l.load_mode = l.tile < axis_ic_count(2 * (int)a) ? kLoadRealPair : kLoadReal;
+  l.load_mode = l.tile < axis_ic_count((int)Lx) ? kLoadRealPair : kLoadReal;
   l.p.t_len = (int)n;
   l.p.t_scale = 1.0f / (float)(n - 1);
   l.p.ld_dev_scale = s_in;
@@ -540,8 +547,8 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk x-forward");
   NLOS_MARK(p, s, sid++);
-  // FK1: y forward (zero-padded to 2b)
-  l = axis(st, 2 * b, a + 1, b0, b1, n, b * n, n, 2 * b * n, n, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
+  // FK1: y forward (zero-padded to Ly)
+  l = axis(st, (int)Ly, hx, b0, b1, n, b * n, n, Ly * n, n, (int)b, (int)Ly, 0, g2b, p->tw[(int)Ly], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk y-forward");
@@ -550,31 +557,33 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   FkZParams z{};
   z.G = b1;
   z.psi = b2;
-  z.tw = p->tw[2 * n];
+  z.tw = p->tw[(int)Lt];
   z.ax = p->ax;
   z.ay = p->ay;
-  z.a = (int)a;
-  z.b = (int)b;
+  z.a_pad = (int)Lx;
+  z.b_pad = (int)Ly;
   z.n = (int)n;
-  z.npencils = (a + 1) * 2 * b;
+  z.pad = (int)pf;
+  z.npencils = hx * Ly;
   z.ld_scale = g2n;
   z.st_scale = g2n;
   NLOS_CU(launch_fk_zstage(z, st, p->tiles[sid], s), "fk stolt stage");
   NLOS_MARK(p, s, sid++);
   // FK4: y inverse (keep y < b)
-  l = axis(st, 2 * b, 2 * a, b2, b0, n, 2 * b * n, n, b * n, n, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b], p->tiles[sid]);
+  l = axis(st, (int)Ly, Lx, b2, b0, n, Ly * n, n, b * n, n, (int)Ly, (int)b, 1, g2b, p->tw[(int)Ly], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk y-inverse");
   NLOS_MARK(p, s, sid++);
-  // FK4: x inverse (keep x < a), |psi|^2 with the 1/(8abn) normalisation
-  const double N = 8.0 * a * b * n;
+  // FK4: x inverse (keep x < a), |psi|^2 with the 1/(Lx Ly Lt) normalisation
+  const double N = (double)Lx * Ly * Lt;
   // pass scales applied to the data before this last pass (it applies none of its own)
   const double gprod = (double)g2a * g2b * g2n * g2n * g2b;
-  const float fscale = (float)(1.0 / (N * N * gprod * gprod));
-  l = axis(st, 2 * a, 1, b0, vol, b * n, 0, b * n, 0, b * n, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a], p->tiles[sid]);
-  l.store_mode = kStoreAbs2;
-  l.p.st_dev_scale = inv_s2;
+  const bool cpx = p->d.output == NLOS_OUT_COMPLEX;
+  const float fscale = (float)(cpx ? 1.0 / (N * gprod) : 1.0 / (N * N * gprod * gprod));
+  l = axis(st, (int)Lx, 1, b0, vol, b * n, 0, b * n, 0, b * n, (int)Lx, (int)a, 1, fscale, p->tw[(int)Lx], p->tiles[sid]);
+  l.store_mode = cpx ? kStoreCpx32 : kStoreAbs2;
+  l.p.st_dev_scale = cpx ? inv_s : inv_s2;
   l.err = err;
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk x-inverse");
@@ -659,7 +668,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   const double gprod = (double)gn * g2b * g2a * c3_data * g2b;
   const float fscale = (float)(1.0 / (4.0 * a * b * gprod));
   l = axis(st, 2 * a, 1, b0, vol, b * D, 0, b * D, 0, b * D, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a], p->tiles[sid]);
-  l.store_mode = kStoreAbs;
+  l.store_mode = p->d.output == NLOS_OUT_COMPLEX ? kStoreCpx32 : kStoreAbs;
   l.p.st_dev_scale = inv_s;
   l.err = err;
   attach_tmap(l);
@@ -704,7 +713,13 @@ nlos_status_t validate(const nlos_plan_desc_t* d) {
   if (d->nx <= 0 || d->ny <= 0 || d->nt <= 0) return fail(NLOS_ERR_INVALID_ARG, "sizes must be positive");
   if (!(d->bin_width_s > 0) || !(d->wall_w_m > 0) || !(d->wall_h_m > 0))
     return fail(NLOS_ERR_INVALID_ARG, "bin width and wall extent must be > 0");
-  if (d->pad_factor != 2) return fail(NLOS_ERR_UNSUPPORTED, "only pad_factor 2 is supported");
+  if (d->pad_factor != 2 && d->pad_factor != 1) return fail(NLOS_ERR_INVALID_ARG, "pad_factor must be 1 or 2");
+  if (d->output != NLOS_OUT_MAGNITUDE && d->output != NLOS_OUT_COMPLEX)
+    return fail(NLOS_ERR_INVALID_ARG, "unknown output %d", d->output);
+  if (d->pad_factor == 1 && d->method != NLOS_FK)
+    return fail(NLOS_ERR_UNSUPPORTED, "the unpadded variant exists for f-k only");
+  if (d->pad_factor == 1 && (d->nx < 16 || d->ny < 16))
+    return fail(NLOS_ERR_UNSUPPORTED, "unpadded f-k needs nx, ny >= 16");
   if (!is_pow2(d->nx) || !is_pow2(d->ny) || !is_pow2(d->nt))
     return fail(NLOS_ERR_UNSUPPORTED, "sizes must be powers of two");
   if (d->nx < 8 || d->ny < 8 || d->nx > 1024 || d->ny > 1024)
@@ -760,7 +775,8 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   for (const std::string& nm : p->stage_names) {
     const bool xs = nm.find("_x_") != std::string::npos, ys = nm.find("_y_") != std::string::npos;
     p->stage_kind.push_back(xs || ys ? 1 : (nm == "fk_stolt_z" ? 2 : 0));
-    p->stage_len.push_back(xs ? 2 * p->a : ys ? 2 * p->b : nm == "fk_stolt_z" ? 2 * p->n : 0);
+    const int pf = desc->method == NLOS_FK ? desc->pad_factor : 2;
+    p->stage_len.push_back(xs ? pf * p->a : ys ? pf * p->b : nm == "fk_stolt_z" ? pf * p->n : 0);
   }
   // default launch shapes: TMA-staged axis transforms (each falls back to
   // direct loads where the layout does not allow TMA); the autotuner may
@@ -794,7 +810,8 @@ nlos_status_t nlos_plan_query(nlos_plan_t p, size_t out_shape[3], size_t* worksp
   }
   if (workspace_bytes) *workspace_bytes = p->ws_bytes;
   if (input_bytes) *input_bytes = (size_t)p->a * p->b * p->n * real_bytes(p->storage);
-  if (output_bytes) *output_bytes = (size_t)p->a * p->b * p->nz * sizeof(float);
+  if (output_bytes)
+    *output_bytes = (size_t)p->a * p->b * p->nz * (p->d.output == NLOS_OUT_COMPLEX ? sizeof(float2) : sizeof(float));
   return NLOS_OK;
 }
 

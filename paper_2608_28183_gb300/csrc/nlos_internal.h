@@ -13,7 +13,8 @@ enum Storage : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
 
 // Load/store modes of the strided-axis FFT.
 enum AxisLoad : int { kLoadReal = 0, kLoadCpx = 1, kLoadRealPair = 2 };
-enum AxisStore : int { kStoreCpx = 0, kStoreAbs2 = 1, kStoreAbs = 2 };
+// kStoreCpx32 writes complex float32 whatever the storage type (complex volumes)
+enum AxisStore : int { kStoreCpx = 0, kStoreAbs2 = 1, kStoreAbs = 2, kStoreCpx32 = 3 };
 
 // FFT of length L along one axis of a [outer][L][inner] array (inner
 // contiguous). Elements along the axis beyond L_in are zero; outputs with
@@ -76,11 +77,12 @@ __host__ __device__ constexpr int fk_tile_count(int L) { return 2; }
 struct FkZParams {
   const void* G;
   void* psi;
-  const float2* tw;            // twiddles for L = 2n
-  const float2* ax;            // [2a] float-float (hi, lo) of (n s_x p~ / a)^2
-  const float2* ay;            // [2b] float-float of (n s_y q~ / b)^2
-  int a, b, n;
-  long long npencils;          // (a + 1) * 2b
+  const float2* tw;            // twiddles for the temporal length L = pad * n
+  const float2* ax;            // [a_pad] float-float (hi, lo) of (n s_x p~ / a)^2
+  const float2* ay;            // [b_pad] float-float of (n s_y q~ / b)^2
+  int a_pad, b_pad, n;         // padded lateral lengths (pad * a, pad * b), time bins
+  int pad;                     // 2: zero-padded x2 on every axis; 1: unpadded
+  long long npencils;          // (a_pad / 2 + 1) * b_pad
   float ld_scale;              // multiplies forward loads
   const float* ld_dev_scale;   // optional device scalar multiplying forward loads
   float st_scale;              // multiplies stored values

@@ -64,9 +64,9 @@ struct Slot {
 
 std::string desc_key(const nlos_plan_desc_t& d) {
   char buf[512];
-  snprintf(buf, sizeof buf, "%d %d %d %.17g %.17g %.17g %d %d %d %.17g %.17g %d %.17g %.17g %d %d %.17g", d.nx, d.ny,
-           d.nt, d.bin_width_s, d.wall_w_m, d.wall_h_m, d.method, d.storage, d.pad_factor, d.wavelength_m, d.cycles,
-           d.n_depths, d.depth_min_m, d.depth_max_m, d.sigma_s, d.sigma_t, d.delta_m);
+  snprintf(buf, sizeof buf, "%d %d %d %.17g %.17g %.17g %d %d %d %.17g %.17g %d %.17g %.17g %d %d %.17g %d", d.nx,
+           d.ny, d.nt, d.bin_width_s, d.wall_w_m, d.wall_h_m, d.method, d.storage, d.pad_factor, d.wavelength_m,
+           d.cycles, d.n_depths, d.depth_min_m, d.depth_max_m, d.sigma_s, d.sigma_t, d.delta_m, d.output);
   return buf;
 }
 

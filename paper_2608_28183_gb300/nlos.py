@@ -19,6 +19,7 @@ NLOS_F32, NLOS_F16, NLOS_BF16 = 0, 1, 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 METHODS = {"fk": NLOS_FK, "pf": NLOS_PHASOR_RSD, "phasor": NLOS_PHASOR_RSD}
 STORAGES = {"f32": NLOS_F32, "f16": NLOS_F16, "bf16": NLOS_BF16}
+OUTPUTS = {"magnitude": 0, "complex": 1}
 
 EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nlos_reconstruct",
             "nlos_reconstruct_ws", "nlos_reconstruct_host", "nlos_reconstruct_batch",
@@ -27,7 +28,8 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles",
             "nlos_batch_create", "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex",
             "nlos_server_create", "nlos_server_preload", "nlos_server_submit", "nlos_server_wait",
-            "nlos_server_stats", "nlos_server_destroy", "nlos_workspace_check", "nlos_selftest_bounded_wait"]
+            "nlos_server_stats", "nlos_server_destroy", "nlos_workspace_check", "nlos_selftest_bounded_wait",
+            "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -41,6 +43,7 @@ class PlanDesc(ctypes.Structure):
         ("depth_min_m", ctypes.c_double), ("depth_max_m", ctypes.c_double),
         ("sigma_s", ctypes.c_int), ("sigma_t", ctypes.c_int),
         ("delta_m", ctypes.c_double),
+        ("output", ctypes.c_int),
     ]
 
 
@@ -94,6 +97,13 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_workspace_check.restype = ctypes.c_int
     lib.nlos_selftest_bounded_wait.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.nlos_selftest_bounded_wait.restype = ctypes.c_int
+    ll, fl = ctypes.c_longlong, ctypes.c_float
+    lib.nlos_max_image.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
+    lib.nlos_moe_mix.argtypes = [vp, vp, ll, fl, fl, vp, vp]
+    lib.nlos_coherence_merge.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ll, fl, vp, vp, vp]
+    lib.nlos_dda.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ll, ctypes.c_int, vp, vp]
+    for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles", "nlos_batch_create",
                  "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex", "nlos_server_create",
                  "nlos_server_preload", "nlos_server_submit", "nlos_server_wait", "nlos_server_stats",
@@ -141,7 +151,7 @@ def make_desc(nx: int, ny: int, nt: int, bin_width_s: float, wall_w_m: float, wa
               method: str = "fk", storage: str = "f32", pad_factor: int = 2, *,
               n_depths: int = 0, depth_min_m: float = 0.0, depth_max_m: float = 0.0,
               wavelength_m: float = 0.0, cycles: float = 5.0, sigma_s: int = 0, sigma_t: int = 0,
-              delta_m: float = 0.0) -> PlanDesc:
+              delta_m: float = 0.0, output: str = "magnitude") -> PlanDesc:
     lib = load_library()
     d = PlanDesc()
     lib.nlos_plan_desc_default(ctypes.byref(d))
@@ -153,6 +163,7 @@ def make_desc(nx: int, ny: int, nt: int, bin_width_s: float, wall_w_m: float, wa
     d.wavelength_m, d.cycles = wavelength_m, cycles
     d.n_depths, d.depth_min_m, d.depth_max_m = n_depths, depth_min_m, depth_max_m
     d.sigma_s, d.sigma_t, d.delta_m = sigma_s, sigma_t, delta_m
+    d.output = OUTPUTS[output]
     return d
 
 
@@ -185,20 +196,23 @@ class Plan:
         import torch
         return {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[self.storage]
 
-    def _check_io(self, transient, volume):
+    def output_dtype(self):
         import torch
+        return torch.complex64 if self.desc.output == OUTPUTS["complex"] else torch.float32
+
+    def _check_io(self, transient, volume):
         d = self.desc
         if not (transient.is_cuda and volume.is_cuda):
             raise ValueError("transient and volume must be CUDA tensors")
         if transient.dtype != self.input_dtype() or not transient.is_contiguous() \
                 or tuple(transient.shape) != (d.nx, d.ny, d.nt):
             raise ValueError(f"transient must be contiguous {self.input_dtype()} [{d.nx},{d.ny},{d.nt}]")
-        if volume.dtype != torch.float32 or not volume.is_contiguous() or tuple(volume.shape) != self.out_shape:
-            raise ValueError(f"volume must be contiguous float32 {list(self.out_shape)}")
+        if volume.dtype != self.output_dtype() or not volume.is_contiguous() or tuple(volume.shape) != self.out_shape:
+            raise ValueError(f"volume must be contiguous {self.output_dtype()} {list(self.out_shape)}")
 
     def empty_volume(self):
         import torch
-        return torch.empty(self.out_shape, dtype=torch.float32, device="cuda")
+        return torch.empty(self.out_shape, dtype=self.output_dtype(), device="cuda")
 
     def reconstruct(self, transient, volume=None, stream=None, workspace=None):
         """Reconstruct on the device; returns the volume tensor (asynchronous)."""
@@ -366,3 +380,82 @@ def plan_for_capture(geom, method="fk", storage="f32", **kw) -> Plan:
 
 def version() -> str:
     return load_library().nlos_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Post-processing (Sec. 4.4 and the display reduction of Sec. 4.2)
+# ---------------------------------------------------------------------------
+
+def _dev_f32(x, name, dtype=None):
+    import torch
+    dt = torch.float32 if dtype is None else dtype
+    if not x.is_cuda or x.dtype != dt or not x.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dt} tensor")
+
+
+def max_image(volume, take_sqrt: bool = False, image=None, stream=None):
+    """f(x, y) = max_z v(x, y, z) of a float32 [nx, ny, nz] volume (sqrt of it if take_sqrt)."""
+    import torch
+    load_library()
+    _dev_f32(volume, "volume")
+    nx, ny, nz = volume.shape
+    if image is None:
+        image = torch.empty((nx, ny), dtype=torch.float32, device=volume.device)
+    _dev_f32(image, "image")
+    if tuple(image.shape) != (nx, ny):
+        raise ValueError("image must be [nx, ny]")
+    _check(_lib.nlos_max_image(ctypes.c_void_p(volume.data_ptr()), nx, ny, nz, int(bool(take_sqrt)),
+                               ctypes.c_void_p(image.data_ptr()), _stream_ptr(stream)))
+    return image
+
+
+def moe_mix(img_fk, img_rsd, beta: float = 0.3, eps: float = 1e-3, out=None, stream=None):
+    """Eq. 10 on max-normalised images; the result is normalised to peak 1."""
+    import torch
+    load_library()
+    _dev_f32(img_fk, "img_fk")
+    _dev_f32(img_rsd, "img_rsd")
+    if img_fk.shape != img_rsd.shape:
+        raise ValueError("images must have the same shape")
+    if out is None:
+        out = torch.empty_like(img_fk)
+    _dev_f32(out, "out")
+    _check(_lib.nlos_moe_mix(ctypes.c_void_p(img_fk.data_ptr()), ctypes.c_void_p(img_rsd.data_ptr()),
+                             img_fk.numel(), beta, eps, ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def coherence_merge(frames, eps: float = 1e-6, merged=None, coherence=None, stream=None):
+    """Eqs. 8-9 over N_w complex64 volumes of one shape: returns (merged, coherence)."""
+    import torch
+    load_library()
+    for f in frames:
+        _dev_f32(f, "frame", torch.complex64)
+        if f.shape != frames[0].shape:
+            raise ValueError("frames must have one shape")
+    shape = frames[0].shape
+    if merged is None:
+        merged = torch.empty(shape, dtype=torch.float32, device=frames[0].device)
+    if coherence is None:
+        coherence = torch.empty(shape, dtype=torch.float32, device=frames[0].device)
+    F = (ctypes.c_void_p * len(frames))(*[f.data_ptr() for f in frames])
+    _check(_lib.nlos_coherence_merge(F, len(frames), frames[0].numel(), eps, ctypes.c_void_p(merged.data_ptr()),
+                                     ctypes.c_void_p(coherence.data_ptr()), _stream_ptr(stream)))
+    return merged, coherence
+
+
+def dda(frames, out=None, stream=None):
+    """Depth-dependent average of N_w float32 [nx, ny, nz] volumes, frames[0] the newest."""
+    import torch
+    load_library()
+    for f in frames:
+        _dev_f32(f, "frame")
+        if f.shape != frames[0].shape:
+            raise ValueError("frames must have one shape")
+    shape = frames[0].shape
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=frames[0].device)
+    F = (ctypes.c_void_p * len(frames))(*[f.data_ptr() for f in frames])
+    _check(_lib.nlos_dda(F, len(frames), frames[0].numel() // shape[-1], shape[-1],
+                         ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out

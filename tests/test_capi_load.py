@@ -52,9 +52,11 @@ def _create(lib, **kw):
 
 @pytest.mark.parametrize("kw,status", [
     (dict(nx=0), 1), (dict(bin_width_s=0.0), 1), (dict(wall_w_m=-1.0), 1), (dict(method=7), 1),
-    (dict(storage=9), 1), (dict(pad_factor=1), 4), (dict(nx=24), 4), (dict(nt=4096), 4),
+    (dict(storage=9), 1), (dict(pad_factor=3), 1), (dict(pad_factor=1, method=1, n_depths=8,
+                                                           depth_min_m=0.5, depth_max_m=1.0), 4),
+    (dict(pad_factor=1, nx=8), 4), (dict(nx=24), 4), (dict(nt=4096), 4),
     (dict(nx=4, ny=4), 4), (dict(method=1, n_depths=0), 1),
-    (dict(method=1, n_depths=8, depth_min_m=1.0, depth_max_m=0.5), 1),
+    (dict(method=1, n_depths=8, depth_min_m=1.0, depth_max_m=0.5), 1), (dict(output=2), 1), (dict(output=-1), 1),
 ])
 def test_invalid_descriptions_rejected_before_device_work(lib, kw, status):
     st, msg = _create(lib, **kw)
@@ -66,5 +68,9 @@ def test_null_arguments(lib):
     assert lib.nlos_reconstruct(None, None, None, None) == 1
     assert lib.nlos_plan_query(None, None, None, None, None) == 1
     assert lib.nlos_plan_destroy(None) == 1
+    assert lib.nlos_max_image(None, 4, 4, 4, 0, None, None) == 1
+    assert lib.nlos_moe_mix(None, None, 10, 0.3, 1e-3, None, None) == 1
+    assert lib.nlos_coherence_merge(None, 2, 10, 1e-6, None, None, None) == 1
+    assert lib.nlos_dda(None, 2, 10, 4, None, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, -1, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, 0, None) == 0

@@ -131,3 +131,34 @@ def test_fk_batch_matches_single_calls():
     torch.cuda.synchronize()
     for p, c, o in zip(plans, caps, outs):
         assert np.array_equal(o.cpu().numpy().astype(np.float64), _gpu(p, c.counts))
+
+
+UNPADDED = [
+    synth.Geometry(16, 16, 16, 300e-12, 0.5, 0.5),        # minimum unpadded sizes
+    synth.Geometry(32, 16, 128, 32e-12, 1.0, 0.6),        # non-square
+    synth.Geometry(64, 64, 512, 16e-12, 1.5, 1.5),
+]
+
+
+@pytest.mark.parametrize("geom", UNPADDED, ids=lambda g: f"{g.nx}x{g.ny}x{g.nt}")
+def test_fk_unpadded_parity(geom):
+    """The unpadded variant (Pad x1) against the oracle with pad_factor 1."""
+    from paper_2608_28183_gb300 import nlos
+    cap = _noise_capture(geom, seed=geom.nx + 3 * geom.nt)
+    plan = nlos.plan_for_capture(geom, "fk", "f32", pad_factor=1)
+    got = _gpu(plan, cap.counts)
+    ref = fk.fk_reconstruct(exact_input(cap.counts, torch.float32), geom.bin_width_s, geom.wall_w_m,
+                            geom.wall_h_m, pad_factor=1)
+    assert rel_l2(got, ref) <= 1e-5
+    assert same_peak(got, ref)
+
+
+def test_fk_unpadded_fp16():
+    from paper_2608_28183_gb300 import nlos
+    geom = UNPADDED[2]
+    cap = _noise_capture(geom, seed=9)
+    plan = nlos.plan_for_capture(geom, "fk", "f16", pad_factor=1)
+    got = _gpu(plan, cap.counts)
+    ref = fk.fk_reconstruct(exact_input(cap.counts, torch.float16), geom.bin_width_s, geom.wall_w_m,
+                            geom.wall_h_m, pad_factor=1)
+    assert rel_l2(got, ref) <= 2e-3
