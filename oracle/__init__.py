@@ -15,6 +15,11 @@ computes, written from the paper in float64 with numpy/scipy:
                     baseline of Sec. 2), used only to pin peak locations
   rsd_direct.py     direct spatial Rayleigh-Sommerfeld summation (Eq. 3),
                     used only to pin peak locations of the radial operator
+  post.py           max-over-depth images, mixture of experts (Eq. 10),
+                    coherence merge (Eqs. 8-9), depth-dependent average
+                    (Sec. 4.4)
+  binning.py        photon binning into transients and compact phasors
+                    (Sec. 4.1)
 
 Library primitives used as single steps: scipy.fft (DFTs), scipy.special.j0
 (Bessel J0), numpy matmul. Every function cites the passage it follows.

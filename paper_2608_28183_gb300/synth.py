@@ -262,3 +262,61 @@ def point_capture(geom: Geometry, points, *, peak: float = 1e3, background: floa
     """Capture of explicit point reflectors [(x, y, z, albedo), ...]."""
     scene = Scene(points=np.asarray(points, dtype=np.float64).reshape(-1, 4))
     return render(geom, scene, peak=peak, background=background, seed=seed, noise=noise)
+
+
+# ---------------------------------------------------------------------------
+# Photon streams: the SPAD records a photon binner consumes
+# ---------------------------------------------------------------------------
+
+@dataclass
+class PhotonStream:
+    pixel: np.ndarray        # uint32 wall index x * ny + y
+    ticks: np.ndarray        # uint32 time of flight in integer ticks
+    t0: int                  # tick of the start of bin 0
+    ticks_per_bin: int
+
+
+def photons_from_counts(counts: np.ndarray, *, ticks_per_bin: int = 16, t0: int = 1000, seed: int = 0,
+                        order: str = "scan", stray: int = 0) -> PhotonStream:
+    """One photon record per count of an integer [nx][ny][nt] histogram.
+
+    Each photon gets a uniformly drawn tick inside its bin. order="scan" emits
+    the wall points one after another (photons of a point in random time
+    order, like a scanning capture); order="shuffled" interleaves all points.
+    `stray` extra records fall outside the window (before t0, after the last
+    bin, or on a wall index past the grid) and must be dropped by a binner.
+    """
+    c = np.asarray(counts)
+    nx, ny, nt = c.shape
+    flat = np.rint(c.reshape(-1)).astype(np.int64)
+    idx = np.repeat(np.arange(flat.size, dtype=np.int64), flat)
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    pixel = idx // nt
+    ticks = t0 + (idx % nt) * ticks_per_bin + rng.integers(0, ticks_per_bin, size=idx.size)
+    if stray:
+        k = np.arange(stray)
+        sp = rng.integers(0, nx * ny, size=stray)
+        st = np.where(k % 3 == 0, rng.integers(0, t0, size=stray),
+                      t0 + nt * ticks_per_bin + rng.integers(0, 4 * ticks_per_bin, size=stray))
+        sp = np.where(k % 3 == 2, nx * ny + rng.integers(0, 64, size=stray), sp)
+        st = np.where(k % 3 == 2, t0 + rng.integers(0, nt * ticks_per_bin, size=stray), st)
+        pixel = np.concatenate([pixel, sp])
+        ticks = np.concatenate([ticks, st])
+    if order == "shuffled":
+        perm = rng.permutation(pixel.size)
+    else:
+        perm = np.lexsort((rng.random(pixel.size), pixel))
+    return PhotonStream(pixel=pixel[perm].astype(np.uint32), ticks=ticks[perm].astype(np.uint32),
+                        t0=int(t0), ticks_per_bin=int(ticks_per_bin))
+
+
+def photon_frame(capture: Capture, n_photons: int, *, seed: int = 0, ticks_per_bin: int = 16,
+                 order: str = "scan") -> PhotonStream:
+    """About n_photons records drawn from a capture's expected counts (signal
+    + the 0.5-count background, rescaled to the requested total)."""
+    e = capture.expected
+    e = e.cpu().numpy() if hasattr(e, "cpu") else e
+    lam = np.asarray(e, dtype=np.float64) + 0.5
+    lam = lam * (n_photons / lam.sum())
+    rng = np.random.Generator(np.random.PCG64(seed + 15485863))
+    return photons_from_counts(rng.poisson(lam), ticks_per_bin=ticks_per_bin, seed=seed, order=order)
