@@ -400,6 +400,145 @@ def pf_bench(torch, nlos, synth, steps=200, with_oracle=True):
     return out
 
 
+def _event_ms(torch, fn, reps):
+    """Mean CUDA-event milliseconds of fn() over reps calls on the current stream."""
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def binning_bench(torch, nlos, synth, reps=20):
+    """Photon binning on the 128 x 128 x 1024 phasor-field grid: frames of
+    1.2M photons (the size of a dynamic-capture frame), 20M and 100M (the
+    20M frame oversampled 5x), records resident on the device; plus the
+    streaming frame (pinned records -> device, phasors, reconstruction,
+    volume -> host)."""
+    import numpy as np
+    cap = synth.make_capture("pf_128x128x1024", 0, device="cuda", noise=False)
+    g = cap.geometry
+    plan = nlos.plan_for_capture(g, "pf", n_depths=128, depth_min_m=0.5, depth_max_m=2.5)
+    plan.autotune()
+    out = {"grid": [g.nx, g.ny, g.nt], "band_frequencies": plan.band[1], "record_bytes": 8,
+           "order": "scan (wall points in turn, photons of a point in random time order)"}
+    base = synth.photon_frame(cap, 20_000_000, seed=2)
+    small = synth.photon_frame(cap, 1_200_000, seed=1)
+    frames = {"1.2M": (small.pixel, small.ticks), "20M": (base.pixel, base.ticks),
+              "100M": (np.tile(base.pixel, 5), np.tile(base.ticks, 5))}
+    P = plan.empty_phasors()
+    H = torch.empty((g.nx, g.ny, g.nt), dtype=torch.float32, device="cuda")
+    for name, (px_h, tk_h) in frames.items():
+        px, tk = torch.from_numpy(px_h).cuda(), torch.from_numpy(tk_h).cuda()
+        n = px.numel()
+        r = max(3, reps if n < 50_000_000 else reps // 4)
+        ms_p = _event_ms(torch, lambda: plan.bin_phasors(px, tk, base.t0, base.ticks_per_bin, phasors=P), r)
+        ms_h = _event_ms(torch, lambda: nlos.bin_transient(px, tk, g.nx, g.ny, g.nt, base.t0, base.ticks_per_bin,
+                                                           transient=H), r)
+        out[name] = {"photons": n, "phasor_ms": ms_p, "phasor_photons_per_s": n / (ms_p * 1e-3),
+                     "transient_ms": ms_h, "transient_photons_per_s": n / (ms_h * 1e-3),
+                     "record_read_gbs_phasor": 8 * n / (ms_p * 1e-3) / 1e9}
+        del px, tk
+    # streaming frame through the public calls: pinned records in, volume out
+    px_h = torch.from_numpy(small.pixel).pin_memory()
+    tk_h = torch.from_numpy(small.ticks).pin_memory()
+    px = torch.empty_like(px_h, device="cuda")
+    tk = torch.empty_like(tk_h, device="cuda")
+    vol = plan.empty_volume()
+    vol_h = torch.empty(vol.shape, dtype=vol.dtype).pin_memory()
+
+    def frame():
+        px.copy_(px_h, non_blocking=True)
+        tk.copy_(tk_h, non_blocking=True)
+        plan.bin_phasors(px, tk, small.t0, small.ticks_per_bin, phasors=P)
+        plan.reconstruct_phasors(P, vol)
+        vol_h.copy_(vol, non_blocking=True)
+    ms_f = _event_ms(torch, frame, reps * 5)
+    out["stream_frame_1.2M"] = {"ms_per_frame": ms_f, "frames_per_s": 1e3 / ms_f,
+                                "h2d_bytes": 8 * px_h.numel(), "d2h_bytes": vol_h.numel() * 4,
+                                "path": "pinned records -> nlos_bin_phasors -> nlos_reconstruct_phasors -> pinned volume"}
+    return out
+
+
+def post_bench(torch, nlos, synth, reps=50):
+    """Post-processing kernels on 256 x 256 x 512 volumes (HBM-bound):
+    max image, coherence merge and depth-dependent average over N_w = 4
+    frames; the mixture of experts of two 256 x 256 images (one CTA)."""
+    peaks, _ = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    g = synth.WORKLOADS["fk_256x256x512"]["geom"]
+    shape = (g.nx, g.ny, g.nt)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    vols = [torch.rand(shape, device="cuda", generator=gen) for _ in range(4)]
+    cplx = [torch.complex(torch.rand(shape, device="cuda", generator=gen), torch.rand(shape, device="cuda", generator=gen))
+            for _ in range(4)]
+    img = torch.empty(shape[:2], device="cuda")
+    merged = torch.empty(shape, device="cuda")
+    coh = torch.empty(shape, device="cuda")
+    dda_out = torch.empty(shape, device="cuda")
+    V = g.nx * g.ny * g.nt
+    out = {"grid": list(shape), "n_w": 4}
+    cases = {
+        "max_image": (lambda: nlos.max_image(vols[0], image=img), 4 * V + 4 * g.nx * g.ny),
+        "coherence_merge": (lambda: nlos.coherence_merge(cplx, merged=merged, coherence=coh), 4 * 8 * V + 2 * 4 * V),
+        "dda": (lambda: nlos.dda(vols, out=dda_out), sum(4 * V * min(4, 1 + (4 * z) // g.nt) for z in range(g.nt)) // g.nt + 4 * V),
+    }
+    for name, (fn, nbytes) in cases.items():
+        ms = _event_ms(torch, fn, reps)
+        out[name] = {"ms": ms, "bytes": nbytes, "achieved_gbs": nbytes / (ms * 1e-3) / 1e9,
+                     "frac": nbytes / (ms * 1e-3) / 1e9 / peak}
+    a, b = torch.rand((g.nx, g.ny), device="cuda"), torch.rand((g.nx, g.ny), device="cuda")
+    mix = torch.empty_like(a)
+    out["moe_mix_256x256_ms"] = _event_ms(torch, lambda: nlos.moe_mix(a, b, out=mix), reps)
+    return out
+
+
+def moe_bench(torch, nlos, synth, reps=20):
+    """Mixture of experts (Eq. 10) on the 128 x 128 x 1024 capture: f-k and
+    phasor-field reconstructions of one transient, their images and the mix;
+    the two branches one after the other and on two streams."""
+    cap = synth.make_capture("pf_128x128x1024", 0, device="cuda")
+    g = cap.geometry
+    fk = nlos.plan_for_capture(g, "fk")
+    pf = nlos.plan_for_capture(g, "pf", n_depths=128, depth_min_m=0.5, depth_max_m=2.5)
+    fk.autotune()
+    pf.autotune()
+    x = torch.as_tensor(cap.counts, dtype=torch.float32).cuda()
+    vf, vp = fk.empty_volume(), pf.empty_volume()
+    i_f = torch.empty((g.nx, g.ny), device="cuda")
+    i_p = torch.empty_like(i_f)
+    mix = torch.empty_like(i_f)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def serial():
+        fk.reconstruct(x, vf)
+        nlos.max_image(vf, take_sqrt=True, image=i_f)
+        pf.reconstruct(x, vp)
+        nlos.max_image(vp, image=i_p)
+        nlos.moe_mix(i_f, i_p, out=mix)
+
+    def concurrent():
+        cur = torch.cuda.current_stream()
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            fk.reconstruct(x, vf)
+            nlos.max_image(vf, take_sqrt=True, image=i_f)
+        with torch.cuda.stream(s2):
+            pf.reconstruct(x, vp)
+            nlos.max_image(vp, image=i_p)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+        nlos.moe_mix(i_f, i_p, out=mix)
+    return {"grid": [g.nx, g.ny, g.nt], "serial_ms": _event_ms(torch, serial, reps),
+            "two_streams_ms": _event_ms(torch, concurrent, reps)}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -554,7 +693,8 @@ def main():
     extras = {}
     if world == 1 and not args.no_extras and not args.grid:
         for name, fn in (("batch", batch_bench), ("serving", serving_bench),
-                         ("phasor_field", lambda t, n, sy: pf_bench(t, n, sy, with_oracle=not args.no_cpu_baseline))):
+                         ("phasor_field", lambda t, n, sy: pf_bench(t, n, sy, with_oracle=not args.no_cpu_baseline)),
+                         ("binning", binning_bench), ("post", post_bench), ("moe", moe_bench)):
             try:
                 extras[name] = fn(torch, nlos, synth)
             except Exception as exc:     # report, do not lose the headline line
@@ -599,6 +739,9 @@ def main():
         "batch": extras.get("batch"),
         "serving": extras.get("serving"),
         "phasor_field": extras.get("phasor_field"),
+        "binning": extras.get("binning"),
+        "post": extras.get("post"),
+        "moe": extras.get("moe"),
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": Ke,
                 "h2d_bytes_per_step": plan.input_bytes, "d2h_bytes_per_step": plan.output_bytes,
                 "path": "nlos_reconstruct_host, pinned host buffers"},

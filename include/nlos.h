@@ -289,6 +289,53 @@ nlos_status_t nlos_plan_stage_times(nlos_plan_t plan, double* times_ms, int capa
 const char* nlos_plan_stage_name(nlos_plan_t plan, int stage);
 
 /*
+ * Photon binning (Sec. 4.1). A SPAD stream is `count` photon records given as
+ * two device arrays: pixel[i], the wall index x * ny + y of the point the
+ * photon was detected at, and ticks[i], its time of flight in integer clock
+ * ticks. The record's bin is (ticks - t0_ticks) / ticks_per_bin (integer
+ * division); records with ticks < t0_ticks, bin >= nt or pixel >= nx * ny are
+ * dropped. With accumulate == 0 the output is cleared first, otherwise the
+ * photons are added to it (streaming several batches into one frame).
+ * Asynchronous on stream; allocates nothing. Errors: INVALID_ARG (NULL
+ * output, NULL records with count > 0, count < 0, ticks_per_bin == 0).
+ *
+ * nlos_bin_transient: transient[x][y][t] (float32, nx * ny * nt) += 1 per
+ *   kept photon: the histogram H consumed by nlos_reconstruct. Counts are
+ *   exact up to 2^24 per bin.
+ */
+nlos_status_t nlos_bin_transient(const uint32_t* pixel, const uint32_t* ticks, long long count, int nx, int ny,
+                                 int nt, uint32_t t0_ticks, uint32_t ticks_per_bin, int accumulate,
+                                 float* transient, void* stream);
+
+/*
+ * nlos_bin_phasors: photons of a phasor-field plan's grid (nx, ny, nt)
+ *   accumulated directly into its compact phasor field, skipping the
+ *   histogram: phasors[x][y][f] (interleaved float32 complex, nx * ny * F
+ *   values, F from nlos_plan_band) += w(f) exp(-2 pi i k_f b / nt) for a
+ *   photon in bin b, with k_f = k_lo + f the band bins and w(f) the
+ *   virtual-wave weights of the plan (Sec. 3.1). This equals w(f) times the
+ *   temporal DFT of the binned histogram at the band bins.
+ *   Errors: as above, and INVALID_ARG for a plan that is not phasor-field.
+ */
+nlos_status_t nlos_bin_phasors(nlos_plan_t plan, const uint32_t* pixel, const uint32_t* ticks, long long count,
+                               uint32_t t0_ticks, uint32_t ticks_per_bin, int accumulate, void* phasors,
+                               void* stream);
+
+/* Band of a phasor-field plan: first DFT bin k_lo and count F of the band
+ * frequencies (either pointer may be NULL). INVALID_ARG for f-k plans. */
+nlos_status_t nlos_plan_band(nlos_plan_t plan, int* k_lo, int* n_freqs);
+
+/*
+ * Reconstruct from a compact phasor field (Alg. 4 from its spatial
+ * transforms on; the band transform of the transient is skipped): phasors
+ * as written by nlos_bin_phasors, device, [x][y][F] complex float32. Uses the
+ * plan's workspace; asynchronous on stream. Errors: INVALID_ARG (NULL
+ * pointers, f-k plan, plan without workspace), UNSUPPORTED (16-bit storage
+ * plans: the phasor input is float32).
+ */
+nlos_status_t nlos_reconstruct_phasors(nlos_plan_t plan, const void* phasors, void* volume, void* stream);
+
+/*
  * Post-processing of reconstructed volumes. All pointers are device memory
  * owned by the caller; volumes are [nx][ny][nz] with depth innermost; every
  * call is asynchronous on stream and allocates nothing. Errors: INVALID_ARG

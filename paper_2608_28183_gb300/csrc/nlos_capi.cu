@@ -113,6 +113,7 @@ struct nlos_plan_s {
   // phasor-field tables
   int F = 0, D = 0, k_lo = 0, nchunks = 0, kr_storage = kF32;
   float* w = nullptr;
+  float2* phase = nullptr;              // [n] exp(-2 pi i m / n) for photon binning
   void* Kr = nullptr;
   int2* ch_i01 = nullptr;
   int* ch_pix = nullptr;
@@ -396,6 +397,12 @@ nlos_status_t build_pf(nlos_plan_s* p) {
     if ((st = upload(p, &p->ch_acut, cc, "chunk table")) != NLOS_OK) return st;
   }
   if ((st = upload(p, &p->w, w, "band weights")) != NLOS_OK) return st;
+  std::vector<float2> phase(p->n);
+  for (int m = 0; m < p->n; ++m) {
+    const double t = 2.0 * kPi * m / p->n;
+    phase[m] = make_float2((float)cos(t), (float)-sin(t));
+  }
+  if ((st = upload(p, &p->phase, phase, "phase table")) != NLOS_OK) return st;
   if ((st = ensure_twiddles(p, p->n)) != NLOS_OK) return st;
   if ((st = ensure_twiddles(p, Nu)) != NLOS_OK) return st;
   if ((st = ensure_twiddles(p, Nv)) != NLOS_OK) return st;
@@ -591,7 +598,9 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   return NLOS_OK;
 }
 
-nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStream_t s) {
+// H: the transient; or, when P_in is given (float32 plans only), the band
+// transform is skipped and P_in is the compact phasor field [x][y][F].
+nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol, char* ws, cudaStream_t s) {
   const int st = p->storage;
   const long long a = p->a, b = p->b, n = p->n, F = p->F, D = p->D;
   void* b0 = ws + p->off[0];
@@ -603,7 +612,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   const float* inv_s = nullptr;
   int sid = 0;
   NLOS_MARK(p, s, -1);
-  if (st != kF32) {
+  if (st != kF32 && !P_in) {
     NLOS_CU(launch_volume_scale(H, a * b * n, (int)n, 0.0f, st, kVolumeTarget,
                                 reinterpret_cast<float*>(ws + p->off_part), kScalePartials, scal, s),
             "volume scale");
@@ -629,10 +638,11 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   bp.ld_scale = 1.0f;
   bp.ld_dev_scale = s_in;
   bp.st_scale = gn;
-  NLOS_CU(launch_pf_band(bp, st, s), "pf band transform");
+  if (!P_in) NLOS_CU(launch_pf_band(bp, st, s), "pf band transform");
   NLOS_MARK(p, s, sid++);
   // PF2: top-left padding and 2D forward transform (y then x) of every band slice
-  AxisLaunch l = axis(st, 2 * b, a, b0, b1, F, b * F, F, 2 * b * F, F, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
+  const void* P = P_in ? P_in : b0;
+  AxisLaunch l = axis(st, 2 * b, a, P, b1, F, b * F, F, 2 * b * F, F, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf y-forward");
@@ -683,7 +693,7 @@ nlos_status_t run_plan(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaS
   // (the runtime is shared with the host application) must not be reported
   // against this sequence's launches
   cudaGetLastError();
-  return p->d.method == NLOS_FK ? run_fk(p, H, vol, w, s) : run_pf(p, H, vol, w, s);
+  return p->d.method == NLOS_FK ? run_fk(p, H, vol, w, s) : run_pf(p, H, nullptr, vol, w, s);
 }
 
 std::mutex g_pool_mu;
@@ -829,6 +839,53 @@ nlos_status_t nlos_reconstruct(nlos_plan_t p, const void* transient, void* volum
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
   if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace; use nlos_reconstruct_ws");
   return nlos_reconstruct_ws(p, transient, volume, p->ws, p->ws_bytes, stream);
+}
+
+nlos_status_t nlos_plan_band(nlos_plan_t p, int* k_lo, int* n_freqs) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (p->d.method != NLOS_PHASOR_RSD) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
+  if (k_lo) *k_lo = p->k_lo;
+  if (n_freqs) *n_freqs = p->F;
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_bin_phasors(nlos_plan_t p, const uint32_t* pixel, const uint32_t* ticks, long long count,
+                               uint32_t t0_ticks, uint32_t ticks_per_bin, int accumulate, void* phasors,
+                               void* stream) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (p->d.method != NLOS_PHASOR_RSD) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
+  if (!phasors || count < 0 || (count > 0 && (!pixel || !ticks)) || ticks_per_bin == 0)
+    return fail(NLOS_ERR_INVALID_ARG, "bad binning arguments");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaGetLastError();
+  if (!accumulate) NLOS_CU(cudaMemsetAsync(phasors, 0, sizeof(float2) * (size_t)p->a * p->b * p->F, s), "phasor clear");
+  if (count == 0) return NLOS_OK;
+  PhasorBinParams q{};
+  q.pixel = pixel;
+  q.ticks = ticks;
+  q.count = count;
+  q.npix = (uint32_t)((long long)p->a * p->b);
+  q.nt = p->n;
+  q.n = p->n;
+  q.t0 = t0_ticks;
+  q.tpb = ticks_per_bin;
+  q.phase = p->phase;
+  q.w = p->w;
+  q.k_lo = p->k_lo;
+  q.F = p->F;
+  q.P = static_cast<float2*>(phasors);
+  NLOS_CU(launch_bin_phasors(q, s), "phasor binning");
+  return NLOS_OK;
+}
+
+nlos_status_t nlos_reconstruct_phasors(nlos_plan_t p, const void* phasors, void* volume, void* stream) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (p->d.method != NLOS_PHASOR_RSD) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
+  if (p->storage != kF32) return fail(NLOS_ERR_UNSUPPORTED, "phasor input needs a float32 plan");
+  if (!phasors || !volume) return fail(NLOS_ERR_INVALID_ARG, "phasors/volume is NULL");
+  if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace");
+  cudaGetLastError();
+  return run_pf(p, nullptr, phasors, volume, static_cast<char*>(p->ws), static_cast<cudaStream_t>(stream));
 }
 
 nlos_status_t nlos_reconstruct_host(nlos_plan_t p, const void* th, void* vh, void* stream) {

@@ -104,6 +104,22 @@ struct PfBandParams {
 };
 cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s);
 
+// Photon binning into the compact phasor field P[pixel][f] (float32 complex):
+// P += w_f * exp(-2 pi i (k_lo + f) b / n) per kept photon.
+struct PhasorBinParams {
+  const uint32_t* pixel;
+  const uint32_t* ticks;
+  long long count;
+  uint32_t npix;
+  int nt, n;                   // time bins; phase table length (n == nt)
+  uint32_t t0, tpb;
+  const float2* phase;         // [n] exp(-2 pi i m / n)
+  const float* w;              // [F]
+  int k_lo, F;
+  float2* P;
+};
+cudaError_t launch_bin_phasors(const PhasorBinParams& q, cudaStream_t s);
+
 // Phasor-field depth sum over pixel chunks sharing a radial index i0:
 // C[pix][d] = acut * sum_f Phat[pix][f] * ((1 - alpha) K[i0][f][d] + alpha K[i1][f][d]).
 constexpr int kPfChunk = 16;

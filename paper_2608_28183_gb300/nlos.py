@@ -29,7 +29,8 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_batch_create", "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex",
             "nlos_server_create", "nlos_server_preload", "nlos_server_submit", "nlos_server_wait",
             "nlos_server_stats", "nlos_server_destroy", "nlos_workspace_check", "nlos_selftest_bounded_wait",
-            "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda"]
+            "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
+            "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -102,7 +103,14 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_moe_mix.argtypes = [vp, vp, ll, fl, fl, vp, vp]
     lib.nlos_coherence_merge.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ll, fl, vp, vp, vp]
     lib.nlos_dda.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ll, ctypes.c_int, vp, vp]
-    for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda"):
+    u32 = ctypes.c_uint32
+    lib.nlos_bin_transient.argtypes = [vp, vp, ll, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32, u32, ctypes.c_int,
+                                       vp, vp]
+    lib.nlos_bin_phasors.argtypes = [vp, vp, vp, ll, u32, u32, ctypes.c_int, vp, vp]
+    lib.nlos_plan_band.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.nlos_reconstruct_phasors.argtypes = [vp, vp, vp, vp]
+    for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda", "nlos_bin_transient",
+                 "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles", "nlos_batch_create",
                  "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex", "nlos_server_create",
@@ -236,6 +244,43 @@ class Plan:
             return ctypes.c_void_p(x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data)
         _check(_lib.nlos_reconstruct_host(self._h, ptr(transient_host), ptr(volume_host), _stream_ptr(stream)))
         return volume_host
+
+    @property
+    def band(self):
+        """(k_lo, F): first DFT bin and number of band frequencies (phasor-field plans)."""
+        k, f = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.nlos_plan_band(self._h, ctypes.byref(k), ctypes.byref(f)))
+        return k.value, f.value
+
+    def empty_phasors(self):
+        import torch
+        d = self.desc
+        return torch.empty((d.nx, d.ny, self.band[1]), dtype=torch.complex64, device="cuda")
+
+    def bin_phasors(self, pixel, ticks, t0_ticks: int, ticks_per_bin: int, phasors=None, accumulate=False,
+                    stream=None):
+        """Accumulate photon records straight into the compact phasor field [nx, ny, F]."""
+        _check_photons(pixel, ticks)
+        if phasors is None:
+            phasors = self.empty_phasors()
+        d = self.desc
+        if phasors.dtype != _torch().complex64 or not phasors.is_contiguous() \
+                or tuple(phasors.shape) != (d.nx, d.ny, self.band[1]):
+            raise ValueError("phasors must be contiguous complex64 [nx, ny, F]")
+        _check(_lib.nlos_bin_phasors(self._h, ctypes.c_void_p(pixel.data_ptr()), ctypes.c_void_p(ticks.data_ptr()),
+                                     pixel.numel(), t0_ticks, ticks_per_bin, int(bool(accumulate)),
+                                     ctypes.c_void_p(phasors.data_ptr()), _stream_ptr(stream)))
+        return phasors
+
+    def reconstruct_phasors(self, phasors, volume=None, stream=None):
+        """Reconstruct from a compact phasor field (the band transform is skipped)."""
+        if volume is None:
+            volume = self.empty_volume()
+        if volume.dtype != self.output_dtype() or not volume.is_contiguous() or tuple(volume.shape) != self.out_shape:
+            raise ValueError(f"volume must be contiguous {self.output_dtype()} {list(self.out_shape)}")
+        _check(_lib.nlos_reconstruct_phasors(self._h, ctypes.c_void_p(phasors.data_ptr()),
+                                             ctypes.c_void_p(volume.data_ptr()), _stream_ptr(stream)))
+        return volume
 
     def set_profiling(self, enable: bool):
         """Record a CUDA event after every stage of each reconstruction."""
@@ -459,3 +504,38 @@ def dda(frames, out=None, stream=None):
     _check(_lib.nlos_dda(F, len(frames), frames[0].numel() // shape[-1], shape[-1],
                          ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Photon binning (Sec. 4.1)
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _check_photons(pixel, ticks):
+    torch = _torch()
+    for x, name in ((pixel, "pixel"), (ticks, "ticks")):
+        if not x.is_cuda or x.dtype != torch.uint32 or not x.is_contiguous() or x.dim() != 1:
+            raise ValueError(f"{name} must be a contiguous 1-D CUDA uint32 tensor")
+    if pixel.numel() != ticks.numel():
+        raise ValueError("pixel and ticks must have one length")
+
+
+def bin_transient(pixel, ticks, nx: int, ny: int, nt: int, t0_ticks: int, ticks_per_bin: int, transient=None,
+                  accumulate: bool = False, stream=None):
+    """Histogram photon records into a float32 transient [nx, ny, nt] on the device."""
+    torch = _torch()
+    load_library()
+    _check_photons(pixel, ticks)
+    if transient is None:
+        transient = torch.empty((nx, ny, nt), dtype=torch.float32, device=pixel.device)
+    _dev_f32(transient, "transient")
+    if tuple(transient.shape) != (nx, ny, nt):
+        raise ValueError("transient must be [nx, ny, nt]")
+    _check(_lib.nlos_bin_transient(ctypes.c_void_p(pixel.data_ptr()), ctypes.c_void_p(ticks.data_ptr()),
+                                   pixel.numel(), nx, ny, nt, t0_ticks, ticks_per_bin, int(bool(accumulate)),
+                                   ctypes.c_void_p(transient.data_ptr()), _stream_ptr(stream)))
+    return transient

@@ -72,5 +72,9 @@ def test_null_arguments(lib):
     assert lib.nlos_moe_mix(None, None, 10, 0.3, 1e-3, None, None) == 1
     assert lib.nlos_coherence_merge(None, 2, 10, 1e-6, None, None, None) == 1
     assert lib.nlos_dda(None, 2, 10, 4, None, None) == 1
+    assert lib.nlos_bin_transient(None, None, 10, 4, 4, 16, 0, 1, 0, None, None) == 1
+    assert lib.nlos_bin_phasors(None, None, None, 10, 0, 1, 0, None, None) == 1
+    assert lib.nlos_plan_band(None, None, None) == 1
+    assert lib.nlos_reconstruct_phasors(None, None, None, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, -1, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, 0, None) == 0
