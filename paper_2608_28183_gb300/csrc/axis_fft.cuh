@@ -167,14 +167,6 @@ cudaError_t launch_axis_pair_ic(const AxisLaunch& l, cudaStream_t s) {
   return axis_report("realpair", L, IC, Tile::THREADS, smem, grid.x, grid.y, cudaGetLastError());
 }
 
-template <int L, class TS, bool kHalfIn>
-cudaError_t launch_axis_pair(const AxisLaunch& l, cudaStream_t s) {
-  const int v = (l.tile >= 0 && l.tile < axis_tile_count(L)) ? l.tile % axis_ic_count(L) : 0;
-  if (v == 0) return launch_axis_pair_ic<L, axis_ic(L, 0), TS, kHalfIn>(l, s);
-  if (v == 1) return launch_axis_pair_ic<L, axis_ic(L, 1), TS, kHalfIn>(l, s);
-  return launch_axis_pair_ic<L, axis_ic(L, 2), TS, kHalfIn>(l, s);
-}
-
 template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 __global__ void __launch_bounds__(AxisTile<L, IC>::THREADS)
 axis_fft_kernel(const AxisParams p) {
@@ -276,6 +268,10 @@ axis_fft_tma_kernel(const __grid_constant__ CUtensorMap tmap, const AxisParams p
     if (threadIdx.x == 0 && next < ntiles) issue(next, slot ^ 1);
     if (!mbar_wait_bounded(&bar[slot], (k >> 1) & 1, kTmaWaitLimit)) {
       if (err) atomicExch(err, kDevErrTmaTimeout);
+      // give the copies still in flight into this CTA's buffers a last
+      // bounded chance to land before the CTA exits
+      mbar_wait_bounded(&bar[slot], (k >> 1) & 1, kTmaWaitLimit);
+      if (next < ntiles) mbar_wait_bounded(&bar[slot ^ 1], ((k + 1) >> 1) & 1, kTmaWaitLimit);
       return;
     }
     const int ti = (int)(tile % tiles_inner);
@@ -326,6 +322,145 @@ cudaError_t launch_axis_tma(const AxisLaunch& l, cudaStream_t s) {
   const long long grid = std::min<long long>(ntiles, (long long)sms * blocks_per_sm);
   k<<<(unsigned)grid, T::THREADS, T::SMEM, s>>>(l.tmap, l.p, tiles_inner, ntiles, l.err);
   return axis_report("tma", L, IC, T::THREADS, T::SMEM, grid, ntiles, cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged real pairs: the persistent double-buffered loop of the TMA
+// kernel above with tiles of 2*IC real columns; columns c and c + IC ride as
+// the real and imaginary parts of one transform and are split after it, as
+// in axis_fft_realpair_kernel.
+// ---------------------------------------------------------------------------
+template <int L, int IC, class TS>
+struct AxisTmaPairCtx {
+  using TR = typename RealOf<TS>::T;
+  static constexpr int SSTRIDE = IC;
+  static constexpr bool kSmemInput = true;
+  const TR* tile;       // staged tile, [row][2 IC] reals
+  float2* smem;
+  const float2* tw;
+  int L_in, c;
+  float m0, m1;
+  __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
+    x[0] = make_float2(0.f, 0.f);
+    if (l >= L_in) return;
+    x[0].x = Real<TR>::get(tile + l * (2 * IC) + c) * m0;
+    x[0].y = Real<TR>::get(tile + l * (2 * IC) + IC + c) * m1;
+  }
+  __device__ __forceinline__ float2* sm(int) const { return smem + c; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { smem[pad16(l) * IC + c] = x[0]; }
+};
+
+template <int L, int IC, class TS, bool kHalfIn>
+__global__ void __launch_bounds__(AxisTile<L, IC>::THREADS)
+axis_fft_tma_pair_kernel(const __grid_constant__ CUtensorMap tmap, const AxisParams p, const int tiles_inner,
+                         const long long ntiles, int* err) {
+  using TR = typename RealOf<TS>::T;
+  constexpr size_t BUF = sizeof(float2) * FftShape<L>::SMEM * IC;
+  constexpr int TPC = L / 16;
+  extern __shared__ __align__(128) unsigned char tp_sm[];
+  auto buf = [&](int slot) { return reinterpret_cast<float2*>(tp_sm + slot * BUF); };
+  uint64_t* bar = reinterpret_cast<uint64_t*>(tp_sm + 2 * BUF);
+  const int c = threadIdx.x % IC;
+  const int j0 = threadIdx.x / IC;
+  const int rows = p.L_in;
+  const uint32_t tile_bytes = (uint32_t)(rows * 2 * IC * sizeof(TR));
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](long long tile, int slot) {
+    const int ti = (int)(tile % tiles_inner);
+    const int to = (int)(tile / tiles_inner);
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&bar[slot], tile_bytes);
+    for (int r0 = 0; r0 < rows; r0 += 256)
+      tma_load_3d(reinterpret_cast<unsigned char*>(buf(slot)) + (size_t)r0 * 2 * IC * sizeof(TR), &tmap, &bar[slot],
+                  ti * 2 * IC, r0, to);
+  };
+  long long tile = blockIdx.x;
+  if (threadIdx.x == 0 && tile < ntiles) issue(tile, 0);
+  const float ldmul = p.ld_dev_scale ? *p.ld_dev_scale : 1.0f;
+  const float h = 0.5f * p.scale * (p.st_dev_scale ? *p.st_dev_scale : 1.0f);
+  TS* out = static_cast<TS*>(p.out);
+  for (int k = 0; tile < ntiles; ++k, tile += gridDim.x) {
+    const int slot = k & 1;
+    const long long next = tile + gridDim.x;
+    if (threadIdx.x == 0 && next < ntiles) issue(next, slot ^ 1);
+    if (!mbar_wait_bounded(&bar[slot], (k >> 1) & 1, kTmaWaitLimit)) {
+      if (err) atomicExch(err, kDevErrTmaTimeout);
+      // give the copies still in flight into this CTA's buffers a last
+      // bounded chance to land before the CTA exits
+      mbar_wait_bounded(&bar[slot], (k >> 1) & 1, kTmaWaitLimit);
+      if (next < ntiles) mbar_wait_bounded(&bar[slot ^ 1], ((k + 1) >> 1) & 1, kTmaWaitLimit);
+      return;
+    }
+    const int ti = (int)(tile % tiles_inner);
+    const long long outer = tile / tiles_inner;
+    const long long ii0 = (long long)ti * (2 * IC) + c;
+    const long long ii1 = ii0 + IC;
+    AxisTmaPairCtx<L, IC, TS> ctx;
+    ctx.tile = reinterpret_cast<const TR*>(buf(slot));
+    ctx.smem = buf(slot);
+    ctx.tw = p.tw;
+    ctx.L_in = rows;
+    ctx.c = c;
+    ctx.m0 = ldmul * (p.t_len > 0 ? (float)(int)(ii0 % p.t_len) * p.t_scale : 1.0f);
+    ctx.m1 = ldmul * (p.t_len > 0 ? (float)(int)(ii1 % p.t_len) * p.t_scale : 1.0f);
+    fftn_run<L, 1, kHalfIn, false>(ctx, j0);
+    __syncthreads();
+    const float2* z = buf(slot);
+    const bool v0 = ii0 < p.inner, v1 = ii1 < p.inner;
+    for (int q = j0; q < p.L_out; q += TPC) {
+      const float2 zk = z[pad16(q) * IC + c];
+      const float2 zm = z[pad16((L - q) & (L - 1)) * IC + c];
+      if (v0) Cpx<TS>::put(out + outer * p.out_outer + ii0 + q * p.out_axis, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
+      if (v1) Cpx<TS>::put(out + outer * p.out_outer + ii1 + q * p.out_axis, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
+    }
+    __syncthreads();   // the buffer is free before the next issue into it
+  }
+}
+
+template <int L, int IC, class TS, bool kHalfIn>
+cudaError_t launch_axis_tma_pair(const AxisLaunch& l, cudaStream_t s) {
+  constexpr size_t BUF = sizeof(float2) * FftShape<L>::SMEM * IC;
+  constexpr size_t SMEM = 2 * BUF + 2 * sizeof(uint64_t);
+  constexpr int THREADS = AxisTile<L, IC>::THREADS;
+  auto k = axis_fft_tma_pair_kernel<L, IC, TS, kHalfIn>;
+  static int blocks_per_sm = 0;
+  static int sms = 0;
+  if (blocks_per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k, THREADS, SMEM);
+    if (e != cudaSuccess) return e;
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+  }
+  const int tiles_inner = (int)((l.p.inner + 2 * IC - 1) / (2 * IC));
+  const long long ntiles = (long long)tiles_inner * l.n_outer;
+  const long long grid = std::min<long long>(ntiles, (long long)sms * blocks_per_sm);
+  k<<<(unsigned)grid, THREADS, SMEM, s>>>(l.tmap, l.p, tiles_inner, ntiles, l.err);
+  return axis_report("tma-pair", L, IC, THREADS, SMEM, grid, ntiles, cudaGetLastError());
+}
+
+// real-pair variants: tiles [0, n) direct loads, [2n, 3n) TMA staging (n
+// column widths); tiles [n, 2n) of a real-input stage are single columns
+template <int L, class TS, bool kHalfIn>
+cudaError_t launch_axis_pair(const AxisLaunch& l, cudaStream_t s) {
+  const int nic = axis_ic_count(L);
+  const int v = l.tile >= 0 ? l.tile % nic : 0;
+  if (l.has_tmap && l.tile >= 2 * nic) {
+    if (v == 0) return launch_axis_tma_pair<L, axis_ic(L, 0), TS, kHalfIn>(l, s);
+    if (v == 1) return launch_axis_tma_pair<L, axis_ic(L, 1), TS, kHalfIn>(l, s);
+    return launch_axis_tma_pair<L, axis_ic(L, 2), TS, kHalfIn>(l, s);
+  }
+  if (v == 0) return launch_axis_pair_ic<L, axis_ic(L, 0), TS, kHalfIn>(l, s);
+  if (v == 1) return launch_axis_pair_ic<L, axis_ic(L, 1), TS, kHalfIn>(l, s);
+  return launch_axis_pair_ic<L, axis_ic(L, 2), TS, kHalfIn>(l, s);
 }
 
 template <int L, int IC, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>

@@ -86,11 +86,13 @@ struct FkFwdCtx {
 };
 
 // both inverse transforms at once: t = 0 the stored pencil, t = 1 its
-// Hermitian partner; one Stolt coordinate per m feeds both
-template <int L, class TS>
+// Hermitian partner; one Stolt coordinate per m feeds both. kAliasU: the
+// pencil's transform runs in U's own buffer, so the first pass must finish
+// reading U before it writes (kSmemInput adds that barrier).
+template <int L, class TS, bool kAliasU>
 struct FkInvCtx {
   static constexpr int SSTRIDE = 1;
-  static constexpr bool kSmemInput = false;
+  static constexpr bool kSmemInput = kAliasU;
   const float2* U;
   float2* W0;
   float2* W1;
@@ -130,17 +132,22 @@ __host__ __device__ constexpr int fk_ppc(int L, int v) {
        : (L <= 1024 ? (v == 0 ? 2 : 4) : (v == 0 ? 2 : 1));
 }
 
-template <int L, int PPC_> struct FkTile {
+// kAlias: two shared buffers per pencil instead of three (the pencil's
+// inverse transform reuses the spectrum's buffer) and a register cap of
+// about 100 per thread, so that more CTAs fit on an SM.
+template <int L, int PPC_, bool kAlias = false> struct FkTile {
   static constexpr int PPC = PPC_;   // pencils per CTA
   static constexpr int THREADS = PPC * (L / 16);
-  static constexpr size_t SMEM = sizeof(float2) * 3 * PPC * FftShape<L>::SMEM;
+  static constexpr int NBUF = kAlias ? 2 : 3;
+  static constexpr size_t SMEM = sizeof(float2) * NBUF * PPC * FftShape<L>::SMEM;
+  static constexpr int MIN_BLOCKS = kAlias ? (65536 / (THREADS * 96) > 1 ? 65536 / (THREADS * 96) : 1) : 1;
 };
 
 // kPad2: the temporal axis is zero-padded to L = 2n (the forward input's upper
 // half is zero and only z < n is kept); otherwise L = n and every output is
 // kept. Either way the Stolt source must stay below L/2.
-template <int L, int PPC, class TS, bool kPad2>
-__global__ void __launch_bounds__(FkTile<L, PPC>::THREADS)
+template <int L, int PPC, class TS, bool kPad2, bool kAlias>
+__global__ void __launch_bounds__(FkTile<L, PPC, kAlias>::THREADS, FkTile<L, PPC, kAlias>::MIN_BLOCKS)
 fk_zstage_kernel(const FkZParams p) {
   using S = FftShape<L>;
   extern __shared__ float2 fk_sm[];
@@ -152,8 +159,8 @@ fk_zstage_kernel(const FkZParams p) {
   const int kx = valid ? (int)(pid / twob) : 0;
   const int ky = valid ? (int)(pid % twob) : 0;
   float2* U = fk_sm + w * S::SMEM;
-  float2* W0 = fk_sm + (PPC + w) * S::SMEM;
-  float2* W1 = fk_sm + (2 * PPC + w) * S::SMEM;
+  float2* W0 = kAlias ? U : fk_sm + (PPC + w) * S::SMEM;
+  float2* W1 = fk_sm + ((kAlias ? 1 : 2) * PPC + w) * S::SMEM;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
     FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul};
@@ -170,15 +177,15 @@ fk_zstage_kernel(const FkZParams p) {
   const int mky = (twob - ky) & (twob - 1);
   const long long o_mirror = ((long long)mkx * twob + mky) * p.n;
   // the partner is stored only where it is not itself a stored pencil
-  FkInvCtx<L, TS> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, L / 2, A.x, A.y,
+  FkInvCtx<L, TS, kAlias> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, L / 2, A.x, A.y,
                       valid, valid && kx > 0 && 2 * kx < p.a_pad, p.st_scale};
   fftn_run<L, 2, true, kPad2>(ctx, j0);
 }
 
-template <int L, int PPC, class TS>
+template <int L, int PPC, class TS, bool kAlias>
 cudaError_t launch_fk_ppc(const FkZParams& p, cudaStream_t s) {
-  using T = FkTile<L, PPC>;
-  auto k = p.pad == 2 ? fk_zstage_kernel<L, PPC, TS, true> : fk_zstage_kernel<L, PPC, TS, false>;
+  using T = FkTile<L, PPC, kAlias>;
+  auto k = p.pad == 2 ? fk_zstage_kernel<L, PPC, TS, true, kAlias> : fk_zstage_kernel<L, PPC, TS, false, kAlias>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -188,10 +195,15 @@ cudaError_t launch_fk_ppc(const FkZParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// tiles 0/1: the two CTA sizes; 2/3: the same with aliased buffers
 template <int L, class TS>
 cudaError_t launch_fk_one(const FkZParams& p, int tile, cudaStream_t s) {
-  if (tile == 1) return launch_fk_ppc<L, fk_ppc(L, 1), TS>(p, s);
-  return launch_fk_ppc<L, fk_ppc(L, 0), TS>(p, s);
+  switch (tile) {
+    case 1: return launch_fk_ppc<L, fk_ppc(L, 1), TS, false>(p, s);
+    case 2: return launch_fk_ppc<L, fk_ppc(L, 0), TS, true>(p, s);
+    case 3: return launch_fk_ppc<L, fk_ppc(L, 1), TS, true>(p, s);
+    default: return launch_fk_ppc<L, fk_ppc(L, 0), TS, false>(p, s);
+  }
 }
 
 template <class TS>

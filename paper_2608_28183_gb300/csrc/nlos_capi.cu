@@ -132,7 +132,7 @@ struct nlos_plan_s {
   // per-stage tile variant (autotuner) and the transform length it applies to
   std::vector<int> tiles;
   std::vector<int> stage_len;     // 0: stage has no variants
-  std::vector<int> stage_kind;    // 1: strided-axis transform, 2: f-k temporal stage
+  std::vector<int> stage_kind;    // 1: strided-axis transform, 2: f-k temporal stage, 3: real-input axis
   bool tuned = false;
   // stage tracing
   std::vector<std::string> stage_names;
@@ -473,8 +473,9 @@ void attach_tmap(AxisLaunch& l) {
   if (l.tile < nic) return;
   EncodeTiledFn fn = encode_fn();
   if (!fn) return;
-  const size_t elem = l.load_mode == kLoadReal ? real_bytes(l.storage) : complex_bytes(l.storage);
-  const int IC = axis_ic(l.L, l.tile % nic);
+  const bool real_in = l.load_mode == kLoadReal || l.load_mode == kLoadRealPair;
+  const size_t elem = real_in ? real_bytes(l.storage) : complex_bytes(l.storage);
+  const int IC = axis_ic(l.L, l.tile % nic) * (l.load_mode == kLoadRealPair ? 2 : 1);   // columns per box
   const unsigned long long s1 = (unsigned long long)l.p.in_axis * elem;
   const unsigned long long s2 =
       l.n_outer > 1 ? (unsigned long long)l.p.in_outer * elem : (unsigned long long)l.p.L_in * s1;
@@ -544,9 +545,11 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   const float g2a = pass_scale(st, (int)Lx), g2b = pass_scale(st, (int)Ly), g2n = pass_scale(st, (int)Lt);
   // FK1: x forward (real input, scaled by t/(n-1), zero-padded to Lx, kx in [0, Lx/2])
   AxisLaunch l = axis(st, (int)Lx, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)hx, 0, g2a, p->tw[(int)Lx], p->tiles[sid]);
-  // direct variants pack two real columns per complex transform; TMA-staged
-  // variants transform each real column on its own
-  l.load_mode = l.tile < axis_ic_count((int)Lx) ? kLoadRealPair : kLoadReal;
+  // tiles [0, n): direct loads, two real columns per complex transform;
+  // [n, 2n): TMA staging, one real column per transform; [2n, 3n): TMA
+  // staging of column pairs (n column widths)
+  const int nicx = axis_ic_count((int)Lx);
+  l.load_mode = (l.tile < nicx || l.tile >= 2 * nicx) ? kLoadRealPair : kLoadReal;
   l.p.t_len = (int)n;
   l.p.t_scale = 1.0f / (float)(n - 1);
   l.p.ld_dev_scale = s_in;
@@ -784,7 +787,7 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   else for (const char* nm : pf_names) p->stage_names.push_back(nm);
   for (const std::string& nm : p->stage_names) {
     const bool xs = nm.find("_x_") != std::string::npos, ys = nm.find("_y_") != std::string::npos;
-    p->stage_kind.push_back(xs || ys ? 1 : (nm == "fk_stolt_z" ? 2 : 0));
+    p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : (nm == "fk_stolt_z" ? 2 : 0));
     const int pf = desc->method == NLOS_FK ? desc->pad_factor : 2;
     p->stage_len.push_back(xs ? pf * p->a : ys ? pf * p->b : nm == "fk_stolt_z" ? pf * p->n : 0);
   }
@@ -793,7 +796,7 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   // choose others
   p->tiles.assign(p->stage_names.size(), 0);
   for (size_t i = 0; i < p->tiles.size(); ++i)
-    if (p->stage_kind[i] == 1) p->tiles[i] = axis_ic_count(p->stage_len[i]);
+    if (p->stage_kind[i] == 1 || p->stage_kind[i] == 3) p->tiles[i] = axis_ic_count(p->stage_len[i]);
   st = desc->method == NLOS_FK ? build_fk(p) : build_pf(p);
   const bool own_ws = !(flags & NLOS_PLAN_NO_WORKSPACE);
   if (st == NLOS_OK && own_ws) st = dalloc(p, &p->ws, p->ws_bytes, "workspace");
@@ -1009,6 +1012,7 @@ void tune_cache_save() {
 int stage_variants(const nlos_plan_s* p, size_t i) {
   if (p->stage_kind[i] == 1) return axis_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 2) return fk_tile_count(p->stage_len[i]);
+  if (p->stage_kind[i] == 3) return 3 * axis_ic_count(p->stage_len[i]);
   return 1;
 }
 }  // namespace

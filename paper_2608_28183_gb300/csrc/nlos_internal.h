@@ -67,7 +67,7 @@ __host__ __device__ constexpr int axis_tile_count(int L) { return 2 * axis_ic_co
 // error codes written to the device error word
 constexpr int kDevErrTmaTimeout = 1;
 // number of pencils-per-CTA variants of the f-k temporal stage of length L = 2n
-__host__ __device__ constexpr int fk_tile_count(int L) { return 2; }
+__host__ __device__ constexpr int fk_tile_count(int L) { return 4; }
 
 // f-k temporal-frequency stage: forward length-2n FFT of each stored pencil
 // G[kx][ky][0..n) (kx in [0, a], ky in [0, 2b)), Stolt resampling with the

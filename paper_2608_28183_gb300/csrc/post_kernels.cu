@@ -2,6 +2,8 @@
 // the display reduction of Sec. 4.2): max-over-depth images, the mixture of
 // experts of Eq. 10, coherence-weighted merging of Eqs. 8-9 and the
 // depth-dependent average.
+#include <algorithm>
+#include <cstdint>
 #include <cstdio>
 
 #include "nlos.h"
@@ -68,12 +70,22 @@ __global__ void __launch_bounds__(1024) moe_kernel(const float* a, const float* 
 }
 
 constexpr int kMaxFrames = 16;
+// passed as a __grid_constant__ parameter: the per-frame loops index it in
+// the parameter bank instead of copying it to the stack
 struct FramePtrs {
   const void* p[kMaxFrames];
 };
 
 // Eqs. 8-9: C = |sum f| / (eps + sum |f|), merged = C |sum f| / N_w
-__global__ void coherence_kernel(FramePtrs fr, int nw, long long n, float eps, float* merged, float* coh) {
+__device__ __forceinline__ void coherence_one(float sx, float sy, float sa, float eps, float inv_nw, float* m, float* c) {
+  const float s = sqrtf(fmaf(sx, sx, sy * sy));
+  *c = s / (eps + sa);
+  *m = *c * s * inv_nw;
+}
+
+// scalar path: any count and alignment
+__global__ void coherence_kernel(const __grid_constant__ FramePtrs fr, int nw, long long n, float eps, float* merged, float* coh) {
+  const float inv_nw = 1.0f / (float)nw;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     float sx = 0.f, sy = 0.f, sa = 0.f;
     for (int j = 0; j < nw; ++j) {
@@ -82,23 +94,100 @@ __global__ void coherence_kernel(FramePtrs fr, int nw, long long n, float eps, f
       sy += f.y;
       sa += sqrtf(fmaf(f.x, f.x, f.y * f.y));
     }
-    const float s = sqrtf(fmaf(sx, sx, sy * sy));
-    const float c = s / (eps + sa);
-    merged[i] = c * s / (float)nw;
+    float m, c;
+    coherence_one(sx, sy, sa, eps, inv_nw, &m, &c);
+    merged[i] = m;
     if (coh) coh[i] = c;
   }
 }
 
+// vector path: two voxels per thread (one 16-byte load per frame, four
+// frames' loads in flight), for even counts and 16-byte aligned frames
+__global__ void coherence_vec_kernel(const __grid_constant__ FramePtrs fr, int nw, long long n2, float eps, float2* merged, float2* coh) {
+  const float inv_nw = 1.0f / (float)nw;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n2; i += (long long)gridDim.x * blockDim.x) {
+    float ax = 0.f, ay = 0.f, aa = 0.f, bx = 0.f, by = 0.f, ba = 0.f;
+    int j = 0;
+    for (; j + 4 <= nw; j += 4) {
+      float4 f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) f[u] = __ldcs(static_cast<const float4*>(fr.p[j + u]) + i);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ax += f[u].x;
+        ay += f[u].y;
+        aa += sqrtf(fmaf(f[u].x, f[u].x, f[u].y * f[u].y));
+        bx += f[u].z;
+        by += f[u].w;
+        ba += sqrtf(fmaf(f[u].z, f[u].z, f[u].w * f[u].w));
+      }
+    }
+    for (; j < nw; ++j) {
+      const float4 f = __ldcs(static_cast<const float4*>(fr.p[j]) + i);
+      ax += f.x;
+      ay += f.y;
+      aa += sqrtf(fmaf(f.x, f.x, f.y * f.y));
+      bx += f.z;
+      by += f.w;
+      ba += sqrtf(fmaf(f.z, f.z, f.w * f.w));
+    }
+    float2 m, c;
+    coherence_one(ax, ay, aa, eps, inv_nw, &m.x, &c.x);
+    coherence_one(bx, by, ba, eps, inv_nw, &m.y, &c.y);
+    __stcs(merged + i, m);
+    if (coh) __stcs(coh + i, c);
+  }
+}
+
 // depth-dependent average: plane z averages the newest N(z) = min(N_w, 1 + N_w z / n_z) frames
-__global__ void dda_kernel(FramePtrs fr, int nw, long long nxy, int nz, float* out) {
+__device__ __forceinline__ int dda_count(int nw, int z, int nz) { return min(nw, 1 + (int)(((long long)nw * z) / nz)); }
+
+__global__ void dda_kernel(const __grid_constant__ FramePtrs fr, int nw, long long nxy, int nz, float* out) {
   const long long n = nxy * nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int z = (int)(i % nz);
-    const int cnt = min(nw, 1 + (int)(((long long)nw * z) / nz));
+    const int cnt = dda_count(nw, z, nz);
     float s = 0.f;
     for (int j = 0; j < cnt; ++j) s += static_cast<const float*>(fr.p[j])[i];
     out[i] = s / (float)cnt;
   }
+}
+
+// vector path: four consecutive planes per thread (nz a multiple of 4,
+// 16-byte aligned frames); the thread index splits into (pencil, plane
+// quad) with 32-bit arithmetic
+__global__ void dda_vec_kernel(const __grid_constant__ FramePtrs fr, int nw, long long nxy, int nz, float4* out) {
+  const int q = nz / 4;
+  const long long n4 = nxy * q;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    const int z0 = 4 * (int)((unsigned)i % (unsigned)q);       // the host keeps n4 below 2^32
+    int cnt[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) cnt[e] = dda_count(nw, z0 + e, nz);
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int j = 0; j < cnt[3]; ++j) {        // counts grow with z: cnt[3] is the largest
+      const float4 f = __ldcs(static_cast<const float4*>(fr.p[j]) + i);
+      if (j < cnt[0]) s.x += f.x;
+      if (j < cnt[1]) s.y += f.y;
+      if (j < cnt[2]) s.z += f.z;
+      s.w += f.w;
+    }
+    __stcs(out + i, make_float4(s.x / (float)cnt[0], s.y / (float)cnt[1], s.z / (float)cnt[2], s.w / (float)cnt[3]));
+  }
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int grid_for(long long work) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const long long want = (work + 255) / 256;
+  return (int)std::max<long long>(1, std::min<long long>(want, (long long)sms * 8));
 }
 
 nlos_status_t launch_status(const char* what) {
@@ -141,8 +230,15 @@ nlos_status_t nlos_coherence_merge(const void* const* frames, int nw, long long 
     if (!frames[j]) return set_error(NLOS_ERR_INVALID_ARG, "NULL frame");
     fp.p[j] = frames[j];
   }
+  bool vec = count % 2 == 0 && aligned16(merged) && (!coherence || aligned16(coherence));
+  for (int j = 0; j < nw; ++j) vec = vec && aligned16(frames[j]);
   cudaGetLastError();
-  coherence_kernel<<<1024, 256, 0, static_cast<cudaStream_t>(stream)>>>(fp, nw, count, eps, merged, coherence);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (vec)
+    coherence_vec_kernel<<<grid_for(count / 2), 256, 0, s>>>(fp, nw, count / 2, eps, reinterpret_cast<float2*>(merged),
+                                                            reinterpret_cast<float2*>(coherence));
+  else
+    coherence_kernel<<<grid_for(count), 256, 0, s>>>(fp, nw, count, eps, merged, coherence);
   return launch_status("coherence merge");
 }
 
@@ -154,8 +250,14 @@ nlos_status_t nlos_dda(const float* const* frames, int nw, long long nxy, int nz
     if (!frames[j]) return set_error(NLOS_ERR_INVALID_ARG, "NULL frame");
     fp.p[j] = frames[j];
   }
+  bool vec = nz % 4 == 0 && aligned16(out) && nxy * (nz / 4) < (1LL << 32);
+  for (int j = 0; j < nw; ++j) vec = vec && aligned16(frames[j]);
   cudaGetLastError();
-  dda_kernel<<<1024, 256, 0, static_cast<cudaStream_t>(stream)>>>(fp, nw, nxy, nz, out);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (vec)
+    dda_vec_kernel<<<grid_for(nxy * (nz / 4)), 256, 0, s>>>(fp, nw, nxy, nz, reinterpret_cast<float4*>(out));
+  else
+    dda_kernel<<<grid_for(nxy * nz), 256, 0, s>>>(fp, nw, nxy, nz, out);
   return launch_status("depth-dependent average");
 }
 

@@ -79,7 +79,7 @@ def test_every_launch_shape_gives_identical_volumes():
         base = plan.reconstruct(x).clone()
         n = len(plan.tiles)
         for stage in range(n):
-            for v in range(1, 6):
+            for v in range(1, 10):
                 tiles = [0] * n
                 tiles[stage] = v
                 try:
