@@ -144,6 +144,22 @@ nlos_status_t nlos_reconstruct_host(nlos_plan_t plan, const void* transient_host
                                     void* stream);
 
 /*
+ * Reconstruct n captures from host memory into host memory, pipelined: while
+ * capture i is reconstructed, capture i+1 is copied in and capture i-1
+ * copied out, on library-owned streams and three device staging slots per
+ * plan (allocated on first use, kept until nlos_plan_destroy). The work is
+ * ordered after what is already queued on `stream`; the call returns when
+ * every volume is in host memory. Host buffers should be page-locked for the
+ * copies to overlap. transients_host / volumes_host are host arrays of n
+ * host pointers (input_bytes / output_bytes each, from nlos_plan_query).
+ * Uses the plan's own workspace: no other call may use the plan meanwhile.
+ * Errors: INVALID_ARG (NULL plan or pointers, n < 0, plan without
+ * workspace), OUT_OF_MEMORY (staging), CUDA.
+ */
+nlos_status_t nlos_reconstruct_host_many(nlos_plan_t plan, const void* const* transients_host,
+                                         void* const* volumes_host, int n, void* stream);
+
+/*
  * Reconstruct n captures with one launch sequence each, forked over the
  * library's internal streams so that small captures overlap on the device and
  * joined back to `stream`. plans[i] describes capture i;

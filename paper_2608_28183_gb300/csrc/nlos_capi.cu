@@ -101,6 +101,18 @@ size_t real_bytes(int storage) { return storage == kF32 ? 4 : 2; }
 
 }  // namespace
 
+// Staging for pipelined host-buffer calls: kPipeSlots device input/output
+// pairs and three streams, so that the copy in of capture i+1 and the copy
+// out of capture i-1 overlap the reconstruction of capture i.
+constexpr int kPipeSlots = 3;
+struct HostPipe {
+  void* d_in[kPipeSlots] = {};
+  void* d_out[kPipeSlots] = {};
+  cudaStream_t h2d = nullptr, comp = nullptr, d2h = nullptr;
+  cudaEvent_t start = nullptr;
+  cudaEvent_t in_ready[kPipeSlots] = {}, done[kPipeSlots] = {}, out_free[kPipeSlots] = {};
+};
+
 struct nlos_plan_s {
   nlos_plan_desc_t d{};
   int a = 0, b = 0, n = 0;
@@ -128,6 +140,7 @@ struct nlos_plan_s {
   // host-call staging
   void* d_in = nullptr;
   void* d_out = nullptr;
+  struct HostPipe* pipe = nullptr;      // pipelined host calls (created on first use)
   std::vector<void*> allocs;
   // per-stage tile variant (autotuner) and the transform length it applies to
   std::vector<int> tiles;
@@ -750,6 +763,51 @@ nlos_status_t validate(const nlos_plan_desc_t* d) {
   return NLOS_OK;
 }
 
+void destroy_pipe(HostPipe* hp) {
+  if (!hp) return;
+  for (int k = 0; k < kPipeSlots; ++k) {
+    if (hp->in_ready[k]) cudaEventDestroy(hp->in_ready[k]);
+    if (hp->done[k]) cudaEventDestroy(hp->done[k]);
+    if (hp->out_free[k]) cudaEventDestroy(hp->out_free[k]);
+  }
+  if (hp->start) cudaEventDestroy(hp->start);
+  if (hp->h2d) cudaStreamDestroy(hp->h2d);
+  if (hp->comp) cudaStreamDestroy(hp->comp);
+  if (hp->d2h) cudaStreamDestroy(hp->d2h);
+  delete hp;
+}
+
+nlos_status_t ensure_pipe(nlos_plan_s* p, size_t ib, size_t ob) {
+  if (p->pipe) return NLOS_OK;
+  HostPipe* hp = new HostPipe();
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < kPipeSlots && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&hp->in_ready[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->done[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->out_free[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&hp->start, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->h2d, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->comp, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->d2h, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    destroy_pipe(hp);
+    cudaGetLastError();
+    return cuda_fail(e, "host pipeline streams");
+  }
+  nlos_status_t st = NLOS_OK;
+  for (int k = 0; k < kPipeSlots && st == NLOS_OK; ++k) {
+    st = dalloc(p, &hp->d_in[k], ib, "host pipeline staging");
+    if (st == NLOS_OK) st = dalloc(p, &hp->d_out[k], ob, "host pipeline staging");
+  }
+  if (st != NLOS_OK) {
+    destroy_pipe(hp);
+    return st;
+  }
+  p->pipe = hp;
+  return NLOS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -889,6 +947,51 @@ nlos_status_t nlos_reconstruct_phasors(nlos_plan_t p, const void* phasors, void*
   if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace");
   cudaGetLastError();
   return run_pf(p, nullptr, phasors, volume, static_cast<char*>(p->ws), static_cast<cudaStream_t>(stream));
+}
+
+
+nlos_status_t nlos_reconstruct_host_many(nlos_plan_t p, const void* const* transients_host, void* const* volumes_host,
+                                         int n, void* stream) {
+  if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (n < 0 || (n > 0 && (!transients_host || !volumes_host))) return fail(NLOS_ERR_INVALID_ARG, "bad host arrays");
+  if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace");
+  for (int i = 0; i < n; ++i)
+    if (!transients_host[i] || !volumes_host[i]) return fail(NLOS_ERR_INVALID_ARG, "host buffer %d is NULL", i);
+  if (n == 0) return NLOS_OK;
+  size_t ib = 0, ob = 0;
+  nlos_plan_query(p, nullptr, nullptr, &ib, &ob);
+  nlos_status_t st = ensure_pipe(p, ib, ob);
+  if (st != NLOS_OK) return st;
+  HostPipe* hp = p->pipe;
+  cudaGetLastError();
+  // everything runs after the work already queued on the caller's stream
+  NLOS_CU(cudaEventRecord(hp->start, static_cast<cudaStream_t>(stream)), "host pipeline order");
+  NLOS_CU(cudaStreamWaitEvent(hp->h2d, hp->start, 0), "host pipeline order");
+  NLOS_CU(cudaStreamWaitEvent(hp->comp, hp->start, 0), "host pipeline order");
+  NLOS_CU(cudaStreamWaitEvent(hp->d2h, hp->start, 0), "host pipeline order");
+  for (int i = 0; i < n; ++i) {
+    const int k = i % kPipeSlots;
+    if (i >= kPipeSlots) NLOS_CU(cudaStreamWaitEvent(hp->h2d, hp->done[k], 0), "host pipeline order");
+    NLOS_CU(cudaMemcpyAsync(hp->d_in[k], transients_host[i], ib, cudaMemcpyHostToDevice, hp->h2d), "host->device copy");
+    NLOS_CU(cudaEventRecord(hp->in_ready[k], hp->h2d), "host pipeline order");
+    NLOS_CU(cudaStreamWaitEvent(hp->comp, hp->in_ready[k], 0), "host pipeline order");
+    if (i >= kPipeSlots) NLOS_CU(cudaStreamWaitEvent(hp->comp, hp->out_free[k], 0), "host pipeline order");
+    st = run_plan(p, hp->d_in[k], hp->d_out[k], p->ws, hp->comp);
+    if (st != NLOS_OK) {
+      cudaStreamSynchronize(hp->comp);
+      cudaStreamSynchronize(hp->h2d);
+      cudaStreamSynchronize(hp->d2h);
+      return st;
+    }
+    NLOS_CU(cudaEventRecord(hp->done[k], hp->comp), "host pipeline order");
+    NLOS_CU(cudaStreamWaitEvent(hp->d2h, hp->done[k], 0), "host pipeline order");
+    NLOS_CU(cudaMemcpyAsync(volumes_host[i], hp->d_out[k], ob, cudaMemcpyDeviceToHost, hp->d2h), "device->host copy");
+    NLOS_CU(cudaEventRecord(hp->out_free[k], hp->d2h), "host pipeline order");
+  }
+  NLOS_CU(cudaStreamSynchronize(hp->d2h), "host pipeline sync");
+  NLOS_CU(cudaStreamSynchronize(hp->comp), "host pipeline sync");
+  NLOS_CU(cudaStreamSynchronize(hp->h2d), "host pipeline sync");
+  return NLOS_OK;
 }
 
 nlos_status_t nlos_reconstruct_host(nlos_plan_t p, const void* th, void* vh, void* stream) {
@@ -1284,6 +1387,7 @@ const char* nlos_plan_stage_name(nlos_plan_t p, int i) {
 nlos_status_t nlos_plan_destroy(nlos_plan_t p) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
   cudaDeviceSynchronize();
+  destroy_pipe(p->pipe);
   for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
   for (void* v : p->allocs) cudaFree(v);
   delete p;

@@ -140,7 +140,10 @@ __global__ void coherence_vec_kernel(const __grid_constant__ FramePtrs fr, int n
 }
 
 // depth-dependent average: plane z averages the newest N(z) = min(N_w, 1 + N_w z / n_z) frames
-__device__ __forceinline__ int dda_count(int nw, int z, int nz) { return min(nw, 1 + (int)(((long long)nw * z) / nz)); }
+// 32-bit arithmetic: the host keeps nz below 2^27, so nw * z < 2^31
+__device__ __forceinline__ int dda_count(int nw, int z, int nz) {
+  return min(nw, 1 + (int)((unsigned)(nw * z) / (unsigned)nz));
+}
 
 __global__ void dda_kernel(const __grid_constant__ FramePtrs fr, int nw, long long nxy, int nz, float* out) {
   const long long n = nxy * nz;
@@ -165,13 +168,21 @@ __global__ void dda_vec_kernel(const __grid_constant__ FramePtrs fr, int nw, lon
 #pragma unroll
     for (int e = 0; e < 4; ++e) cnt[e] = dda_count(nw, z0 + e, nz);
     float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int j = 0; j < cnt[3]; ++j) {        // counts grow with z: cnt[3] is the largest
-      const float4 f = __ldcs(static_cast<const float4*>(fr.p[j]) + i);
+    auto add = [&](const float4& f, int j) {
       if (j < cnt[0]) s.x += f.x;
       if (j < cnt[1]) s.y += f.y;
       if (j < cnt[2]) s.z += f.z;
       s.w += f.w;
+    };
+    int j = 0;                                 // counts grow with z: cnt[3] is the largest
+    for (; j + 4 <= cnt[3]; j += 4) {
+      float4 f[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) f[u] = __ldcs(static_cast<const float4*>(fr.p[j + u]) + i);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) add(f[u], j + u);
     }
+    for (; j < cnt[3]; ++j) add(__ldcs(static_cast<const float4*>(fr.p[j]) + i), j);
     __stcs(out + i, make_float4(s.x / (float)cnt[0], s.y / (float)cnt[1], s.z / (float)cnt[2], s.w / (float)cnt[3]));
   }
 }
@@ -243,8 +254,8 @@ nlos_status_t nlos_coherence_merge(const void* const* frames, int nw, long long 
 }
 
 nlos_status_t nlos_dda(const float* const* frames, int nw, long long nxy, int nz, float* out, void* stream) {
-  if (!frames || nw < 1 || nw > kMaxFrames || nxy <= 0 || nz <= 0 || !out)
-    return set_error(NLOS_ERR_INVALID_ARG, "bad depth-dependent average arguments (1 <= N_w <= 16)");
+  if (!frames || nw < 1 || nw > kMaxFrames || nxy <= 0 || nz <= 0 || nz >= (1 << 27) || !out)
+    return set_error(NLOS_ERR_INVALID_ARG, "bad depth-dependent average arguments (1 <= N_w <= 16, nz < 2^27)");
   FramePtrs fp{};
   for (int j = 0; j < nw; ++j) {
     if (!frames[j]) return set_error(NLOS_ERR_INVALID_ARG, "NULL frame");

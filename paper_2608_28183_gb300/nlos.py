@@ -30,7 +30,8 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_server_create", "nlos_server_preload", "nlos_server_submit", "nlos_server_wait",
             "nlos_server_stats", "nlos_server_destroy", "nlos_workspace_check", "nlos_selftest_bounded_wait",
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
-            "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors"]
+            "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
+            "nlos_reconstruct_host_many"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -109,8 +110,9 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_bin_phasors.argtypes = [vp, vp, vp, ll, u32, u32, ctypes.c_int, vp, vp]
     lib.nlos_plan_band.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.nlos_reconstruct_phasors.argtypes = [vp, vp, vp, vp]
+    lib.nlos_reconstruct_host_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]
     for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda", "nlos_bin_transient",
-                 "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors"):
+                 "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors", "nlos_reconstruct_host_many"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles", "nlos_batch_create",
                  "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex", "nlos_server_create",
@@ -281,6 +283,26 @@ class Plan:
         _check(_lib.nlos_reconstruct_phasors(self._h, ctypes.c_void_p(phasors.data_ptr()),
                                              ctypes.c_void_p(volume.data_ptr()), _stream_ptr(stream)))
         return volume
+
+    def reconstruct_host_many(self, transients_host, volumes_host, stream=None):
+        """Pipelined end-to-end calls on lists of host buffers (page-locked for
+        overlap); synchronous. Copies in, reconstructions and copies out of
+        consecutive captures overlap."""
+        if len(transients_host) != len(volumes_host):
+            raise ValueError("one output buffer per input")
+
+        def ptr(x):
+            return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+        for t, v in zip(transients_host, volumes_host):
+            nb_t = t.numel() * t.element_size() if hasattr(t, "numel") else t.nbytes
+            nb_v = v.numel() * v.element_size() if hasattr(v, "numel") else v.nbytes
+            if nb_t != self.input_bytes or nb_v != self.output_bytes:
+                raise ValueError(f"host buffers must hold {self.input_bytes} / {self.output_bytes} bytes")
+        n = len(transients_host)
+        T = (ctypes.c_void_p * n)(*[ptr(t) for t in transients_host])
+        V = (ctypes.c_void_p * n)(*[ptr(v) for v in volumes_host])
+        _check(_lib.nlos_reconstruct_host_many(self._h, T, V, n, _stream_ptr(stream)))
+        return volumes_host
 
     def set_profiling(self, enable: bool):
         """Record a CUDA event after every stage of each reconstruction."""

@@ -76,5 +76,6 @@ def test_null_arguments(lib):
     assert lib.nlos_bin_phasors(None, None, None, 10, 0, 1, 0, None, None) == 1
     assert lib.nlos_plan_band(None, None, None) == 1
     assert lib.nlos_reconstruct_phasors(None, None, None, None) == 1
+    assert lib.nlos_reconstruct_host_many(None, None, None, 1, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, -1, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, 0, None) == 0

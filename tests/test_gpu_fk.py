@@ -118,6 +118,26 @@ def test_fk_deterministic_and_host_path():
     assert np.array_equal(h_out.numpy().astype(np.float64), a)
 
 
+@pytest.mark.parametrize("n", [1, 2, 7])
+def test_fk_pipelined_host_calls(n):
+    """n captures host -> host through the pipelined entry point equal the
+    device path capture by capture (more captures than staging slots, and
+    pageable as well as page-locked host memory)."""
+    g = SMALL[4]
+    plan = _plan(g)
+    caps = [_noise_capture(g, seed=10 + i).counts for i in range(n)]
+    ins = [torch.as_tensor(c, dtype=torch.float32).contiguous() for c in caps]
+    if n != 2:
+        ins = [t.pin_memory() for t in ins]
+    outs = [torch.full(plan.out_shape, -1.0, dtype=torch.float32) for _ in range(n)]
+    plan.reconstruct_host_many(ins, outs)
+    for c, o in zip(caps, outs):
+        assert np.array_equal(o.numpy().astype(np.float64), _gpu(plan, c))
+    # the plan stays usable for other calls, and a second pipelined call reuses the staging
+    plan.reconstruct_host_many(ins[:1], outs[:1])
+    assert np.array_equal(outs[0].numpy().astype(np.float64), _gpu(plan, caps[0]))
+
+
 def test_fk_batch_matches_single_calls():
     from paper_2608_28183_gb300 import nlos
     geoms = [SMALL[1], SMALL[2], SMALL[4], SMALL[2]]
