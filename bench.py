@@ -437,12 +437,15 @@ def binning_bench(torch, nlos, synth, reps=20):
         px, tk = torch.from_numpy(px_h).cuda(), torch.from_numpy(tk_h).cuda()
         n = px.numel()
         r = max(3, reps if n < 50_000_000 else reps // 4)
-        ms_p = _event_ms(torch, lambda: plan.bin_phasors(px, tk, base.t0, base.ticks_per_bin, phasors=P), r)
+        ms_p = _event_ms(torch, lambda: plan.bin_phasors(px, tk, base.t0, base.ticks_per_bin, phasors=P,
+                                                         route="direct"), r)
+        ms_a = _event_ms(torch, lambda: plan.bin_phasors(px, tk, base.t0, base.ticks_per_bin, phasors=P), r)
         ms_h = _event_ms(torch, lambda: nlos.bin_transient(px, tk, g.nx, g.ny, g.nt, base.t0, base.ticks_per_bin,
                                                            transient=H), r)
-        out[name] = {"photons": n, "phasor_ms": ms_p, "phasor_photons_per_s": n / (ms_p * 1e-3),
+        out[name] = {"photons": n, "phasor_direct_ms": ms_p, "phasor_direct_photons_per_s": n / (ms_p * 1e-3),
+                     "phasor_auto_ms": ms_a, "phasor_auto_photons_per_s": n / (ms_a * 1e-3),
                      "transient_ms": ms_h, "transient_photons_per_s": n / (ms_h * 1e-3),
-                     "record_read_gbs_phasor": 8 * n / (ms_p * 1e-3) / 1e9}
+                     "record_read_gbs_phasor_direct": 8 * n / (ms_p * 1e-3) / 1e9}
         del px, tk
     # streaming frame through the public calls: pinned records in, volume out
     px_h = torch.from_numpy(small.pixel).pin_memory()
@@ -537,6 +540,25 @@ def moe_bench(torch, nlos, synth, reps=20):
         nlos.moe_mix(i_f, i_p, out=mix)
     return {"grid": [g.nx, g.ny, g.nt], "serial_ms": _event_ms(torch, serial, reps),
             "two_streams_ms": _event_ms(torch, concurrent, reps)}
+
+
+def cufft_reference(torch, g, reps=10):
+    """cuFFT (through torch.fft) on the same padded volume, as a reference
+    point only: one 3D complex forward and one inverse transform of
+    2a x 2b x 2n complex float32 (what the method's two transforms cost as
+    library calls, before any Stolt work), and the real-input forward of the
+    zero-padded transient."""
+    shape = (2 * g.nx, 2 * g.ny, 2 * g.nt)
+    x = torch.zeros(shape, dtype=torch.complex64, device="cuda")
+    r = torch.zeros(shape, dtype=torch.float32, device="cuda")
+    out = {"shape": list(shape), "dtype": "complex64"}
+    out["fftn_c2c_ms"] = _event_ms(torch, lambda: torch.fft.fftn(x), reps)
+    out["ifftn_c2c_ms"] = _event_ms(torch, lambda: torch.fft.ifftn(x), reps)
+    out["rfftn_r2c_ms"] = _event_ms(torch, lambda: torch.fft.rfftn(r), reps)
+    out["two_c2c_transforms_ms"] = out["fftn_c2c_ms"] + out["ifftn_c2c_ms"]
+    del x, r
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_reference(args):
@@ -705,7 +727,8 @@ def main():
     if world == 1 and not args.no_extras and not args.grid:
         for name, fn in (("batch", batch_bench), ("serving", serving_bench),
                          ("phasor_field", lambda t, n, sy: pf_bench(t, n, sy, with_oracle=not args.no_cpu_baseline)),
-                         ("binning", binning_bench), ("post", post_bench), ("moe", moe_bench)):
+                         ("binning", binning_bench), ("post", post_bench), ("moe", moe_bench),
+                         ("cufft_reference", lambda t, n, sy: cufft_reference(t, g))):
             try:
                 extras[name] = fn(torch, nlos, synth)
             except Exception as exc:     # report, do not lose the headline line
@@ -753,6 +776,7 @@ def main():
         "binning": extras.get("binning"),
         "post": extras.get("post"),
         "moe": extras.get("moe"),
+        "cufft_reference": extras.get("cufft_reference"),
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": Ke,
                 "h2d_bytes_per_step": plan.input_bytes, "d2h_bytes_per_step": plan.output_bytes,
                 "path": "nlos_reconstruct_host_many (copies in/out overlap reconstruction), pinned host buffers",

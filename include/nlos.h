@@ -325,16 +325,28 @@ nlos_status_t nlos_bin_transient(const uint32_t* pixel, const uint32_t* ticks, l
 
 /*
  * nlos_bin_phasors: photons of a phasor-field plan's grid (nx, ny, nt)
- *   accumulated directly into its compact phasor field, skipping the
- *   histogram: phasors[x][y][f] (interleaved float32 complex, nx * ny * F
- *   values, F from nlos_plan_band) += w(f) exp(-2 pi i k_f b / nt) for a
- *   photon in bin b, with k_f = k_lo + f the band bins and w(f) the
- *   virtual-wave weights of the plan (Sec. 3.1). This equals w(f) times the
- *   temporal DFT of the binned histogram at the band bins.
- *   Errors: as above, and INVALID_ARG for a plan that is not phasor-field.
+ *   accumulated into its compact phasor field: phasors[x][y][f]
+ *   (interleaved float32 complex, nx * ny * F values, F from nlos_plan_band)
+ *   += w(f) exp(-2 pi i k_f b / nt) for a photon in bin b, with k_f = k_lo + f
+ *   the band bins and w(f) the virtual-wave weights of the plan (Sec. 3.1);
+ *   i.e. w(f) times the temporal DFT of the binned histogram at the band bins.
+ *   Two routes give these phasors: per photon (one warp per 32 records,
+ *   lanes over frequencies, vector atomics; cost ~ photons x F), or through
+ *   an atomic histogram in the plan's workspace and a temporal FFT per wall
+ *   point (cost ~ nx ny nt). By default the second is taken when
+ *   photons x F > 2 nx ny nt and the plan has a workspace; the histogram
+ *   route uses the plan's workspace like nlos_reconstruct.
+ *   flags: NLOS_BIN_ACCUMULATE adds to `phasors` instead of overwriting them;
+ *   NLOS_BIN_DIRECT / NLOS_BIN_VIA_HISTOGRAM force a route.
+ *   Errors: as above, and INVALID_ARG for a plan that is not phasor-field,
+ *   unknown or contradictory flags, or the histogram route forced on a plan
+ *   without workspace.
  */
+#define NLOS_BIN_ACCUMULATE 1
+#define NLOS_BIN_DIRECT 2
+#define NLOS_BIN_VIA_HISTOGRAM 4
 nlos_status_t nlos_bin_phasors(nlos_plan_t plan, const uint32_t* pixel, const uint32_t* ticks, long long count,
-                               uint32_t t0_ticks, uint32_t ticks_per_bin, int accumulate, void* phasors,
+                               uint32_t t0_ticks, uint32_t ticks_per_bin, int flags, void* phasors,
                                void* stream);
 
 /* Band of a phasor-field plan: first DFT bin k_lo and count F of the band
@@ -392,6 +404,13 @@ nlos_status_t nlos_coherence_merge(const void* const* frames, int nw, long long 
  * to [nxy][nz] volumes.
  */
 nlos_status_t nlos_dda(const float* const* frames, int nw, long long nxy, int nz, float* out, void* stream);
+
+/* Testing hook for the failure path (fault injection on the host): the k-th
+ * device allocation that plan creation or host staging makes from now on
+ * (k >= 1) fails as if the device were out of memory, and the call returns
+ * NLOS_ERR_OUT_OF_MEMORY after releasing what it had allocated; k = 0
+ * disables. Process-wide; not for production use. */
+void nlos_debug_fail_allocation(int k);
 
 /* Release the plan's tables, workspace and staging buffers (synchronises the device). */
 nlos_status_t nlos_plan_destroy(nlos_plan_t plan);

@@ -12,6 +12,11 @@
 // (k_f b) mod n. Consecutive records of the same wall point (a scanning
 // capture emits them in runs) are summed in registers, so the warp issues
 // one vector atomic per run and frequency instead of one per photon.
+//
+// For large photon counts the plan code takes another route to the same
+// phasors: an atomic histogram in the plan's workspace followed by the band
+// transform of the phasor pipeline (a temporal FFT per wall point), whose
+// cost grows with the grid rather than with photons x frequencies.
 #include <algorithm>
 #include <cstdint>
 
@@ -102,6 +107,14 @@ int sm_count() {
 
 }  // namespace
 
+cudaError_t launch_bin_transient(const uint32_t* pixel, const uint32_t* ticks, long long count, uint32_t npix,
+                                 uint32_t nt, uint32_t t0, uint32_t tpb, float* H, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const long long blocks = std::min<long long>((count + 255) / 256, (long long)sm_count() * 16);
+  bin_transient_kernel<<<(unsigned)blocks, 256, 0, s>>>(pixel, ticks, count, npix, nt, t0, tpb, H);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bin_phasors(const PhasorBinParams& q, cudaStream_t s) {
   const size_t smem = sizeof(float2) * (size_t)q.n;
   if (smem > 48 * 1024) {
@@ -130,12 +143,9 @@ extern "C" nlos_status_t nlos_bin_transient(const uint32_t* pixel, const uint32_
     const cudaError_t e = cudaMemsetAsync(transient, 0, sizeof(float) * (size_t)nx * ny * nt, s);
     if (e != cudaSuccess) return set_error(NLOS_ERR_CUDA, cudaGetErrorString(e));
   }
-  if (count > 0) {
-    const long long blocks = std::min<long long>((count + 255) / 256, (long long)sm_count() * 16);
-    bin_transient_kernel<<<(unsigned)blocks, 256, 0, s>>>(pixel, ticks, count, (uint32_t)((long long)nx * ny),
-                                                         (uint32_t)nt, t0_ticks, ticks_per_bin, transient);
-  }
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = launch_bin_transient(pixel, ticks, count, (uint32_t)((long long)nx * ny), (uint32_t)nt, t0_ticks,
+                                       ticks_per_bin, transient, s);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return set_error(NLOS_ERR_CUDA, cudaGetErrorString(e));
   return NLOS_OK;
 }

@@ -1,9 +1,11 @@
 // Host side of the library: plan creation (float64 tables), the stage
 // sequences of f-k migration and phasor-field reconstruction, and the C ABI
 // declared in include/nlos.h.
+#include <nvtx3/nvToolsExt.h>
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <cstdlib>
 #include <cstdio>
@@ -157,7 +159,17 @@ struct nlos_plan_s {
 
 namespace {
 
+// failure-path testing hook: the n-th plan allocation from now fails (0: off)
+std::atomic<int> g_fail_alloc{0};
+
 nlos_status_t dalloc(nlos_plan_s* p, void** ptr, size_t bytes, const char* what) {
+  int k = g_fail_alloc.load();
+  while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+  }
+  if (k == 1) {
+    *ptr = nullptr;
+    return fail(NLOS_ERR_OUT_OF_MEMORY, "%s: injected allocation failure", what);
+  }
   cudaError_t e = cudaMalloc(ptr, bytes ? bytes : 16);
   if (e != cudaSuccess) {
     *ptr = nullptr;
@@ -435,8 +447,13 @@ nlos_status_t build_pf(nlos_plan_s* p) {
 }
 
 // records a tracing event after `stage` (or a call start for stage -1)
+// With stage tracing on, each stage is also an NVTX range named after it
+// (host-side enqueue ranges, visible to ncu's --nvtx filters): mark(-1) opens
+// stage 0, mark(i) closes stage i and opens stage i + 1.
 nlos_status_t mark(nlos_plan_s* p, cudaStream_t s, int stage) {
   if (!p->prof_on) return NLOS_OK;
+  if (stage >= 0) nvtxRangePop();
+  if (stage + 1 < (int)p->stage_names.size()) nvtxRangePushA(p->stage_names[stage + 1].c_str());
   if (p->prof_used == p->prof_pool.size()) {
     cudaEvent_t e;
     NLOS_CU(cudaEventCreate(&e), "profiling event");
@@ -911,14 +928,46 @@ nlos_status_t nlos_plan_band(nlos_plan_t p, int* k_lo, int* n_freqs) {
 }
 
 nlos_status_t nlos_bin_phasors(nlos_plan_t p, const uint32_t* pixel, const uint32_t* ticks, long long count,
-                               uint32_t t0_ticks, uint32_t ticks_per_bin, int accumulate, void* phasors,
+                               uint32_t t0_ticks, uint32_t ticks_per_bin, int flags, void* phasors,
                                void* stream) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
   if (p->d.method != NLOS_PHASOR_RSD) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
-  if (!phasors || count < 0 || (count > 0 && (!pixel || !ticks)) || ticks_per_bin == 0)
+  if (!phasors || count < 0 || (count > 0 && (!pixel || !ticks)) || ticks_per_bin == 0 || (flags & ~7) ||
+      (flags & NLOS_BIN_DIRECT && flags & NLOS_BIN_VIA_HISTOGRAM))
     return fail(NLOS_ERR_INVALID_ARG, "bad binning arguments");
+  const bool accumulate = flags & NLOS_BIN_ACCUMULATE;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaGetLastError();
+  // route: per-photon phasors (cost ~ photons x F) or a histogram in the
+  // workspace plus the band transform (cost ~ grid size)
+  const long long cells = (long long)p->a * p->b * p->n;
+  const size_t hbytes = sizeof(float) * (size_t)cells;
+  const bool room = p->ws && hbytes <= p->off_scal;
+  if (flags & NLOS_BIN_VIA_HISTOGRAM && !room)
+    return fail(NLOS_ERR_INVALID_ARG, "the histogram route needs the plan's workspace");
+  const bool hist = room && !(flags & NLOS_BIN_DIRECT) &&
+                    ((flags & NLOS_BIN_VIA_HISTOGRAM) || (double)count * p->F > 2.0 * (double)cells);
+  if (hist) {
+    float* Hs = static_cast<float*>(p->ws);
+    NLOS_CU(cudaMemsetAsync(Hs, 0, hbytes, s), "histogram clear");
+    NLOS_CU(launch_bin_transient(pixel, ticks, count, (uint32_t)((long long)p->a * p->b), (uint32_t)p->n, t0_ticks,
+                                 ticks_per_bin, Hs, s),
+            "photon histogram");
+    PfBandParams bp{};
+    bp.H = Hs;
+    bp.P = phasors;
+    bp.tw = p->tw[p->n];
+    bp.w = p->w;
+    bp.n = p->n;
+    bp.k_lo = p->k_lo;
+    bp.F = p->F;
+    bp.npencils = (long long)p->a * p->b;
+    bp.ld_scale = 1.0f;
+    bp.st_scale = 1.0f;
+    bp.accumulate = accumulate ? 1 : 0;
+    NLOS_CU(launch_pf_band(bp, kF32, s), "phasors from histogram");
+    return NLOS_OK;
+  }
   if (!accumulate) NLOS_CU(cudaMemsetAsync(phasors, 0, sizeof(float2) * (size_t)p->a * p->b * p->F, s), "phasor clear");
   if (count == 0) return NLOS_OK;
   PhasorBinParams q{};
@@ -1393,6 +1442,8 @@ nlos_status_t nlos_plan_destroy(nlos_plan_t p) {
   delete p;
   return NLOS_OK;
 }
+
+void nlos_debug_fail_allocation(int k) { g_fail_alloc.store(k > 0 ? k : 0); }
 
 const char* nlos_last_error(void) { return g_err.c_str(); }
 

@@ -101,6 +101,7 @@ struct PfBandParams {
   float ld_scale;
   const float* ld_dev_scale;
   float st_scale;
+  int accumulate;              // add to P instead of overwriting it
 };
 cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s);
 
@@ -119,6 +120,9 @@ struct PhasorBinParams {
   float2* P;
 };
 cudaError_t launch_bin_phasors(const PhasorBinParams& q, cudaStream_t s);
+// photon records -> float32 histogram H[pixel][bin] (+= 1 per kept record)
+cudaError_t launch_bin_transient(const uint32_t* pixel, const uint32_t* ticks, long long count, uint32_t npix,
+                                 uint32_t nt, uint32_t t0, uint32_t tpb, float* H, cudaStream_t s);
 
 // Phasor-field depth sum over pixel chunks sharing a radial index i0:
 // C[pix][d] = acut * sum_f Phat[pix][f] * ((1 - alpha) K[i0][f][d] + alpha K[i1][f][d]).

@@ -23,13 +23,17 @@ struct PfBandCtx {
   int k_lo, F;
   bool valid;
   float ldmul, stmul;
+  int accumulate;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
     x[0] = valid ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f) : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     const int f = l - k_lo;
-    if (valid && f >= 0 && f < F) Cpx<TS>::put(P + f, cscale(x[0], __ldg(w + f) * stmul));
+    if (!valid || f < 0 || f >= F) return;
+    float2 v = cscale(x[0], __ldg(w + f) * stmul);
+    if (accumulate) v = cadd(v, Cpx<TS>::get(P + f));
+    Cpx<TS>::put(P + f, v);
   }
 };
 
@@ -52,7 +56,7 @@ pf_band_kernel(const PfBandParams p) {
   const long long q = valid ? pid : 0;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   PfBandCtx<L, TR, TS> ctx{static_cast<const TR*>(p.H) + q * p.n, static_cast<TS*>(p.P) + q * p.F,
-                           pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale};
+                           pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale, p.accumulate};
   fftn_run<L, 1, false, false>(ctx, j0);
 }
 

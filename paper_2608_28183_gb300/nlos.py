@@ -31,7 +31,7 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_server_stats", "nlos_server_destroy", "nlos_workspace_check", "nlos_selftest_bounded_wait",
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
             "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
-            "nlos_reconstruct_host_many"]
+            "nlos_reconstruct_host_many", "nlos_debug_fail_allocation"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -111,6 +111,8 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_plan_band.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.nlos_reconstruct_phasors.argtypes = [vp, vp, vp, vp]
     lib.nlos_reconstruct_host_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]
+    lib.nlos_debug_fail_allocation.argtypes = [ctypes.c_int]
+    lib.nlos_debug_fail_allocation.restype = None
     for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda", "nlos_bin_transient",
                  "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors", "nlos_reconstruct_host_many"):
         getattr(lib, name).restype = ctypes.c_int
@@ -260,8 +262,9 @@ class Plan:
         return torch.empty((d.nx, d.ny, self.band[1]), dtype=torch.complex64, device="cuda")
 
     def bin_phasors(self, pixel, ticks, t0_ticks: int, ticks_per_bin: int, phasors=None, accumulate=False,
-                    stream=None):
-        """Accumulate photon records straight into the compact phasor field [nx, ny, F]."""
+                    route: str = "auto", stream=None):
+        """Photon records into the compact phasor field [nx, ny, F]; route is
+        "auto", "direct" (per photon) or "histogram" (atomic histogram + FFT)."""
         _check_photons(pixel, ticks)
         if phasors is None:
             phasors = self.empty_phasors()
@@ -270,7 +273,8 @@ class Plan:
                 or tuple(phasors.shape) != (d.nx, d.ny, self.band[1]):
             raise ValueError("phasors must be contiguous complex64 [nx, ny, F]")
         _check(_lib.nlos_bin_phasors(self._h, ctypes.c_void_p(pixel.data_ptr()), ctypes.c_void_p(ticks.data_ptr()),
-                                     pixel.numel(), t0_ticks, ticks_per_bin, int(bool(accumulate)),
+                                     pixel.numel(), t0_ticks, ticks_per_bin,
+                                     int(bool(accumulate)) | {"auto": 0, "direct": 2, "histogram": 4}[route],
                                      ctypes.c_void_p(phasors.data_ptr()), _stream_ptr(stream)))
         return phasors
 

@@ -81,18 +81,34 @@ def test_bin_empty_and_all_stray():
     assert float(H.abs().sum()) == 0.0
 
 
+@pytest.mark.parametrize("route", ["direct", "histogram", "auto"])
 @pytest.mark.parametrize("order", ["scan", "shuffled"])
-def test_bin_phasors_parity(order):
+def test_bin_phasors_parity(order, route):
     g = GEOM
     plan, oplan = _pf_plans(g)
     k_lo, F = plan.band
     assert k_lo == oplan.band.bins[0] and F == len(oplan.band.bins)
     s = _stream(g, 5, order)
     px, tk = _dev(s)
-    P = plan.bin_phasors(px, tk, s.t0, s.ticks_per_bin).cpu().numpy()
+    P = plan.bin_phasors(px, tk, s.t0, s.ticks_per_bin, route=route).cpu().numpy()
     ref = binning.bin_phasors(s.pixel, s.ticks, g.nx, g.ny, g.nt, s.t0, s.ticks_per_bin,
                               oplan.band.bins, oplan.band.weights)
     assert np.linalg.norm(P - ref) / np.linalg.norm(ref) <= 1e-5
+
+
+@pytest.mark.parametrize("route", ["direct", "histogram"])
+def test_bin_phasors_accumulate(route):
+    g = GEOM
+    plan, oplan = _pf_plans(g)
+    s = _stream(g, 8, "shuffled")
+    px, tk = _dev(s)
+    h = px.numel() // 2
+    P = plan.bin_phasors(px[:h], tk[:h], s.t0, s.ticks_per_bin, route=route)
+    plan.bin_phasors(px[h:], tk[h:], s.t0, s.ticks_per_bin, phasors=P, accumulate=True, route=route)
+    ref = binning.bin_phasors(s.pixel, s.ticks, g.nx, g.ny, g.nt, s.t0, s.ticks_per_bin,
+                              oplan.band.bins, oplan.band.weights)
+    got = P.cpu().numpy()
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
 
 
 def test_reconstruct_from_binned_phasors():
@@ -124,6 +140,8 @@ def test_bin_phasors_full_workload_sampled():
     s = synth.photon_frame(cap, 1_200_000, seed=1)
     px, tk = _dev(s)
     P = plan.bin_phasors(px, tk, s.t0, s.ticks_per_bin).cpu().numpy()
+    Pd = plan.bin_phasors(px, tk, s.t0, s.ticks_per_bin, route="direct").cpu().numpy()
+    assert np.linalg.norm(P - Pd) / np.linalg.norm(Pd) <= 1e-5
     rng = np.random.default_rng(0)
     pick = rng.choice(g.nx * g.ny, size=64, replace=False)
     sel = np.isin(s.pixel, pick)
@@ -146,6 +164,10 @@ def test_binning_rejects_bad_arguments():
         nlos.bin_transient(px, px, g.nx, g.ny, g.nt, 0, 0)
     with pytest.raises(nlos.NlosError, match="INVALID_ARG"):
         plan.bin_phasors(px, px, 0, 0)
+    lib = nlos.load_library()
+    with pytest.raises(nlos.NlosError, match="INVALID_ARG"):      # both routes forced at once
+        nlos._check(lib.nlos_bin_phasors(plan.handle, px.data_ptr(), px.data_ptr(), 4, 0, 1, 6,
+                                               plan.empty_phasors().data_ptr(), None))
     fkp = nlos.plan_for_capture(g, "fk")
     with pytest.raises(nlos.NlosError, match="INVALID_ARG"):
         _ = fkp.band

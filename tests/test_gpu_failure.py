@@ -58,3 +58,49 @@ def test_tma_staged_variants_leave_error_word_clear(lib):
             assert err <= 1e-6, (stage, v, err)
     code = ctypes.c_int(-1)
     assert lib.nlos_workspace_check(plan.handle, None, ctypes.byref(code)) == 0 and code.value == 0
+
+
+def test_injected_allocation_failures_are_reported_and_leak_nothing(lib):
+    """Host-side fault injection: each of the first allocations of a plan
+    fails in turn; creation returns OUT_OF_MEMORY, releases what it had, and
+    the next creation succeeds."""
+    import ctypes
+    from paper_2608_28183_gb300 import nlos
+    g = synth.Geometry(32, 32, 256, 24e-12, 0.8, 0.8)
+    desc = nlos.desc_for_capture(g, "pf", n_depths=16, depth_min_m=0.4, depth_max_m=1.0)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for k in range(1, 8):
+        lib.nlos_debug_fail_allocation(k)
+        h = ctypes.c_void_p()
+        st = lib.nlos_plan_create(ctypes.byref(desc), ctypes.byref(h))
+        lib.nlos_debug_fail_allocation(0)
+        assert st == 2 and not h.value, (k, st)
+        assert b"injected" in lib.nlos_last_error()
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (64 << 20)
+    plan = nlos.plan_for_capture(g, "pf", n_depths=16, depth_min_m=0.4, depth_max_m=1.0)
+    # a failure of the host-call staging leaves the plan usable
+    x = torch.zeros((g.nx, g.ny, g.nt))
+    v = torch.empty(plan.out_shape)
+    lib.nlos_debug_fail_allocation(1)
+    with pytest.raises(nlos.NlosError, match="OUT_OF_MEMORY"):
+        plan.reconstruct_host(x, v)
+    lib.nlos_debug_fail_allocation(0)
+    plan.reconstruct_host(x, v)
+    assert float(v.abs().sum()) == 0.0
+
+
+def test_server_wait_times_out_then_completes(lib):
+    from paper_2608_28183_gb300 import nlos
+    g = synth.Geometry(128, 128, 512, 16e-12, 2.0, 2.0)
+    server = nlos.Server(memory_budget_bytes=8 << 30, n_slots=2)
+    desc = nlos.desc_for_capture(g, "fk")          # not preloaded: the plan is built on admission
+    x = torch.zeros((g.nx, g.ny, g.nt), device="cuda")
+    out = torch.empty((g.nx, g.ny, g.nt), device="cuda")
+    t = server.submit(desc, x, out)
+    with pytest.raises(nlos.NlosError, match="TIMEOUT"):
+        server.wait(t, timeout_s=1e-4)
+    assert server.wait(t, timeout_s=60.0) > 0
+    torch.cuda.synchronize()
+    assert float(out.abs().sum()) == 0.0
