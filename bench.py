@@ -392,6 +392,40 @@ def pf_bench(torch, nlos, synth, steps=200, with_oracle=True):
         else:
             rec["rel_l2_vs_f32"] = float(np.linalg.norm(v.cpu().numpy() - vol32) / np.linalg.norm(vol32))
         out[storage] = rec
+    # dense Fourier-domain kernel (Alg. 3) on the same workload: the depth sum
+    # streams the whole kernel (4ab x F x D complex float32) once per volume
+    try:
+        dplan = nlos.plan_for_capture(g, "pf_dense", "f32", n_depths=128, depth_min_m=0.5, depth_max_m=2.5)
+        dplan.autotune()
+        x = torch.as_tensor(cap.counts, dtype=torch.float32).cuda()
+        v = dplan.empty_volume()
+        for _ in range(3):
+            dplan.reconstruct(x, v)
+        dplan.set_profiling(True)
+        dsteps = max(20, steps // 10)
+        tot, st = time_plan(dplan, x, v, dsteps, torch)
+        stages, calls = dplan.stage_times()
+        dplan.set_profiling(False)
+        F = dplan.band[1]
+        kbytes = 4 * g.nx * g.ny * F * 128 * 8
+        dbytes = kbytes + 4 * g.nx * g.ny * (F + 128) * 8
+        ms = stages["pf_depth_sum"] / calls
+        peaks, _ = measured_peaks()
+        peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+        out["dense_f32"] = {"volumes_per_s": dsteps / (tot / 1e3), "ms_per_volume": tot / dsteps,
+                            "stages_ms": {k: val / calls for k, val in stages.items()},
+                            "kernel_bytes": kbytes,
+                            "depth_sum_hbm": {"bound": "hbm", "bytes": dbytes, "achieved_gbs": dbytes / (ms * 1e-3) / 1e9,
+                                              "frac": dbytes / (ms * 1e-3) / 1e9 / peak},
+                            # the dense sum runs over wall samples and the radial operator
+                            # integrates over the wall: they differ by the area 1/(dx dy),
+                            # so compare peak-normalised volumes
+                            "rel_l2_vs_radial_peak_normalised": float(
+                                np.linalg.norm(v.cpu().numpy() / v.max().item() - vol32 / vol32.max())
+                                / np.linalg.norm(vol32 / vol32.max()))}
+        del dplan
+    except Exception as exc:
+        out["dense_f32"] = {"error": f"{type(exc).__name__}: {exc}"}
     if with_oracle:
         from oracle import pf as opf
         op = opf.make_plan(g.nx, g.ny, g.nt, g.bin_width_s, g.wall_w_m, g.wall_h_m, 128, 0.5, 2.5)

@@ -33,7 +33,13 @@
 extern "C" {
 #endif
 
-typedef enum { NLOS_FK = 0, NLOS_PHASOR_RSD = 1 } nlos_method_t;
+/* NLOS_FK: f-k migration (Alg. 1/2). NLOS_PHASOR_RSD: symmetry-aware radial
+ * phasor-field reconstruction (Alg. 4). NLOS_PHASOR_DENSE: phasor fields with
+ * the dense Fourier-domain propagation kernel (Alg. 3): per plan, every
+ * (frequency, depth) kernel is stored over the padded grid (4 nx ny F D
+ * complex float32 values; float32 storage only); it reproduces the direct
+ * Rayleigh-Sommerfeld sum of Eq. 3 on the wall grid. */
+typedef enum { NLOS_FK = 0, NLOS_PHASOR_RSD = 1, NLOS_PHASOR_DENSE = 2 } nlos_method_t;
 typedef enum { NLOS_F32 = 0, NLOS_F16 = 1, NLOS_BF16 = 2 } nlos_storage_t;
 typedef enum { NLOS_OUT_MAGNITUDE = 0, NLOS_OUT_COMPLEX = 1 } nlos_output_t;
 typedef enum {
@@ -101,7 +107,8 @@ void nlos_plan_desc_default(nlos_plan_desc_t* desc);
  * allocates the default workspace. Synchronous. *out receives an opaque
  * handle owned by the caller until nlos_plan_destroy.
  * Errors: INVALID_ARG (null pointer, sizes, extents <= 0, empty band),
- * UNSUPPORTED (unpadded phasor fields, non-power-of-two sizes), OUT_OF_MEMORY, CUDA.
+ * UNSUPPORTED (unpadded phasor fields, non-power-of-two sizes, 16-bit dense phasor
+ * fields), OUT_OF_MEMORY, CUDA.
  */
 nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out);
 

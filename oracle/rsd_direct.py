@@ -40,3 +40,21 @@ def rsd_direct(P: np.ndarray, freqs: np.ndarray, weights: np.ndarray, depths: np
             acc += weights[fi] * np.exp(1j * kappa[fi] * (sigma_t * d + delta_m)) * (ph @ Pf[:, fi])
         out[:, di] = acc
     return out.reshape(a, b, len(depths))
+
+
+def rsd_direct_at(P: np.ndarray, freqs: np.ndarray, weights: np.ndarray, voxels, wall_w_m: float,
+                  wall_h_m: float, sigma_s: int = 2, sigma_t: int = 0, delta_m: float = 0.0,
+                  c: float = C_LIGHT) -> np.ndarray:
+    """The same sum as rsd_direct at chosen voxels only: voxels = [(ix, iy, depth_m), ...]."""
+    a, b, F = P.shape
+    xs = -wall_w_m / 2 + (np.arange(a) + 0.5) * (wall_w_m / a)
+    ys = -wall_h_m / 2 + (np.arange(b) + 0.5) * (wall_h_m / b)
+    wx, wy = np.meshgrid(xs, ys, indexing="ij")
+    Pf = P.reshape(a * b, F)
+    kappa = 2.0 * np.pi * np.asarray(freqs) / c
+    out = np.zeros(len(voxels), dtype=np.complex128)
+    for n, (ix, iy, d) in enumerate(voxels):
+        R = np.sqrt((wx.reshape(-1) - xs[ix]) ** 2 + (wy.reshape(-1) - ys[iy]) ** 2 + d * d)   # [s]
+        ph = np.exp(1j * sigma_s * np.outer(R, kappa))                                       # [s, f]
+        out[n] = np.sum(weights * np.exp(1j * kappa * (sigma_t * d + delta_m)) * np.sum(ph * Pf, axis=0))
+    return out

@@ -128,6 +128,7 @@ struct nlos_plan_s {
   int F = 0, D = 0, k_lo = 0, nchunks = 0, kr_storage = kF32;
   float* w = nullptr;
   float2* phase = nullptr;              // [n] exp(-2 pi i m / n) for photon binning
+  float2* Kd = nullptr;                 // dense method: Khat [Nu*Nv][F][D]
   void* Kr = nullptr;
   int2* ch_i01 = nullptr;
   int* ch_pix = nullptr;
@@ -281,6 +282,10 @@ double taper_weight(double rb, double rc) {
   return t * t * (3.0 - 2.0 * t);
 }
 
+nlos_status_t build_dense(nlos_plan_s* p, const std::vector<double>& kappa, const std::vector<double>& depth,
+                          int sig_s, int sig_t, double dx, double dy);
+nlos_status_t pf_finish(nlos_plan_s* p, const std::vector<float>& w);
+
 nlos_status_t build_pf(nlos_plan_s* p) {
   const auto& d = p->d;
   const double dx = d.wall_w_m / d.nx, dy = d.wall_h_m / d.ny;
@@ -319,6 +324,10 @@ nlos_status_t build_pf(nlos_plan_s* p) {
   std::vector<double> depth(p->D), r(n_r), rho(n_rho);
   for (int j = 0; j < p->D; ++j)
     depth[j] = p->D == 1 ? d.depth_min_m : d.depth_min_m + j * (d.depth_max_m - d.depth_min_m) / (p->D - 1);
+  if (d.method == NLOS_PHASOR_DENSE) {
+    nlos_status_t st = build_dense(p, kappa, depth, sig_s, sig_t, dx, dy);
+    return st != NLOS_OK ? st : pf_finish(p, w);
+  }
   for (int j = 0; j < n_r; ++j) r[j] = j * dr;
   for (int i = 0; i < n_rho; ++i) rho[i] = i * (rho_max / (n_rho - 1));
   // ring basis with trapezoid weights (Eq. 5, Eq. 6), zero beyond the cutoff
@@ -421,6 +430,14 @@ nlos_status_t build_pf(nlos_plan_s* p) {
     if ((st = upload(p, &p->ch_alpha, ca, "chunk table")) != NLOS_OK) return st;
     if ((st = upload(p, &p->ch_acut, cc, "chunk table")) != NLOS_OK) return st;
   }
+  return pf_finish(p, w);
+}
+
+// band weights, phase table, twiddles and the workspace layout of a
+// phasor-field plan (both kernel representations)
+nlos_status_t pf_finish(nlos_plan_s* p, const std::vector<float>& w) {
+  nlos_status_t st;
+  const int Nu = 2 * p->a, Nv = 2 * p->b;
   if ((st = upload(p, &p->w, w, "band weights")) != NLOS_OK) return st;
   std::vector<float2> phase(p->n);
   for (int m = 0; m < p->n; ++m) {
@@ -685,21 +702,27 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf x-forward");
   NLOS_MARK(p, s, sid++);
-  // PF3: depth sum (pixels beyond the cutoff stay zero)
-  NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * 4 * a * b * D, s), "pf clear");
-  PfDepthParams dp{};
-  dp.Phat = b2;
-  dp.K = p->Kr;
-  dp.C = b1;
-  dp.chunk_i01 = p->ch_i01;
-  dp.chunk_pix = p->ch_pix;
-  dp.chunk_alpha = p->ch_alpha;
-  dp.chunk_acut = p->ch_acut;
-  dp.nchunks = p->nchunks;
-  dp.F = (int)F;
-  dp.D = (int)D;
-  dp.scale = c3;
-  NLOS_CU(launch_pf_depth(dp, st, p->kr_storage, s), "pf depth sum");
+  if (p->d.method == NLOS_PHASOR_DENSE) {
+    // PF3, dense kernel: C = sum_f Phat * Khat (Alg. 3), every pixel written
+    PfDenseParams dp{static_cast<const float2*>(b2), p->Kd, static_cast<float2*>(b1), 4 * a * b, (int)F, (int)D};
+    NLOS_CU(launch_pf_dense(dp, s), "pf dense depth sum");
+  } else {
+    // PF3: depth sum (pixels beyond the cutoff stay zero)
+    NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * 4 * a * b * D, s), "pf clear");
+    PfDepthParams dp{};
+    dp.Phat = b2;
+    dp.K = p->Kr;
+    dp.C = b1;
+    dp.chunk_i01 = p->ch_i01;
+    dp.chunk_pix = p->ch_pix;
+    dp.chunk_alpha = p->ch_alpha;
+    dp.chunk_acut = p->ch_acut;
+    dp.nchunks = p->nchunks;
+    dp.F = (int)F;
+    dp.D = (int)D;
+    dp.scale = c3;
+    NLOS_CU(launch_pf_depth(dp, st, p->kr_storage, s), "pf depth sum");
+  }
   NLOS_MARK(p, s, sid++);
   // PF4: 2D inverse transform per depth (y then x), crop, |.| with 1/(4ab)
   l = axis(st, 2 * b, 2 * a, b1, b0, D, 2 * b * D, D, b * D, D, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b], p->tiles[sid]);
@@ -729,6 +752,52 @@ nlos_status_t run_plan(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaS
   return p->d.method == NLOS_FK ? run_fk(p, H, vol, w, s) : run_pf(p, H, nullptr, vol, w, s);
 }
 
+// Dense method (Alg. 3): Khat[kx][ky][f][d] = DFT2 of the spatial kernel on
+// the signed padded grid, built once per plan (float64 phase, float32 FFTs
+// along y then x through the axis kernels).
+nlos_status_t build_dense(nlos_plan_s* p, const std::vector<double>& kappa, const std::vector<double>& depth,
+                          int sig_s, int sig_t, double dx, double dy) {
+  const int Nu = 2 * p->a, Nv = 2 * p->b;
+  const long long FD = (long long)p->F * p->D;
+  const size_t bytes = sizeof(float2) * (size_t)Nu * Nv * FD;
+  nlos_status_t st;
+  if ((st = ensure_twiddles(p, Nu)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, Nv)) != NLOS_OK) return st;
+  void* Kd = nullptr;
+  if ((st = dalloc(p, &Kd, bytes, "dense kernel")) != NLOS_OK) return st;
+  double *dk = nullptr, *ddep = nullptr;
+  float2* T = nullptr;
+  cudaError_t e = cudaMalloc(&dk, sizeof(double) * p->F);
+  if (e == cudaSuccess) e = cudaMalloc(&ddep, sizeof(double) * p->D);
+  if (e == cudaSuccess) e = cudaMalloc(&T, bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(dk, kappa.data(), sizeof(double) * p->F, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ddep, depth.data(), sizeof(double) * p->D, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    DenseGenParams g{dk, ddep, Nu, Nv, p->F, p->D, dx, dy, (double)sig_s, (double)sig_t, p->d.delta_m,
+                     static_cast<float2*>(Kd)};
+    e = launch_dense_gen(g, 0);    // spatial kernel into Kd, then y (Kd -> T) and x (T -> Kd)
+  }
+  if (e == cudaSuccess) {
+    AxisLaunch l = axis(kF32, Nv, Nu, Kd, T, FD, Nv * FD, FD, Nv * FD, FD, Nv, Nv, 0, 1.0f, p->tw[Nv], 0);
+    e = launch_axis_fft(l, 0);
+  }
+  if (e == cudaSuccess) {
+    AxisLaunch l = axis(kF32, Nu, 1, T, Kd, (long long)Nv * FD, 0, (long long)Nv * FD, 0, (long long)Nv * FD, Nu, Nu, 0,
+                        1.0f, p->tw[Nu], 0);
+    e = launch_axis_fft(l, 0);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (dk) cudaFree(dk);
+  if (ddep) cudaFree(ddep);
+  if (T) cudaFree(T);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "dense kernel build");
+  }
+  p->Kd = static_cast<float2*>(Kd);
+  return NLOS_OK;
+}
+
 std::mutex g_pool_mu;
 cudaStream_t g_streams[kBatchStreams];
 cudaEvent_t g_fork = nullptr;
@@ -749,8 +818,10 @@ nlos_status_t ensure_pool() {
 
 nlos_status_t validate(const nlos_plan_desc_t* d) {
   if (!d) return fail(NLOS_ERR_INVALID_ARG, "desc is NULL");
-  if (d->method != NLOS_FK && d->method != NLOS_PHASOR_RSD)
+  if (d->method != NLOS_FK && d->method != NLOS_PHASOR_RSD && d->method != NLOS_PHASOR_DENSE)
     return fail(NLOS_ERR_INVALID_ARG, "unknown method %d", d->method);
+  if (d->method == NLOS_PHASOR_DENSE && d->storage != NLOS_F32)
+    return fail(NLOS_ERR_UNSUPPORTED, "the dense phasor-field method stores float32 only");
   if (d->storage != NLOS_F32 && d->storage != NLOS_F16 && d->storage != NLOS_BF16)
     return fail(NLOS_ERR_INVALID_ARG, "unknown storage %d", d->storage);
   if (d->nx <= 0 || d->ny <= 0 || d->nt <= 0) return fail(NLOS_ERR_INVALID_ARG, "sizes must be positive");
@@ -769,7 +840,7 @@ nlos_status_t validate(const nlos_plan_desc_t* d) {
     return fail(NLOS_ERR_UNSUPPORTED, "nx, ny must be in [8, 1024]");
   const int tmax = d->method == NLOS_FK ? 2048 : 4096;
   if (d->nt < 16 || d->nt > tmax) return fail(NLOS_ERR_UNSUPPORTED, "nt must be in [16, %d]", tmax);
-  if (d->method == NLOS_PHASOR_RSD) {
+  if (d->method != NLOS_FK) {
     if (d->n_depths < 1 || d->n_depths > 8192) return fail(NLOS_ERR_INVALID_ARG, "n_depths must be in [1, 8192]");
     if (!(d->depth_min_m > 0) || d->depth_max_m < d->depth_min_m)
       return fail(NLOS_ERR_INVALID_ARG, "depth range must satisfy 0 < min <= max");
@@ -921,7 +992,7 @@ nlos_status_t nlos_reconstruct(nlos_plan_t p, const void* transient, void* volum
 
 nlos_status_t nlos_plan_band(nlos_plan_t p, int* k_lo, int* n_freqs) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
-  if (p->d.method != NLOS_PHASOR_RSD) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
+  if (p->d.method == NLOS_FK) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
   if (k_lo) *k_lo = p->k_lo;
   if (n_freqs) *n_freqs = p->F;
   return NLOS_OK;
@@ -931,7 +1002,7 @@ nlos_status_t nlos_bin_phasors(nlos_plan_t p, const uint32_t* pixel, const uint3
                                uint32_t t0_ticks, uint32_t ticks_per_bin, int flags, void* phasors,
                                void* stream) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
-  if (p->d.method != NLOS_PHASOR_RSD) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
+  if (p->d.method == NLOS_FK) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
   if (!phasors || count < 0 || (count > 0 && (!pixel || !ticks)) || ticks_per_bin == 0 || (flags & ~7) ||
       (flags & NLOS_BIN_DIRECT && flags & NLOS_BIN_VIA_HISTOGRAM))
     return fail(NLOS_ERR_INVALID_ARG, "bad binning arguments");
@@ -990,7 +1061,7 @@ nlos_status_t nlos_bin_phasors(nlos_plan_t p, const uint32_t* pixel, const uint3
 
 nlos_status_t nlos_reconstruct_phasors(nlos_plan_t p, const void* phasors, void* volume, void* stream) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
-  if (p->d.method != NLOS_PHASOR_RSD) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
+  if (p->d.method == NLOS_FK) return fail(NLOS_ERR_INVALID_ARG, "not a phasor-field plan");
   if (p->storage != kF32) return fail(NLOS_ERR_UNSUPPORTED, "phasor input needs a float32 plan");
   if (!phasors || !volume) return fail(NLOS_ERR_INVALID_ARG, "phasors/volume is NULL");
   if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace");

@@ -158,6 +158,27 @@ cudaError_t launch_kr_build(const KrBuildParams& p, cudaStream_t s);
 cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int storage, double scale,
                             cudaStream_t s);
 
+// Dense phasor-field kernel (Alg. 3), spatial form on the signed padded grid:
+// k[x][y][f][d] = exp(i kappa_f (sigma_s R + sigma_t d + Delta)),
+// R = sqrt((x~ dx)^2 + (y~ dy)^2 + d^2), phase in float64.
+struct DenseGenParams {
+  const double* kappa;         // [F]
+  const double* depth;         // [D]
+  int Nu, Nv, F, D;
+  double dx, dy, sigma_s, sigma_t, delta;
+  float2* k;                   // out [Nu][Nv][F][D]
+};
+cudaError_t launch_dense_gen(const DenseGenParams& p, cudaStream_t s);
+// Dense depth sum: C[pix][d] = sum_f Phat[pix][f] * Khat[pix][f][d] (float32).
+struct PfDenseParams {
+  const float2* Phat;          // [npix][F]
+  const float2* K;             // [npix][F][D]
+  float2* C;                   // [npix][D]
+  long long npix;
+  int F, D;
+};
+cudaError_t launch_pf_dense(const PfDenseParams& p, cudaStream_t s);
+
 // Per-volume scale for reduced-precision storage: out[0] = target / ||u||_2,
 // out[1] = 1 / out[0], out[2] = 1 / out[0]^2, where u = H * (t % n) * t_scale (t_scale = 0: no ramp).
 cudaError_t launch_volume_scale(const void* H, long long count, int n, float t_scale, int storage,

@@ -388,4 +388,78 @@ cudaError_t launch_volume_scale(const void* H, long long count, int n, float t_s
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Dense phasor-field method (Alg. 3): the propagation kernel of every
+// (frequency, depth) pair stored in Fourier form over the padded grid. The
+// spatial kernel is generated here with its phase in float64 (the phase runs
+// to hundreds of radians), then transformed by the axis FFTs at plan time.
+// ---------------------------------------------------------------------------
+__global__ void dense_gen_kernel(const DenseGenParams p) {
+  const long long FD = (long long)p.F * p.D;
+  const long long total = (long long)p.Nu * p.Nv * FD;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int dd = (int)(i % p.D);
+    const int f = (int)((i / p.D) % p.F);
+    const long long pix = i / FD;
+    const int x = (int)(pix / p.Nv), y = (int)(pix % p.Nv);
+    const double sx = (x < p.Nu / 2 ? x : x - p.Nu) * p.dx;
+    const double sy = (y < p.Nv / 2 ? y : y - p.Nv) * p.dy;
+    const double z = p.depth[dd];
+    const double R = sqrt(sx * sx + sy * sy + z * z);
+    double sn, cs;
+    sincos(p.kappa[f] * (p.sigma_s * R + p.sigma_t * z + p.delta), &sn, &cs);
+    p.k[i] = make_float2((float)cs, (float)sn);
+  }
+}
+
+cudaError_t launch_dense_gen(const DenseGenParams& p, cudaStream_t s) {
+  dense_gen_kernel<<<152 * 16, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// One CTA per padded pixel, threads over depths; the pixel's F phasors sit in
+// shared memory and each thread streams its column of the kernel (read once,
+// evict first), four frequencies in flight.
+__global__ void __launch_bounds__(128) pf_dense_kernel(const PfDenseParams p) {
+  extern __shared__ float2 ph_sm[];
+  const long long pix = blockIdx.x;
+  for (int f = threadIdx.x; f < p.F; f += blockDim.x) ph_sm[f] = p.Phat[pix * p.F + f];
+  __syncthreads();
+  const float2* K = p.K + pix * p.F * (long long)p.D;
+  for (int d = threadIdx.x; d < p.D; d += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    int f = 0;
+    for (; f + 4 <= p.F; f += 4) {
+      float2 k[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) k[u] = __ldcs(K + (long long)(f + u) * p.D + d);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float2 x = ph_sm[f + u];
+        acc.x = fmaf(x.x, k[u].x, fmaf(-x.y, k[u].y, acc.x));
+        acc.y = fmaf(x.x, k[u].y, fmaf(x.y, k[u].x, acc.y));
+      }
+    }
+    for (; f < p.F; ++f) {
+      const float2 k = __ldcs(K + (long long)f * p.D + d), x = ph_sm[f];
+      acc.x = fmaf(x.x, k.x, fmaf(-x.y, k.y, acc.x));
+      acc.y = fmaf(x.x, k.y, fmaf(x.y, k.x, acc.y));
+    }
+    p.C[pix * p.D + d] = acc;
+  }
+}
+
+cudaError_t launch_pf_dense(const PfDenseParams& p, cudaStream_t s) {
+  if (p.npix <= 0 || p.F <= 0 || p.D <= 0) return cudaErrorInvalidValue;
+  const int threads = p.D <= 64 ? 64 : 128;
+  const size_t smem = sizeof(float2) * p.F;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(pf_dense_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  pf_dense_kernel<<<(unsigned)p.npix, threads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace nlos

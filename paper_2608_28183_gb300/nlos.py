@@ -14,10 +14,10 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libnlos_gb300.so")
 
-NLOS_FK, NLOS_PHASOR_RSD = 0, 1
+NLOS_FK, NLOS_PHASOR_RSD, NLOS_PHASOR_DENSE = 0, 1, 2
 NLOS_F32, NLOS_F16, NLOS_BF16 = 0, 1, 2
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
-METHODS = {"fk": NLOS_FK, "pf": NLOS_PHASOR_RSD, "phasor": NLOS_PHASOR_RSD}
+METHODS = {"fk": NLOS_FK, "pf": NLOS_PHASOR_RSD, "phasor": NLOS_PHASOR_RSD, "pf_dense": NLOS_PHASOR_DENSE}
 STORAGES = {"f32": NLOS_F32, "f16": NLOS_F16, "bf16": NLOS_BF16}
 OUTPUTS = {"magnitude": 0, "complex": 1}
 

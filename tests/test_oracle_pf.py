@@ -171,6 +171,28 @@ def test_agrees_with_direct_rsd_peak():
         assert _peak(I) == _peak(Id), (_peak(I), _peak(Id))
 
 
+def test_direct_rsd_sampled_voxels_and_point_focus():
+    """rsd_direct_at (the sum at chosen voxels) equals the full direct sum
+    there, and a single point reflector focuses at its own voxel (nearest
+    wall sample and depth plane) in the direct sum, with or without the
+    non-confocal modality's depth phase."""
+    geom = synth.Geometry(8, 16, 256, 24e-12, 0.5, 0.9)
+    p = pf.make_plan(8, 16, 256, 24e-12, 0.5, 0.9, 12, 0.3, 0.9)
+    pt = (0.06, -0.12, 0.6)
+    cap = synth.point_capture(geom, [(*pt, 1.0)])
+    P = pf.phasor_field(cap.counts, p)
+    full = rsd_direct.rsd_direct(P, p.band.freqs, p.band.weights, p.depths, 0.5, 0.9)
+    vox = [(0, 0, p.depths[0]), (3, 11, p.depths[5]), (7, 15, p.depths[11]), (4, 2, p.depths[7])]
+    at = rsd_direct.rsd_direct_at(P, p.band.freqs, p.band.weights, vox, 0.5, 0.9)
+    idx = [(0, 0, 0), (3, 11, 5), (7, 15, 11), (4, 2, 7)]
+    np.testing.assert_allclose(at, [full[i] for i in idx], rtol=1e-12, atol=1e-9 * np.abs(full).max())
+    xs = synth.wall_coords(8, 0.5)
+    ys = synth.wall_coords(16, 0.9)
+    exp = (np.argmin(abs(xs - pt[0])), np.argmin(abs(ys - pt[1])), np.argmin(abs(p.depths - pt[2])))
+    got = _peak(np.abs(full))
+    assert all(abs(int(g) - int(e)) <= 1 for g, e in zip(got, exp)), (got, exp)
+
+
 def test_lerp_index_rules():
     """Neighbour indices never exceed the cutoff bin, and interpolation is
     exact for a kernel that is linear in rho."""
