@@ -15,8 +15,10 @@ paper is silent:
   * bin = (ticks - t0) // ticks_per_bin, in integers, so the decision is exact
     on both sides; photons with ticks < t0, bin >= nt or a wall index outside
     the grid are dropped.
-  * The phasor of a photon in bin b at band bin k_f is exp(-2 pi i k_f b / n)
-    (the forward DFT sign of the phasor field); the compact phasor field is
+  * The phasor of a photon in bin b at band bin k_f is exp(-2 pi i k_f b / Lt)
+    with Lt the temporal DFT length of the phasor pipeline (nt, or the next
+    power of two for other nt; the forward DFT sign of the phasor field); the
+    compact phasor field is
     P[x][y][f] = w(f) * sum over the photons of (x, y) of that phasor, with
     w(f) the virtual-wave weight of the band (the same P the phasor pipeline
     forms from H).
@@ -30,6 +32,8 @@ an independent route through scipy.fft).
 from __future__ import annotations
 
 import numpy as np
+
+from .pf import temporal_length
 
 
 def bin_indices(pixel: np.ndarray, ticks: np.ndarray, nx: int, ny: int, nt: int, t0: int, ticks_per_bin: int):
@@ -51,12 +55,13 @@ def bin_transient(pixel, ticks, nx: int, ny: int, nt: int, t0: int, ticks_per_bi
 
 def bin_phasors(pixel, ticks, nx: int, ny: int, nt: int, t0: int, ticks_per_bin: int,
                 band_bins: np.ndarray, band_w: np.ndarray) -> np.ndarray:
-    """P[x][y][f] = w(f) * sum_photons exp(-2 pi i k_f b / nt), accumulated per photon."""
+    """P[x][y][f] = w(f) * sum_photons exp(-2 pi i k_f b / Lt), accumulated per photon."""
     p, b = bin_indices(pixel, ticks, nx, ny, nt, t0, ticks_per_bin)
+    Lt = temporal_length(nt)
     k = np.asarray(band_bins, dtype=np.int64)
     P = np.zeros((nx * ny, len(k)), dtype=np.complex128)
     step = 1 << 14
     for s in range(0, len(p), step):                     # one row of phasors per photon
-        ph = np.exp(-2j * np.pi * np.outer(b[s:s + step], k) / nt)
+        ph = np.exp(-2j * np.pi * np.outer(b[s:s + step], k) / Lt)
         np.add.at(P, p[s:s + step], ph)
     return (P * np.asarray(band_w, dtype=np.float64)[None, :]).reshape(nx, ny, len(k))

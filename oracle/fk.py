@@ -58,18 +58,35 @@ def signed_index(N: int) -> np.ndarray:
     return np.where(k < N // 2, k, k - N)
 
 
+def padded_length(N: int, pad_factor: int) -> int:
+    """Transform length of an axis of N samples: pad_factor 2 zero-pads to the
+    smallest power of two >= 2N (exactly 2N for power-of-two N, as in Alg. 1);
+    pad_factor 1 keeps N."""
+    if pad_factor == 1:
+        return N
+    L = 1
+    while L < pad_factor * N:
+        L *= 2
+    return L
+
+
 def fk_spectrum(H: np.ndarray, pad_factor: int = 2, workers=None) -> np.ndarray:
     """Steps (i)-(ii): time scaling t/(n-1), zero padding, forward 3D DFT."""
     H = np.asarray(H, dtype=np.float64)
     a, b, n = H.shape
     ramp = np.arange(n, dtype=np.float64) / (n - 1)
-    psi = np.zeros((pad_factor * a, pad_factor * b, pad_factor * n))
+    psi = np.zeros((padded_length(a, pad_factor), padded_length(b, pad_factor), padded_length(n, pad_factor)))
     psi[:a, :b, :n] = H * ramp[None, None, :]
     return sfft.fftn(psi, workers=_workers(workers))
 
 
 def stolt(U: np.ndarray, s_x: float, s_y: float) -> np.ndarray:
-    """Step (iii): Stolt resampling with the Jacobian weight and the Z > 0 mask."""
+    """Step (iii): Stolt resampling with the Jacobian weight and the Z > 0 mask.
+
+    The grids are those of the padded spectrum (Lx, Ly, Lt): X = p~/(Lx/2),
+    Y = q~/(Ly/2), Z = m~/(Lt/2), so the source index is
+    mu = sqrt((Lt s_x p~/Lx)^2 + (Lt s_y q~/Ly)^2 + m~^2): the same physical
+    Stolt map for any padding (Alg. 1's X = p~/a etc. when L = 2 x size)."""
     Px, Py, Pt = U.shape
     hx, hy, ht = Px // 2, Py // 2, Pt // 2
     X = signed_index(Px) / hx

@@ -7,14 +7,17 @@ trapezoid weights, radial sample count, cutoff, bin coordinate, smoothstep
 taper) and Alg. 4, with these readings where the paper is silent:
 
   * Virtual wave: wavelength lambda = 4 dx unless given; centre frequency
-    f0 = c / lambda; bin spacing df = 1 / (n dt); centre bin k0 = round(f0/df).
+    f0 = c / lambda; bin spacing df = 1 / (Lt dt) with Lt = n for power-of-two
+    n and the next power of two otherwise (zero-padded temporal transform);
+    centre bin k0 = round(f0/df).
     "cycles" wide means +-3 sigma_t spans `cycles` periods:
     sigma_t = cycles / (6 f0), sigma_f = 1 / (2 pi sigma_t). The band keeps
     bins k0 - K_h .. k0 + K_h with K_h = round(5 sigma_f / df), clipped to
     [1, n/2 - 1]; w(f) = exp(-(f_k - f0)^2 / (2 sigma_f^2)).
   * Phasors: P(x, y, f) = sum_t H(x, y, t) exp(-2 pi i k_f t / n)
     (forward DFT sign e^{-i}); w(f) is applied inside the depth sum (Alg. 4).
-  * Spectral coordinates: the top-left padded grid is Nu x Nv = pf*a x pf*b
+  * Spectral coordinates: the top-left padded grid is Nu x Nv = 2a x 2b
+    (the next powers of two >= 2a, 2b for other sizes)
     with physical sides Nu dx and Nv dy; DFT index (kx, ky) has signed indices
     (kx~, ky~) and radius rho = sqrt((kx~/(Nu dx))^2 + (ky~/(Nv dy))^2).
   * Kernel phase e^{+i kappa sigma_s sqrt(r^2 + d^2)} (Eq. 4) with
@@ -59,6 +62,18 @@ def _ceil_int(x: float) -> int:
 
 def _pow2_at_least(x: int) -> int:
     return 1 << int(math.ceil(math.log2(x)))
+
+
+def _padded(N: int, pad_factor: int) -> int:
+    """Spatial transform length: the smallest power of two >= pad_factor * N
+    (exactly 2N for power-of-two N, Alg. 4's pad_tl)."""
+    return _pow2_at_least(pad_factor * N)
+
+
+def temporal_length(nt: int) -> int:
+    """Length of the temporal DFT: nt for power-of-two nt, otherwise the
+    transient zero-padded to the next power of two (finer band spacing)."""
+    return _pow2_at_least(nt)
 
 
 @dataclass
@@ -210,9 +225,9 @@ def make_plan(nx: int, ny: int, nt: int, bin_width_s: float, wall_w_m: float, wa
     dx = wall_w_m / nx
     dy = wall_h_m / ny
     lam = wavelength_m if wavelength_m > 0 else 4.0 * dx
-    band = virtual_wave_band(nt, bin_width_s, lam, cycles, c)
+    band = virtual_wave_band(temporal_length(nt), bin_width_s, lam, cycles, c)
     lambda_min = c / band.freqs.max()
-    Nu, Nv = pad_factor * nx, pad_factor * ny
+    Nu, Nv = _padded(nx, pad_factor), _padded(ny, pad_factor)
     rs = radial_sampling(Nu, Nv, dx, dy, sigma_s, lambda_min)
     depths = depth_planes(n_depths, depth_min_m, depth_max_m)
     kappa = 2.0 * np.pi * band.freqs / c                                   # [F]
@@ -238,9 +253,10 @@ def pixel_radius_bins(plan: PhasorPlan) -> np.ndarray:
 
 
 def phasor_field(H: np.ndarray, plan: PhasorPlan) -> np.ndarray:
-    """P(x, y, f) = sum_t H(x, y, t) e^{-2 pi i k_f t / n} at the band bins."""
+    """P(x, y, f) = sum_t H(x, y, t) e^{-2 pi i k_f t / Lt} at the band bins
+    (Lt = temporal_length(nt))."""
     H = np.asarray(H, dtype=np.float64)
-    spec = sfft.rfft(H, axis=2, workers=_workers(None))
+    spec = sfft.rfft(H, n=temporal_length(H.shape[2]), axis=2, workers=_workers(None))
     return spec[:, :, plan.band.bins]
 
 

@@ -43,6 +43,20 @@ def test_phasors_equal_fft_of_histogram():
     np.testing.assert_allclose(P, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
 
 
+def test_phasors_equal_fft_of_histogram_any_length():
+    """Same identity on a temporal axis that is not a power of two (the
+    phasor DFT runs over the zero-padded length)."""
+    g = synth.Geometry(6, 5, 200, 32e-12, 0.3, 0.3)
+    plan = pf.make_plan(g.nx, g.ny, g.nt, g.bin_width_s, g.wall_w_m, g.wall_h_m, 4, 0.3, 0.6)
+    counts = np.random.default_rng(7).poisson(1.0, size=(g.nx, g.ny, g.nt))
+    s = synth.photons_from_counts(counts, seed=4)
+    P = binning.bin_phasors(s.pixel, s.ticks, g.nx, g.ny, g.nt, s.t0, s.ticks_per_bin, plan.band.bins,
+                            plan.band.weights)
+    ref = pf.phasor_field(binning.bin_transient(s.pixel, s.ticks, g.nx, g.ny, g.nt, s.t0, s.ticks_per_bin), plan)
+    ref = ref * plan.band.weights[None, None, :]
+    np.testing.assert_allclose(P, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+
+
 def test_single_photon_phasor():
     """One photon in bin b gives w(f) exp(-2 pi i k_f b / n), the textbook DFT of a delta."""
     k = np.array([1, 5, 31])

@@ -43,33 +43,39 @@ def test_impulse_closed_form_zero_lateral_factor(t0):
     reconstruction of a wall impulse is the positive-half (analytic) filter of
     the scaled impulse along t; its closed form is a geometric series:
 
-        psi(z) = (t0/(n-1)) / (2n) * sum_{m=1}^{n-1} exp(i pi m (z - t0) / n)
+        psi(z) = (t0/(n-1)) / Lt * sum_{m=1}^{Lt/2-1} exp(2 pi i m (z - t0) / Lt)
 
-    at the impulse's wall sample, and 0 at every other wall sample.
+    at the impulse's wall sample, and 0 at every other wall sample, with Lt
+    the padded temporal length (2n for power-of-two n, here the next power
+    of two >= 2n = 48, i.e. 64).
     """
     a, b, n = 4, 3, 24
     x0, y0 = 2, 1
     H = np.zeros((a, b, n))
     H[x0, y0, t0] = 1.0
     psi = fk.fk_reconstruct(H, 0, 0, 0, lateral=(0.0, 0.0), return_complex=True)
+    Lt = fk.padded_length(n, 2)
+    assert Lt == 64
+    M = Lt // 2 - 1
     z = np.arange(n)
-    theta = np.pi * (z - t0) / n
+    theta = 2 * np.pi * (z - t0) / Lt
     with np.errstate(invalid="ignore", divide="ignore"):
-        geo = np.exp(1j * theta) * (1 - np.exp(1j * (n - 1) * theta)) / (1 - np.exp(1j * theta))
-    geo = np.where(z == t0, n - 1, geo)
-    expect = (t0 / (n - 1)) / (2 * n) * geo
+        geo = np.exp(1j * theta) * (1 - np.exp(1j * M * theta)) / (1 - np.exp(1j * theta))
+    geo = np.where(z == t0, M, geo)
+    expect = (t0 / (n - 1)) / Lt * geo
     np.testing.assert_allclose(psi[x0, y0], expect, atol=1e-14)
     others = np.ones((a, b), bool)
     others[x0, y0] = False
     assert np.max(abs(psi[others])) < 1e-14
     R = fk.fk_reconstruct(H, 0, 0, 0, lateral=(0.0, 0.0))
-    assert np.isclose(R[x0, y0, t0], ((t0 / (n - 1)) * (n - 1) / (2 * n)) ** 2, rtol=1e-12)
+    assert np.isclose(R[x0, y0, t0], ((t0 / (n - 1)) * M / Lt) ** 2, rtol=1e-12)
 
 
 @pytest.mark.parametrize("geom,pt", [
     (synth.Geometry(32, 32, 256, 32e-12, 1.0, 1.0), (0.1, -0.2, 0.7)),
     (synth.Geometry(32, 32, 256, 32e-12, 1.0, 1.0), (-0.3, 0.25, 1.0)),
     (synth.Geometry(24, 40, 256, 32e-12, 0.8, 1.3), (-0.15, 0.3, 0.6)),
+    (synth.Geometry(20, 28, 200, 32e-12, 0.7, 0.9), (0.1, -0.15, 0.6)),      # no power-of-two axis
 ])
 def test_point_reflector_peak(geom, pt):
     """A single rendered point reflector reconstructs to a peak within one
@@ -106,10 +112,12 @@ def test_lateral_factors_follow_their_own_axis():
     assert all(abs(g - e) <= 1 for g, e in zip(_peak(R), exp))
 
 
-def test_agrees_with_backprojection_peaks():
-    """On an 8 x 8 x 64 grid, f-k and brute-force backprojection put the peak of
-    each rendered point reflector at the same voxel (within one voxel)."""
-    geom = synth.Geometry(8, 8, 64, 64e-12, 0.6, 0.6)
+@pytest.mark.parametrize("geom", [synth.Geometry(8, 8, 64, 64e-12, 0.6, 0.6),
+                                  synth.Geometry(10, 12, 96, 64e-12, 0.6, 0.7)])
+def test_agrees_with_backprojection_peaks(geom):
+    """On 8 x 8 x 64 and 10 x 12 x 96 grids (the latter padded to the next
+    powers of two), f-k and brute-force backprojection put the peak of each
+    rendered point reflector at the same voxel (within one voxel)."""
     for pt in [(0.05, -0.1, 0.6), (-0.15, 0.12, 0.9)]:
         cap = synth.point_capture(geom, [(*pt, 1.0)])
         R = fk.fk_reconstruct(cap.counts, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m)

@@ -143,6 +143,7 @@ def test_cos_sin_linearity_identity():
 @pytest.mark.parametrize("geom,pt,depths", [
     (synth.Geometry(32, 32, 512, 16e-12, 1.0, 1.0), (0.12, -0.2, 0.9), (32, 0.4, 1.2)),
     (synth.Geometry(24, 32, 512, 16e-12, 0.9, 1.2), (-0.2, 0.1, 0.8), (24, 0.5, 1.1)),
+    (synth.Geometry(24, 20, 300, 16e-12, 0.8, 0.7), (0.1, -0.12, 0.55), (20, 0.35, 0.7)),  # no power of two
 ])
 def test_point_reflector_focus(geom, pt, depths):
     """A single point reflector reconstructs at the nearest depth plane (+-1)
