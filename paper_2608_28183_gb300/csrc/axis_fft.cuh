@@ -522,7 +522,7 @@ template <class TS, int RANGE>
 cudaError_t launch_axis_typed(const AxisLaunch& l, cudaStream_t s) {
   if (l.n_outer <= 0 || l.n_outer > 65535 || l.p.inner <= 0)
     return axis_report("bad-shape", l.L, 0, 0, 0, l.p.inner, l.n_outer, cudaErrorInvalidValue);
-  const bool half_in = 2 * l.p.L_in == l.L, half_out = 2 * l.p.L_out <= l.L;
+  const bool half_in = 2 * l.p.L_in <= l.L, half_out = 2 * l.p.L_out <= l.L;   // zero beyond L_in
   if (axis_debug())
     fprintf(stderr, "[nlos axis] dispatch L=%d load=%d store=%d L_in=%d L_out=%d tile=%d tmap=%d\n", l.L, l.load_mode,
             l.store_mode, l.p.L_in, l.p.L_out, l.tile, l.has_tmap);

@@ -1,16 +1,17 @@
 // f-k migration, temporal-frequency stage (Sec. 4.2, Alg. 1 Stolt step).
 //
-// The x/y transforms before this stage keep only kx in [0, a] of the real
+// The x/y transforms before this stage keep only kx in [0, Lx/2] of the real
 // input's spectrum (Hermitian half along x). Each stored pencil (kx, ky) is
-// transformed along t (length 2n, upper half zero) into U(kx, ky, m), held in
-// shared memory. The Stolt step reads U at the source coordinate
-// mu = sqrt(A + m^2), A = (n s_x p~/a)^2 + (n s_y q~/b)^2, with a two-tap
-// linear interpolation along the contiguous axis, weights it by Z/Z' = m/mu
-// and keeps 1 <= m <= n-1 with mu <= n-1 (Z > 0 and interpn's zero fill).
+// transformed along t (length L >= 2n, zero beyond the n samples) into
+// U(kx, ky, m), held in shared memory. The Stolt step reads U at the source
+// coordinate mu = sqrt(A + m^2), A = (L s_x p~/Lx)^2 + (L s_y q~/Ly)^2 (for
+// L = 2n, Lx = 2a: (n s_x p~/a)^2 ...), with a two-tap linear interpolation
+// along the contiguous axis, weights it by Z/Z' = m/mu and keeps
+// 1 <= m <= L/2-1 with mu <= L/2-1 (Z > 0 and interpn's zero fill).
 // The same pencil also yields its Hermitian partner (-kx, -ky): there
 // U(-p~, -q~, k) = conj(U(p~, q~, -k)), so the partner's resampled spectrum is
 // conj(lerp(U[-k0], U[-k1])) * m/mu. Both resampled spectra are inverse
-// transformed (length 2n, only z < n kept) and written, so the Stolt output
+// transformed (length L, only z < n kept) and written, so the Stolt output
 // never round-trips through global memory.
 //
 // mu is computed in float-float: A comes from float64 per-plan tables split
@@ -78,8 +79,9 @@ struct FkFwdCtx {
   const float2* tw;
   bool valid;
   float ldmul;
+  int n_in;                  // stored samples of the pencil (the rest is zero padding)
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = valid ? cscale(Cpx<TS>::get(g + l), ldmul) : make_float2(0.f, 0.f);
+    x[0] = (valid && l < n_in) ? cscale(Cpx<TS>::get(g + l), ldmul) : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[pad16(l)] = x[0]; }
@@ -99,10 +101,11 @@ struct FkInvCtx {
   const float2* tw;
   TS* out0;
   TS* out1;
-  int n;
+  int n;                     // Stolt source bound: indices below L/2
   float Ahi, Alo;
   bool st0, st1;
   float stmul;
+  int n_out;                 // kept outputs z < n_out
   __device__ __forceinline__ void load(int m, float2 (&x)[2]) const {
     x[0] = x[1] = make_float2(0.f, 0.f);
     if (m < 1) return;                                // m < L/2 (upper half is pruned)
@@ -119,6 +122,7 @@ struct FkInvCtx {
   }
   __device__ __forceinline__ float2* sm(int t) const { return t == 0 ? W0 : W1; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[2]) const {   // every l the schedule keeps
+    if (l >= n_out) return;
     if (st0) Cpx<TS>::put(out0 + l, cscale(cconj(x[0]), stmul));
     if (st1) Cpx<TS>::put(out1 + l, cscale(cconj(x[1]), stmul));
   }
@@ -129,7 +133,8 @@ __host__ __device__ constexpr int fk_ppc(int L, int v) {
   return L <= 128 ? (v == 0 ? 16 : 32)
        : L <= 256 ? (v == 0 ? 8 : 16)
        : L <= 512 ? (v == 0 ? 4 : 8)
-       : (L <= 1024 ? (v == 0 ? 2 : 4) : (v == 0 ? 2 : 1));
+       : L <= 1024 ? (v == 0 ? 2 : 4)
+       : L <= 4096 ? (v == 0 ? 2 : 1) : 1;
 }
 
 // kAlias: two shared buffers per pencil instead of three (the pencil's
@@ -143,9 +148,9 @@ template <int L, int PPC_, bool kAlias = false> struct FkTile {
   static constexpr int MIN_BLOCKS = kAlias ? (65536 / (THREADS * 96) > 1 ? 65536 / (THREADS * 96) : 1) : 1;
 };
 
-// kPad2: the temporal axis is zero-padded to L = 2n (the forward input's upper
-// half is zero and only z < n is kept); otherwise L = n and every output is
-// kept. Either way the Stolt source must stay below L/2.
+// kPad2: the temporal axis is zero-padded to L >= 2n (the forward input's
+// upper half is zero and only z < n is kept); otherwise L = n and every
+// output is kept. Either way the Stolt source must stay below L/2.
 template <int L, int PPC, class TS, bool kPad2, bool kAlias>
 __global__ void __launch_bounds__(FkTile<L, PPC, kAlias>::THREADS, FkTile<L, PPC, kAlias>::MIN_BLOCKS)
 fk_zstage_kernel(const FkZParams p) {
@@ -163,7 +168,7 @@ fk_zstage_kernel(const FkZParams p) {
   float2* W1 = fk_sm + ((kAlias ? 1 : 2) * PPC + w) * S::SMEM;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
-    FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul};
+    FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul, p.n};
     fftn_run<L, 1, kPad2, false>(ctx, j0);
   }
   __syncthreads();
@@ -178,7 +183,7 @@ fk_zstage_kernel(const FkZParams p) {
   const long long o_mirror = ((long long)mkx * twob + mky) * p.n;
   // the partner is stored only where it is not itself a stored pencil
   FkInvCtx<L, TS, kAlias> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, L / 2, A.x, A.y,
-                      valid, valid && kx > 0 && 2 * kx < p.a_pad, p.st_scale};
+                      valid, valid && kx > 0 && 2 * kx < p.a_pad, p.st_scale, p.n};
   fftn_run<L, 2, true, kPad2>(ctx, j0);
 }
 
@@ -209,7 +214,7 @@ cudaError_t launch_fk_one(const FkZParams& p, int tile, cudaStream_t s) {
 template <class TS>
 cudaError_t launch_fk_typed(const FkZParams& p, int tile, cudaStream_t s) {
   if (p.npencils <= 0) return cudaErrorInvalidValue;
-  switch (p.pad * p.n) {
+  switch (p.L) {
     case 16: return launch_fk_one<16, TS>(p, tile, s);
     case 32: return launch_fk_one<32, TS>(p, tile, s);
     case 64: return launch_fk_one<64, TS>(p, tile, s);
@@ -219,6 +224,7 @@ cudaError_t launch_fk_typed(const FkZParams& p, int tile, cudaStream_t s) {
     case 1024: return launch_fk_one<1024, TS>(p, tile, s);
     case 2048: return launch_fk_one<2048, TS>(p, tile, s);
     case 4096: return launch_fk_one<4096, TS>(p, tile, s);
+    case 8192: return launch_fk_one<8192, TS>(p, tile, s);
     default: return cudaErrorInvalidValue;
   }
 }

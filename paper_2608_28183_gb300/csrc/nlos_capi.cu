@@ -118,6 +118,7 @@ struct HostPipe {
 struct nlos_plan_s {
   nlos_plan_desc_t d{};
   int a = 0, b = 0, n = 0;
+  int Lx = 0, Ly = 0, Lt = 0;           // transform lengths (padded, powers of two)
   int storage = kF32;
   int nz = 0;
   std::map<int, float2*> tw;            // twiddle table per FFT length
@@ -228,27 +229,26 @@ float2 split_ff(double v) {
 }
 
 // ---------------------------------------------------------------------------
-// f-k plan: Stolt constants A_x(p) = (n s_x p~ / a)^2 with s_x = c dt / (2 dx)
-// (Alg. 1's s per axis), signed index p~ of the 2a-point padded axis.
+// f-k plan: Stolt constants A_x(p) = (Lt s_x p~ / Lx)^2 with s_x = c dt / (2 dx)
+// (Alg. 1's s per axis), signed index p~ of the Lx-point padded axis; for
+// Lx = 2a, Lt = 2n this is Alg. 1's (n s_x p~ / a)^2.
 // ---------------------------------------------------------------------------
 nlos_status_t build_fk(nlos_plan_s* p) {
   const auto& d = p->d;
-  const int pf = d.pad_factor;
-  const int Lx = pf * p->a, Ly = pf * p->b, Lt = pf * p->n;
+  const int Lx = p->Lx, Ly = p->Ly, Lt = p->Lt;
   const double dx = d.wall_w_m / d.nx, dy = d.wall_h_m / d.ny;
   const double sx = kC * d.bin_width_s / (2.0 * dx);
   const double sy = kC * d.bin_width_s / (2.0 * dy);
-  // signed index p~ of the Lx-point axis; mu^2 = A + m^2 with A = (n s_x p~ / a)^2 + (n s_y q~ / b)^2
-  // for either padding (the padded and unpadded grids give the same constant)
+  // mu^2 = A + m^2 with A = (Lt s_x p~ / Lx)^2 + (Lt s_y q~ / Ly)^2
   std::vector<float2> ax(Lx), ay(Ly);
   for (int i = 0; i < Lx; ++i) {
     const int pt = i < Lx / 2 ? i : i - Lx;
-    const double v = (double)p->n * sx * pt / p->a;
+    const double v = (double)Lt * sx * pt / Lx;
     ax[i] = split_ff(v * v);
   }
   for (int i = 0; i < Ly; ++i) {
     const int qt = i < Ly / 2 ? i : i - Ly;
-    const double v = (double)p->n * sy * qt / p->b;
+    const double v = (double)Lt * sy * qt / Ly;
     ay[i] = split_ff(v * v);
   }
   nlos_status_t st;
@@ -293,11 +293,12 @@ nlos_status_t build_pf(nlos_plan_s* p) {
   const double lam = d.wavelength_m > 0 ? d.wavelength_m : 4.0 * dx;
   const double cyc = d.cycles > 0 ? d.cycles : 5.0;
   const double f0 = kC / lam;
-  const double df = 1.0 / (p->n * d.bin_width_s);
+  // temporal DFT length Lt: n, or the next power of two (zero-padded transient)
+  const double df = 1.0 / (p->Lt * d.bin_width_s);
   const int k0 = (int)llround(f0 / df);
   const double sigma_f = 1.0 / (2.0 * kPi * (cyc / (6.0 * f0)));
   const int kh = (int)llround(5.0 * sigma_f / df);
-  const int lo = std::max(1, k0 - kh), hi = std::min(p->n / 2 - 1, k0 + kh);
+  const int lo = std::max(1, k0 - kh), hi = std::min(p->Lt / 2 - 1, k0 + kh);
   if (hi < lo) return fail(NLOS_ERR_INVALID_ARG, "virtual-wave band is empty (k0=%d, n=%d)", k0, p->n);
   p->k_lo = lo;
   p->F = hi - lo + 1;
@@ -310,7 +311,7 @@ nlos_status_t build_pf(nlos_plan_s* p) {
   }
   const double lambda_min = kC / (hi * df);
   // radial sampling over the padded aperture
-  const int Nu = 2 * p->a, Nv = 2 * p->b;
+  const int Nu = p->Lx, Nv = p->Ly;
   const double r_max = sqrt(pow(0.5 * Nu * dx, 2) + pow(0.5 * Nv * dy, 2));
   const double rho_max = sqrt(pow(1.0 / (2.0 * dx), 2) + pow(1.0 / (2.0 * dy), 2));
   const int sig_s = d.sigma_s > 0 ? d.sigma_s : 2;
@@ -437,22 +438,23 @@ nlos_status_t build_pf(nlos_plan_s* p) {
 // phasor-field plan (both kernel representations)
 nlos_status_t pf_finish(nlos_plan_s* p, const std::vector<float>& w) {
   nlos_status_t st;
-  const int Nu = 2 * p->a, Nv = 2 * p->b;
+  const int Nu = p->Lx, Nv = p->Ly;
   if ((st = upload(p, &p->w, w, "band weights")) != NLOS_OK) return st;
-  std::vector<float2> phase(p->n);
-  for (int m = 0; m < p->n; ++m) {
-    const double t = 2.0 * kPi * m / p->n;
+  std::vector<float2> phase(p->Lt);
+  for (int m = 0; m < p->Lt; ++m) {
+    const double t = 2.0 * kPi * m / p->Lt;
     phase[m] = make_float2((float)cos(t), (float)-sin(t));
   }
   if ((st = upload(p, &p->phase, phase, "phase table")) != NLOS_OK) return st;
-  if ((st = ensure_twiddles(p, p->n)) != NLOS_OK) return st;
+  if ((st = ensure_twiddles(p, p->Lt)) != NLOS_OK) return st;
   if ((st = ensure_twiddles(p, Nu)) != NLOS_OK) return st;
   if ((st = ensure_twiddles(p, Nv)) != NLOS_OK) return st;
   const size_t cb = complex_bytes(p->storage);
   const long long a = p->a, b = p->b, F = p->F, D = p->D;
-  const size_t b0 = std::max(a * b * F, 2 * a * b * D) * cb;       // P, then the y-inverse output
-  const size_t b1 = std::max(a * 2 * b * F, 4 * a * b * D) * cb;   // y-transformed P, then C
-  const size_t b2 = 4 * a * b * F * cb;                            // Phat
+  const long long U = Nu, V = Nv;
+  const size_t b0 = std::max(a * b * F, U * b * D) * cb;           // P, then the y-inverse output
+  const size_t b1 = std::max(a * V * F, U * V * D) * cb;           // y-transformed P, then C
+  const size_t b2 = U * V * F * cb;                                // Phat
   p->off[0] = 0;
   p->off[1] = align256(b0);
   p->off[2] = p->off[1] + align256(b1);
@@ -588,7 +590,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     inv_s = scal + 1;
     inv_s2 = scal + 2;
   }
-  const long long pf = p->d.pad_factor, Lx = pf * a, Ly = pf * b, Lt = pf * n, hx = Lx / 2 + 1;
+  const long long pf = p->d.pad_factor, Lx = p->Lx, Ly = p->Ly, Lt = p->Lt, hx = Lx / 2 + 1;
   const float g2a = pass_scale(st, (int)Lx), g2b = pass_scale(st, (int)Ly), g2n = pass_scale(st, (int)Lt);
   // FK1: x forward (real input, scaled by t/(n-1), zero-padded to Lx, kx in [0, Lx/2])
   AxisLaunch l = axis(st, (int)Lx, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)hx, 0, g2a, p->tw[(int)Lx], p->tiles[sid]);
@@ -620,6 +622,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   z.a_pad = (int)Lx;
   z.b_pad = (int)Ly;
   z.n = (int)n;
+  z.L = (int)Lt;
   z.pad = (int)pf;
   z.npencils = hx * Ly;
   z.ld_scale = g2n;
@@ -670,7 +673,8 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     s_in = scal;
     inv_s = scal + 1;
   }
-  const float gn = pass_scale(st, n), g2a = pass_scale(st, 2 * a), g2b = pass_scale(st, 2 * b);
+  const long long Nu = p->Lx, Nv = p->Ly, Lt = p->Lt;
+  const float gn = pass_scale(st, (int)Lt), g2a = pass_scale(st, (int)Nu), g2b = pass_scale(st, (int)Nv);
   // depth-sum output scale: undoes the stored kernel's scale and, for 16-bit
   // storage, divides by 16 so sums over the band stay inside the half range
   const float c3 = st == kF32 ? 1.0f : (float)(1.0 / (16.0 * p->kr_scale));
@@ -679,9 +683,10 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   PfBandParams bp{};
   bp.H = H;
   bp.P = b0;
-  bp.tw = p->tw[n];
+  bp.tw = p->tw[(int)Lt];
   bp.w = p->w;
   bp.n = (int)n;
+  bp.L = (int)Lt;
   bp.k_lo = p->k_lo;
   bp.F = (int)F;
   bp.npencils = a * b;
@@ -692,23 +697,23 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   NLOS_MARK(p, s, sid++);
   // PF2: top-left padding and 2D forward transform (y then x) of every band slice
   const void* P = P_in ? P_in : b0;
-  AxisLaunch l = axis(st, 2 * b, a, P, b1, F, b * F, F, 2 * b * F, F, (int)b, 2 * (int)b, 0, g2b, p->tw[2 * b], p->tiles[sid]);
+  AxisLaunch l = axis(st, (int)Nv, a, P, b1, F, b * F, F, Nv * F, F, (int)b, (int)Nv, 0, g2b, p->tw[(int)Nv], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf y-forward");
   NLOS_MARK(p, s, sid++);
-  l = axis(st, 2 * a, 1, b1, b2, 2 * b * F, 0, 2 * b * F, 0, 2 * b * F, (int)a, 2 * (int)a, 0, g2a, p->tw[2 * a], p->tiles[sid]);
+  l = axis(st, (int)Nu, 1, b1, b2, Nv * F, 0, Nv * F, 0, Nv * F, (int)a, (int)Nu, 0, g2a, p->tw[(int)Nu], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf x-forward");
   NLOS_MARK(p, s, sid++);
   if (p->d.method == NLOS_PHASOR_DENSE) {
     // PF3, dense kernel: C = sum_f Phat * Khat (Alg. 3), every pixel written
-    PfDenseParams dp{static_cast<const float2*>(b2), p->Kd, static_cast<float2*>(b1), 4 * a * b, (int)F, (int)D};
+    PfDenseParams dp{static_cast<const float2*>(b2), p->Kd, static_cast<float2*>(b1), Nu * Nv, (int)F, (int)D};
     NLOS_CU(launch_pf_dense(dp, s), "pf dense depth sum");
   } else {
     // PF3: depth sum (pixels beyond the cutoff stay zero)
-    NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * 4 * a * b * D, s), "pf clear");
+    NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * Nu * Nv * D, s), "pf clear");
     PfDepthParams dp{};
     dp.Phat = b2;
     dp.K = p->Kr;
@@ -725,15 +730,15 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   }
   NLOS_MARK(p, s, sid++);
   // PF4: 2D inverse transform per depth (y then x), crop, |.| with 1/(4ab)
-  l = axis(st, 2 * b, 2 * a, b1, b0, D, 2 * b * D, D, b * D, D, 2 * (int)b, (int)b, 1, g2b, p->tw[2 * b], p->tiles[sid]);
+  l = axis(st, (int)Nv, Nu, b1, b0, D, Nv * D, D, b * D, D, (int)Nv, (int)b, 1, g2b, p->tw[(int)Nv], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "pf y-inverse");
   NLOS_MARK(p, s, sid++);
   // scales the data carries into this last pass (it applies none of its own)
   const double gprod = (double)gn * g2b * g2a * c3_data * g2b;
-  const float fscale = (float)(1.0 / (4.0 * a * b * gprod));
-  l = axis(st, 2 * a, 1, b0, vol, b * D, 0, b * D, 0, b * D, 2 * (int)a, (int)a, 1, fscale, p->tw[2 * a], p->tiles[sid]);
+  const float fscale = (float)(1.0 / ((double)Nu * Nv * gprod));
+  l = axis(st, (int)Nu, 1, b0, vol, b * D, 0, b * D, 0, b * D, (int)Nu, (int)a, 1, fscale, p->tw[(int)Nu], p->tiles[sid]);
   l.store_mode = p->d.output == NLOS_OUT_COMPLEX ? kStoreCpx32 : kStoreAbs;
   l.p.st_dev_scale = inv_s;
   l.err = err;
@@ -757,7 +762,7 @@ nlos_status_t run_plan(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaS
 // along y then x through the axis kernels).
 nlos_status_t build_dense(nlos_plan_s* p, const std::vector<double>& kappa, const std::vector<double>& depth,
                           int sig_s, int sig_t, double dx, double dy) {
-  const int Nu = 2 * p->a, Nv = 2 * p->b;
+  const int Nu = p->Lx, Nv = p->Ly;
   const long long FD = (long long)p->F * p->D;
   const size_t bytes = sizeof(float2) * (size_t)Nu * Nv * FD;
   nlos_status_t st;
@@ -834,12 +839,11 @@ nlos_status_t validate(const nlos_plan_desc_t* d) {
     return fail(NLOS_ERR_UNSUPPORTED, "the unpadded variant exists for f-k only");
   if (d->pad_factor == 1 && (d->nx < 16 || d->ny < 16))
     return fail(NLOS_ERR_UNSUPPORTED, "unpadded f-k needs nx, ny >= 16");
-  if (!is_pow2(d->nx) || !is_pow2(d->ny) || !is_pow2(d->nt))
-    return fail(NLOS_ERR_UNSUPPORTED, "sizes must be powers of two");
+  if (d->pad_factor == 1 && (!is_pow2(d->nx) || !is_pow2(d->ny) || !is_pow2(d->nt)))
+    return fail(NLOS_ERR_UNSUPPORTED, "unpadded f-k needs power-of-two sizes");
   if (d->nx < 8 || d->ny < 8 || d->nx > 1024 || d->ny > 1024)
     return fail(NLOS_ERR_UNSUPPORTED, "nx, ny must be in [8, 1024]");
-  const int tmax = d->method == NLOS_FK ? 2048 : 4096;
-  if (d->nt < 16 || d->nt > tmax) return fail(NLOS_ERR_UNSUPPORTED, "nt must be in [16, %d]", tmax);
+  if (d->nt < 16 || d->nt > 4096) return fail(NLOS_ERR_UNSUPPORTED, "nt must be in [16, 4096]");
   if (d->method != NLOS_FK) {
     if (d->n_depths < 1 || d->n_depths > 8192) return fail(NLOS_ERR_INVALID_ARG, "n_depths must be in [1, 8192]");
     if (!(d->depth_min_m > 0) || d->depth_max_m < d->depth_min_m)
@@ -924,6 +928,17 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   p->a = desc->nx;
   p->b = desc->ny;
   p->n = desc->nt;
+  {
+    // transform lengths: f-k pads every axis to the next power of two >= 2x
+    // (exactly 2x for power-of-two sizes) or keeps it (pad_factor 1); phasor
+    // fields pad x and y the same way and transform t at the next power of
+    // two >= nt
+    const bool fk = desc->method == NLOS_FK;
+    const int pad = fk ? desc->pad_factor : 2;
+    p->Lx = pad == 1 ? p->a : pow2_at_least(2 * p->a);
+    p->Ly = pad == 1 ? p->b : pow2_at_least(2 * p->b);
+    p->Lt = fk ? (pad == 1 ? p->n : pow2_at_least(2 * p->n)) : pow2_at_least(p->n);
+  }
   p->storage = desc->storage;
   if (p->storage != kF32) p->stage_names.push_back("volume_scale");
   const char* fk_names[] = {"fk_x_forward", "fk_y_forward", "fk_stolt_z", "fk_y_inverse", "fk_x_inverse"};
@@ -934,8 +949,7 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   for (const std::string& nm : p->stage_names) {
     const bool xs = nm.find("_x_") != std::string::npos, ys = nm.find("_y_") != std::string::npos;
     p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : (nm == "fk_stolt_z" ? 2 : 0));
-    const int pf = desc->method == NLOS_FK ? desc->pad_factor : 2;
-    p->stage_len.push_back(xs ? pf * p->a : ys ? pf * p->b : nm == "fk_stolt_z" ? pf * p->n : 0);
+    p->stage_len.push_back(xs ? p->Lx : ys ? p->Ly : nm == "fk_stolt_z" ? p->Lt : 0);
   }
   // default launch shapes: TMA-staged axis transforms (each falls back to
   // direct loads where the layout does not allow TMA); the autotuner may
@@ -1027,9 +1041,10 @@ nlos_status_t nlos_bin_phasors(nlos_plan_t p, const uint32_t* pixel, const uint3
     PfBandParams bp{};
     bp.H = Hs;
     bp.P = phasors;
-    bp.tw = p->tw[p->n];
+    bp.tw = p->tw[p->Lt];
     bp.w = p->w;
     bp.n = p->n;
+    bp.L = p->Lt;
     bp.k_lo = p->k_lo;
     bp.F = p->F;
     bp.npencils = (long long)p->a * p->b;
@@ -1047,7 +1062,7 @@ nlos_status_t nlos_bin_phasors(nlos_plan_t p, const uint32_t* pixel, const uint3
   q.count = count;
   q.npix = (uint32_t)((long long)p->a * p->b);
   q.nt = p->n;
-  q.n = p->n;
+  q.n = p->Lt;
   q.t0 = t0_ticks;
   q.tpb = ticks_per_bin;
   q.phase = p->phase;

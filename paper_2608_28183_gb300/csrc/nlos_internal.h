@@ -77,11 +77,12 @@ __host__ __device__ constexpr int fk_tile_count(int L) { return 4; }
 struct FkZParams {
   const void* G;
   void* psi;
-  const float2* tw;            // twiddles for the temporal length L = pad * n
-  const float2* ax;            // [a_pad] float-float (hi, lo) of (n s_x p~ / a)^2
-  const float2* ay;            // [b_pad] float-float of (n s_y q~ / b)^2
-  int a_pad, b_pad, n;         // padded lateral lengths (pad * a, pad * b), time bins
-  int pad;                     // 2: zero-padded x2 on every axis; 1: unpadded
+  const float2* tw;            // twiddles for the temporal length L
+  const float2* ax;            // [a_pad] float-float (hi, lo) of (L s_x p~ / a_pad)^2
+  const float2* ay;            // [b_pad] float-float of (L s_y q~ / b_pad)^2
+  int a_pad, b_pad, n;         // padded lateral lengths, time bins (pencil stride, kept outputs)
+  int L;                       // temporal transform length (power of two)
+  int pad;                     // 2: zero-padded (L >= 2n); 1: unpadded (L = n)
   long long npencils;          // (a_pad / 2 + 1) * b_pad
   float ld_scale;              // multiplies forward loads
   const float* ld_dev_scale;   // optional device scalar multiplying forward loads
@@ -94,9 +95,10 @@ cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStre
 struct PfBandParams {
   const void* H;
   void* P;
-  const float2* tw;            // twiddles for L = n
+  const float2* tw;            // twiddles for L
   const float* w;              // [F]
-  int n, k_lo, F;
+  int n, k_lo, F;              // n: samples per pencil (stride of H)
+  int L;                       // DFT length (power of two >= n; samples beyond n are zero)
   long long npencils;          // a * b
   float ld_scale;
   const float* ld_dev_scale;

@@ -24,8 +24,9 @@ struct PfBandCtx {
   bool valid;
   float ldmul, stmul;
   int accumulate;
+  int n_in;                    // samples of the pencil; the DFT runs over L >= n_in
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = valid ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f) : make_float2(0.f, 0.f);
+    x[0] = (valid && l < n_in) ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f) : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
@@ -56,7 +57,8 @@ pf_band_kernel(const PfBandParams p) {
   const long long q = valid ? pid : 0;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   PfBandCtx<L, TR, TS> ctx{static_cast<const TR*>(p.H) + q * p.n, static_cast<TS*>(p.P) + q * p.F,
-                           pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale, p.accumulate};
+                           pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale, p.accumulate,
+                           p.n};
   fftn_run<L, 1, false, false>(ctx, j0);
 }
 
@@ -75,7 +77,7 @@ static cudaError_t launch_band_one(const PfBandParams& p, cudaStream_t s) {
 
 template <class TR, class TS>
 static cudaError_t launch_band_typed(const PfBandParams& p, cudaStream_t s) {
-  switch (p.n) {
+  switch (p.L) {
     case 16: return launch_band_one<16, TR, TS>(p, s);
     case 32: return launch_band_one<32, TR, TS>(p, s);
     case 64: return launch_band_one<64, TR, TS>(p, s);

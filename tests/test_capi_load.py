@@ -54,7 +54,7 @@ def _create(lib, **kw):
     (dict(nx=0), 1), (dict(bin_width_s=0.0), 1), (dict(wall_w_m=-1.0), 1), (dict(method=7), 1),
     (dict(storage=9), 1), (dict(pad_factor=3), 1), (dict(pad_factor=1, method=1, n_depths=8,
                                                            depth_min_m=0.5, depth_max_m=1.0), 4),
-    (dict(pad_factor=1, nx=8), 4), (dict(nx=24), 4), (dict(nt=4096), 4),
+    (dict(pad_factor=1, nx=8), 4), (dict(pad_factor=1, nx=24), 4), (dict(nt=8192), 4), (dict(nx=2048), 4),
     (dict(nx=4, ny=4), 4), (dict(method=1, n_depths=0), 1),
     (dict(method=1, n_depths=8, depth_min_m=1.0, depth_max_m=0.5), 1), (dict(output=2), 1), (dict(output=-1), 1),
 ])

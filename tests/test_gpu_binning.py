@@ -111,6 +111,23 @@ def test_bin_phasors_accumulate(route):
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
 
 
+@pytest.mark.parametrize("route", ["direct", "histogram"])
+def test_bin_phasors_any_length(route):
+    """A temporal axis that is not a power of two: the phasors are taken over
+    the zero-padded DFT length."""
+    from paper_2608_28183_gb300 import nlos
+    g = synth.Geometry(20, 12, 200, 32e-12, 0.7, 0.4)
+    plan = nlos.plan_for_capture(g, "pf", n_depths=8, depth_min_m=0.3, depth_max_m=0.9)
+    oplan = pf.make_plan(g.nx, g.ny, g.nt, g.bin_width_s, g.wall_w_m, g.wall_h_m, 8, 0.3, 0.9)
+    assert plan.band == (int(oplan.band.bins[0]), len(oplan.band.bins))
+    s = _stream(g, 12, "shuffled")
+    px, tk = _dev(s)
+    P = plan.bin_phasors(px, tk, s.t0, s.ticks_per_bin, route=route).cpu().numpy()
+    ref = binning.bin_phasors(s.pixel, s.ticks, g.nx, g.ny, g.nt, s.t0, s.ticks_per_bin,
+                              oplan.band.bins, oplan.band.weights)
+    assert np.linalg.norm(P - ref) / np.linalg.norm(ref) <= 1e-5
+
+
 def test_reconstruct_from_binned_phasors():
     """Photons -> phasors -> volume equals photons -> histogram -> volume, and the oracle."""
     from paper_2608_28183_gb300 import nlos

@@ -182,3 +182,30 @@ def test_fk_unpadded_fp16():
     ref = fk.fk_reconstruct(exact_input(cap.counts, torch.float16), geom.bin_width_s, geom.wall_w_m,
                             geom.wall_h_m, pad_factor=1)
     assert rel_l2(got, ref) <= 2e-3
+
+
+ANY_SIZE = [
+    synth.Geometry(24, 40, 200, 32e-12, 0.8, 1.3),       # every axis padded to the next power of two >= 2x
+    synth.Geometry(20, 28, 300, 24e-12, 0.7, 0.9),
+    synth.Geometry(96, 80, 300, 24e-12, 1.2, 1.0),
+]
+
+
+@pytest.mark.parametrize("geom", ANY_SIZE, ids=lambda g: f"{g.nx}x{g.ny}x{g.nt}")
+def test_fk_parity_any_size(geom):
+    """Grids with no power-of-two axis against the oracle with the same padding."""
+    cap = _noise_capture(geom, seed=geom.nt)
+    plan = _plan(geom)
+    got = _gpu(plan, cap.counts)
+    ref = _oracle(geom, exact_input(cap.counts, torch.float32))
+    assert rel_l2(got, ref) <= 1e-5
+    assert same_peak(got, ref)
+
+
+def test_fk_any_size_fp16():
+    geom = ANY_SIZE[1]
+    cap = _noise_capture(geom, seed=4)
+    plan = _plan(geom, "f16")
+    got = _gpu(plan, cap.counts)
+    ref = _oracle(geom, exact_input(cap.counts, torch.float16))
+    assert rel_l2(got, ref) <= 2e-3

@@ -81,3 +81,21 @@ def test_pf_parity_workload_128x128x1024():
     err = rel_l2(got, ref)
     assert err <= 1e-5, err
     assert same_peak(got, ref)
+
+
+ANY_SIZE = [
+    (synth.Geometry(24, 20, 300, 16e-12, 0.8, 0.7), (20, 0.35, 0.7), (0.4, 0.65)),
+    (synth.Geometry(48, 40, 600, 16e-12, 1.2, 1.0), (33, 0.4, 1.2), (0.5, 1.1)),
+]
+
+
+@pytest.mark.parametrize("geom,depths,zr", ANY_SIZE, ids=["24x20x300", "48x40x600"])
+def test_pf_parity_any_size(geom, depths, zr):
+    """Grids with no power-of-two axis: x and y padded to the next power of two
+    >= 2x, t transformed at the next power of two."""
+    plan, oplan = _pair(geom, depths)
+    cap = _capture(geom, seed=geom.nt, zr=zr)
+    got = _gpu(plan, cap.counts)
+    ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float32), oplan)
+    assert rel_l2(got, ref) <= 1e-5
+    assert same_peak(got, ref)

@@ -36,10 +36,11 @@ CASES = [
     (synth.Geometry(16, 8, 512, 16e-12, 0.8, 0.4), (9, 0.4, 1.0), (0.5, 0.9), {}),
     (synth.Geometry(16, 16, 256, 24e-12, 0.6, 0.6), (10, 0.3, 0.9), (0.4, 0.8),
      dict(sigma_s=1, sigma_t=1, delta_m=0.05)),
+    (synth.Geometry(12, 10, 200, 32e-12, 0.5, 0.4), (7, 0.3, 0.9), (0.4, 0.8), {}),   # no power of two
 ]
 
 
-@pytest.mark.parametrize("geom,depths,zr,kw", CASES, ids=["8x8", "16x16", "16x8", "16x16-nonconfocal"])
+@pytest.mark.parametrize("geom,depths,zr,kw", CASES, ids=["8x8", "16x16", "16x8", "16x16-nonconfocal", "12x10x200"])
 def test_dense_matches_direct_rsd(geom, depths, zr, kw):
     from paper_2608_28183_gb300 import nlos
     D, dmin, dmax = depths
