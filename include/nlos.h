@@ -412,6 +412,14 @@ nlos_status_t nlos_coherence_merge(const void* const* frames, int nw, long long 
  */
 nlos_status_t nlos_dda(const float* const* frames, int nw, long long nxy, int nz, float* out, void* stream);
 
+/* Tensor-core self-check (tcgen05 on sm_103a): one CTA computes
+ * D = A B^T for fixed small-integer A (128 x 64) and B (n_cols x 64) with
+ * f16 MMAs into tensor memory and writes D (128 x n_cols float32, row-major)
+ * to the device buffer out; the caller compares it with the exact product.
+ * *code receives the device error word (non-zero: the MMA completion wait
+ * gave up, NLOS_ERR_TIMEOUT). Synchronous. n_cols: multiple of 16 in [16, 256]. */
+nlos_status_t nlos_selftest_umma(int n_cols, float* out, int* code);
+
 /* Testing hook for the failure path (fault injection on the host): the k-th
  * device allocation that plan creation or host staging makes from now on
  * (k >= 1) fails as if the device were out of memory, and the call returns

@@ -130,6 +130,13 @@ struct nlos_plan_s {
   float* w = nullptr;
   float2* phase = nullptr;              // [n] exp(-2 pi i m / n) for photon binning
   float2* Kd = nullptr;                 // dense method: Khat [Nu*Nv][F][D]
+  // tensor-core depth sum (16-bit storage): B operand blocks and 128-pixel tiles
+  void* Bu = nullptr;
+  int2* tu_i01 = nullptr;
+  int* tu_pix = nullptr;
+  float* tu_alpha = nullptr;
+  float* tu_acut = nullptr;
+  int ntiles_u = 0, Db_u = 0, nblk_u = 0, KC_u = 0;
   void* Kr = nullptr;
   int2* ch_i01 = nullptr;
   int* ch_pix = nullptr;
@@ -149,7 +156,8 @@ struct nlos_plan_s {
   // per-stage tile variant (autotuner) and the transform length it applies to
   std::vector<int> tiles;
   std::vector<int> stage_len;     // 0: stage has no variants
-  std::vector<int> stage_kind;    // 1: strided-axis transform, 2: f-k temporal stage, 3: real-input axis
+  std::vector<int> stage_kind;    // 1: strided-axis transform, 2: f-k temporal stage, 3: real-input axis,
+                                  // 4: depth sum with a tensor-core variant
   bool tuned = false;
   // stage tracing
   std::vector<std::string> stage_names;
@@ -380,6 +388,16 @@ nlos_status_t build_pf(nlos_plan_s* p) {
     st = dalloc(p, &Kr, complex_bytes(p->kr_storage) * (size_t)n_rho * NFD, "radial kernel");
     if (st == NLOS_OK) e = launch_kr_store(dK64, Kr, (long long)n_rho * NFD, p->kr_storage, p->kr_scale, 0);
   }
+  if (e == cudaSuccess && st == NLOS_OK && p->storage == kF16) {
+    // the same kernel as tensor-core B operands: [Kr -Ki; Ki Kr] per bin and depth block
+    p->Db_u = p->D <= 16 ? 16 : p->D <= 32 ? 32 : p->D <= 64 ? 64 : 128;
+    p->nblk_u = (p->D + p->Db_u - 1) / p->Db_u;
+    p->KC_u = (2 * p->F + kUmmaKChunk - 1) / kUmmaKChunk;
+    const size_t bbytes = (size_t)n_rho * p->nblk_u * p->KC_u * (2 * p->Db_u) * kUmmaKChunk * 2;
+    st = dalloc(p, &p->Bu, bbytes, "tensor-core kernel operands");
+    if (st == NLOS_OK)
+      e = launch_kr_store_umma(dK64, p->Bu, n_rho, p->F, p->D, p->Db_u, p->nblk_u, p->KC_u, p->kr_scale, 0);
+  }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   free_tmp();
   if (st != NLOS_OK) return st;
@@ -430,6 +448,34 @@ nlos_status_t build_pf(nlos_plan_s* p) {
     if ((st = upload(p, &p->ch_pix, cp, "chunk table")) != NLOS_OK) return st;
     if ((st = upload(p, &p->ch_alpha, ca, "chunk table")) != NLOS_OK) return st;
     if ((st = upload(p, &p->ch_acut, cc, "chunk table")) != NLOS_OK) return st;
+  }
+  if (p->Bu) {
+    // 128-pixel tiles of pixels sharing (i0, i1) for the tensor-core depth sum
+    std::vector<int2> ti;
+    std::vector<int> tp;
+    std::vector<float> ta, tc;
+    for (size_t s0 = 0; s0 < px.size();) {
+      size_t e2 = s0;
+      while (e2 < px.size() && px[e2].i0 == px[s0].i0 && px[e2].i1 == px[s0].i1) ++e2;
+      for (size_t c = s0; c < e2; c += kUmmaTile) {
+        ti.push_back(make_int2(px[s0].i0, px[s0].i1));
+        for (int q = 0; q < kUmmaTile; ++q) {
+          const size_t idx = c + q;
+          const bool ok = idx < e2;
+          tp.push_back(ok ? px[idx].pix : -1);
+          ta.push_back(ok ? px[idx].alpha : 0.f);
+          tc.push_back(ok ? px[idx].acut : 0.f);
+        }
+      }
+      s0 = e2;
+    }
+    p->ntiles_u = (int)ti.size();
+    if (p->ntiles_u > 0) {
+      if ((st = upload(p, &p->tu_i01, ti, "tile table")) != NLOS_OK) return st;
+      if ((st = upload(p, &p->tu_pix, tp, "tile table")) != NLOS_OK) return st;
+      if ((st = upload(p, &p->tu_alpha, ta, "tile table")) != NLOS_OK) return st;
+      if ((st = upload(p, &p->tu_acut, tc, "tile table")) != NLOS_OK) return st;
+    }
   }
   return pf_finish(p, w);
 }
@@ -712,8 +758,28 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     PfDenseParams dp{static_cast<const float2*>(b2), p->Kd, static_cast<float2*>(b1), Nu * Nv, (int)F, (int)D};
     NLOS_CU(launch_pf_dense(dp, s), "pf dense depth sum");
   } else {
-    // PF3: depth sum (pixels beyond the cutoff stay zero)
+    // PF3: depth sum (pixels beyond the cutoff stay zero); 16-bit plans run it
+    // on the tensor cores unless the stage's launch shape asks for the FFMA form
     NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * Nu * Nv * D, s), "pf clear");
+    if (p->Bu && p->tiles[sid] == 0) {
+      PfUmmaParams up{};
+      up.Phat = b2;
+      up.B = p->Bu;
+      up.C = b1;
+      up.tile_i01 = p->tu_i01;
+      up.tile_pix = p->tu_pix;
+      up.tile_alpha = p->tu_alpha;
+      up.tile_acut = p->tu_acut;
+      up.ntiles = p->ntiles_u;
+      up.F = (int)F;
+      up.D = (int)D;
+      up.Db = p->Db_u;
+      up.nblk = p->nblk_u;
+      up.KC = p->KC_u;
+      up.scale = c3;
+      up.err = err;
+      NLOS_CU(launch_pf_umma(up, s), "pf depth sum (tensor cores)");
+    } else {
     PfDepthParams dp{};
     dp.Phat = b2;
     dp.K = p->Kr;
@@ -727,6 +793,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     dp.D = (int)D;
     dp.scale = c3;
     NLOS_CU(launch_pf_depth(dp, st, p->kr_storage, s), "pf depth sum");
+    }
   }
   NLOS_MARK(p, s, sid++);
   // PF4: 2D inverse transform per depth (y then x), crop, |.| with 1/(4ab)
@@ -948,7 +1015,8 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   else for (const char* nm : pf_names) p->stage_names.push_back(nm);
   for (const std::string& nm : p->stage_names) {
     const bool xs = nm.find("_x_") != std::string::npos, ys = nm.find("_y_") != std::string::npos;
-    p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : (nm == "fk_stolt_z" ? 2 : 0));
+    const bool umma = nm == "pf_depth_sum" && desc->method == NLOS_PHASOR_RSD && desc->storage == NLOS_F16;
+    p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : nm == "fk_stolt_z" ? 2 : umma ? 4 : 0);
     p->stage_len.push_back(xs ? p->Lx : ys ? p->Ly : nm == "fk_stolt_z" ? p->Lt : 0);
   }
   // default launch shapes: TMA-staged axis transforms (each falls back to
@@ -1251,6 +1319,7 @@ int stage_variants(const nlos_plan_s* p, size_t i) {
   if (p->stage_kind[i] == 1) return axis_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 2) return fk_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 3) return 3 * axis_ic_count(p->stage_len[i]);
+  if (p->stage_kind[i] == 4) return 2;   // tensor cores, FFMA
   return 1;
 }
 }  // namespace

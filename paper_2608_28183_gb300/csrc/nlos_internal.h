@@ -160,6 +160,31 @@ cudaError_t launch_kr_build(const KrBuildParams& p, cudaStream_t s);
 cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int storage, double scale,
                             cudaStream_t s);
 
+// Tensor-core depth sum for 16-bit storage: per tile of up to 128 pixels that
+// share the radial pair (i0, i1), Y = A0 B(i0)^T + A1 B(i1)^T with
+// A0 = (1 - alpha) [Re Phat | Im Phat], A1 = alpha [Re Phat | Im Phat] (f16,
+// built in shared memory) and B(i) the real form of K_r[i] ([Kr -Ki; Ki Kr],
+// 2 Db output columns x Kp inputs per depth block, f16, stored per plan in the
+// operand layout); C = scale * acut * (Y_re + i Y_im).
+constexpr int kUmmaTile = 128;           // pixels per tile (MMA M)
+constexpr int kUmmaKChunk = 64;          // K columns per shared-memory chunk
+struct PfUmmaParams {
+  const void* Phat;            // [npix][F] half2
+  const void* B;               // [n_rho][nblk][KC][2 Db x 64] f16, operand layout
+  void* C;                     // [npix][D] half2
+  const int2* tile_i01;        // [ntiles]
+  const int* tile_pix;         // [ntiles][128] pixel or -1
+  const float* tile_alpha;     // [ntiles][128]
+  const float* tile_acut;      // [ntiles][128]
+  int ntiles, F, D, Db, nblk, KC;
+  float scale;
+  int* err;                    // device error word (bounded waits)
+};
+cudaError_t launch_pf_umma(const PfUmmaParams& p, cudaStream_t s);
+// K_r (float64 [n_rho][F][D]) -> B operand blocks, scaled, f16
+cudaError_t launch_kr_store_umma(const double2* K64, void* B, int n_rho, int F, int D, int Db, int nblk, int KC,
+                                 double scale, cudaStream_t s);
+
 // Dense phasor-field kernel (Alg. 3), spatial form on the signed padded grid:
 // k[x][y][f][d] = exp(i kappa_f (sigma_s R + sigma_t d + Delta)),
 // R = sqrt((x~ dx)^2 + (y~ dy)^2 + d^2), phase in float64.
