@@ -26,7 +26,8 @@ namespace nlos {
 
 namespace {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;               // two threads per tile row
+constexpr int kPairsPerThread = kUmmaKChunk / 4;   // frequency pairs of a chunk per thread
 constexpr int kWaitLimit = 1 << 21;
 
 template <int Db>
@@ -49,13 +50,22 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
   unsigned char* B0 = um_sm + 2 * S::A_BYTES;
   unsigned char* B1 = B0 + S::B_BYTES;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & (kUmmaTile - 1), half = tid >> 7;   // tile row; which half of each chunk
   const int tile = blockIdx.x;
   const int2 i01 = p.tile_i01[tile];
-  // this thread's row of the tile
-  const int pix = p.tile_pix[(size_t)tile * kUmmaTile + tid];
-  const float al = p.tile_alpha[(size_t)tile * kUmmaTile + tid];
-  const float ac = p.tile_acut[(size_t)tile * kUmmaTile + tid];
+  const int pix = p.tile_pix[(size_t)tile * kUmmaTile + row];
+  const float al = p.tile_alpha[(size_t)tile * kUmmaTile + row];
+  const float ac = p.tile_acut[(size_t)tile * kUmmaTile + row];
   const __half2* prow = static_cast<const __half2*>(p.Phat) + (size_t)(pix >= 0 ? pix : 0) * p.F;
+  // this thread's frequencies of chunk kc: f = kc * 32 + half * 16 + q, q < 16
+  auto load_chunk = [&](int kc, __half2 (&h)[kPairsPerThread]) {
+    const int f0 = kc * (kUmmaKChunk / 2) + half * kPairsPerThread;
+#pragma unroll
+    for (int q = 0; q < kPairsPerThread; ++q)
+      h[q] = (pix >= 0 && f0 + q < p.F) ? prow[f0 + q] : __floats2half2_rn(0.f, 0.f);
+  };
+  __half2 hcur[kPairsPerThread], hnext[kPairsPerThread];
+  load_chunk(0, hcur);
 
   if (warp == 0) tmem_alloc(&tbase, S::TMEM_COLS);
   if (tid == 0) {
@@ -82,22 +92,20 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
         bulk_load(B0, b0g + (size_t)kc * S::B_BYTES, S::B_BYTES, &bar_load);
         bulk_load(B1, b1g + (size_t)kc * S::B_BYTES, S::B_BYTES, &bar_load);
       }
-      // A chunk: frequencies f = kc * 32 + q as column pairs (2q, 2q + 1) = (Re, Im)
+      // A chunk: frequency f as column pair (2 (f - kc * 32), + 1) = (Re, Im)
       {
-        const int f0 = kc * (kUmmaKChunk / 2);
-        __half2 h[kUmmaKChunk / 2];
-#pragma unroll
-        for (int q = 0; q < kUmmaKChunk / 2; ++q)
-          h[q] = (pix >= 0 && f0 + q < p.F) ? prow[f0 + q] : __floats2half2_rn(0.f, 0.f);
         const float w0 = 1.f - al;
 #pragma unroll
-        for (int q = 0; q < kUmmaKChunk / 2; ++q) {
-          const uint32_t off = umma_kmajor_offset(tid, 2 * q, kUmmaKChunk);   // (2q, 2q + 1) adjacent
-          const float2 v = __half22float2(h[q]);
+        for (int q = 0; q < kPairsPerThread; ++q) {
+          const int col = 2 * (half * kPairsPerThread + q);
+          const uint32_t off = umma_kmajor_offset(row, col, kUmmaKChunk);   // (col, col + 1) adjacent
+          const float2 v = __half22float2(hcur[q]);
           *reinterpret_cast<__half2*>(A0 + off) = __floats2half2_rn(w0 * v.x, w0 * v.y);
           *reinterpret_cast<__half2*>(A1 + off) = __floats2half2_rn(al * v.x, al * v.y);
         }
       }
+      // the next chunk's phasors are in flight while this chunk's MMAs run
+      load_chunk(kc + 1 < p.KC ? kc + 1 : 0, hnext);
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -119,6 +127,8 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
       const bool done = mbar_wait_bounded(&bar_mma, phase, kWaitLimit);
       ok = __syncthreads_and(ok && done ? 1 : 0) != 0;
       phase ^= 1;
+#pragma unroll
+      for (int q = 0; q < kPairsPerThread; ++q) hcur[q] = hnext[q];
       if (!ok) break;
     }
     if (!ok) break;
@@ -126,14 +136,17 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
     tc_fence_after_sync();
     __half2* crow = static_cast<__half2*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
     const float g = p.scale * ac;
-    const uint32_t lane_base = dt + ((uint32_t)(32 * warp) << 16);
+    const uint32_t lane_base = dt + ((uint32_t)(32 * (warp & 3)) << 16);
+    constexpr int kCols = Db >= 32 ? Db / 2 : Db;          // depth columns per warp half
+    const int c0 = Db >= 32 ? half * kCols : 0;
+    const bool writer = Db >= 32 || half == 0;
 #pragma unroll
-    for (int c = 0; c < Db; c += 16) {
+    for (int c = c0; c < c0 + kCols; c += 16) {
       uint32_t re[16], im[16];
       tmem_ld16(lane_base + (uint32_t)c, re);
       tmem_ld16(lane_base + (uint32_t)(Db + c), im);
       tmem_wait_ld();
-      if (pix >= 0) {
+      if (pix >= 0 && writer) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int d = blk * Db + c + q;
