@@ -761,7 +761,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     // PF3: depth sum (pixels beyond the cutoff stay zero); 16-bit plans run it
     // on the tensor cores unless the stage's launch shape asks for the FFMA form
     NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * Nu * Nv * D, s), "pf clear");
-    if (p->Bu && p->tiles[sid] == 0) {
+    if (p->Bu && p->tiles[sid] != 1) {
       PfUmmaParams up{};
       up.Phat = b2;
       up.B = p->Bu;
@@ -778,7 +778,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
       up.KC = p->KC_u;
       up.scale = c3;
       up.err = err;
-      NLOS_CU(launch_pf_umma(up, s), "pf depth sum (tensor cores)");
+      NLOS_CU(launch_pf_umma(up, p->tiles[sid] == 2, s), "pf depth sum (tensor cores)");
     } else {
     PfDepthParams dp{};
     dp.Phat = b2;
@@ -1319,7 +1319,7 @@ int stage_variants(const nlos_plan_s* p, size_t i) {
   if (p->stage_kind[i] == 1) return axis_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 2) return fk_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 3) return 3 * axis_ic_count(p->stage_len[i]);
-  if (p->stage_kind[i] == 4) return 2;   // tensor cores, FFMA
+  if (p->stage_kind[i] == 4) return 3;   // tensor cores, FFMA, tensor cores pipelined
   return 1;
 }
 }  // namespace

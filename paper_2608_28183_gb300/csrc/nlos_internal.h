@@ -180,7 +180,8 @@ struct PfUmmaParams {
   float scale;
   int* err;                    // device error word (bounded waits)
 };
-cudaError_t launch_pf_umma(const PfUmmaParams& p, cudaStream_t s);
+// pipelined: persistent double-buffered CTAs (one per SM) instead of one CTA per tile
+cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s);
 // K_r (float64 [n_rho][F][D]) -> B operand blocks, scaled, f16
 cudaError_t launch_kr_store_umma(const double2* K64, void* B, int n_rho, int F, int D, int Db, int nblk, int KC,
                                  double scale, cudaStream_t s);

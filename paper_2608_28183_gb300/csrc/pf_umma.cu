@@ -26,9 +26,39 @@ namespace nlos {
 
 namespace {
 
-constexpr int kThreads = 256;               // two threads per tile row
-constexpr int kPairsPerThread = kUmmaKChunk / 4;   // frequency pairs of a chunk per thread
+constexpr int kThreads = 256;               // 8 warps; the epilogue gives two warps per 32 rows
 constexpr int kWaitLimit = 1 << 21;
+
+// A chunk kc of a tile: element (row r, frequency f = kc * 32 + q) of
+// (1 - alpha_r) Phat / alpha_r Phat as the column pair (2q, 2q + 1). Each warp
+// instruction covers 8 rows x 4 consecutive q: the 32 lanes hit 32 distinct
+// shared-memory banks and read 8 runs of 16 bytes from the phasor rows.
+__device__ __forceinline__ void build_a_chunk(unsigned char* A0, unsigned char* A1, const __half2* Phat, int F,
+                                              const int* tpix, const float* talpha, int kc, int tid) {
+  const int warp = tid >> 5, lane = tid & 31;
+  constexpr int kIters = kUmmaTile * (kUmmaKChunk / 2) / (32 * kThreads / 32);   // 16
+  __half2 h[kIters];
+  float al[kIters];
+#pragma unroll
+  for (int i = 0; i < kIters; ++i) {
+    const int T = i * (kThreads / 32) + warp;                 // 8-row x 4-q block
+    const int r = (T >> 3) * 8 + (lane & 7), q = (T & 7) * 4 + (lane >> 3);
+    const int f = kc * (kUmmaKChunk / 2) + q;
+    const int pix = __ldg(tpix + r);
+    al[i] = __ldg(talpha + r);
+    h[i] = (pix >= 0 && f < F) ? Phat[(size_t)pix * F + f] : __floats2half2_rn(0.f, 0.f);
+  }
+#pragma unroll
+  for (int i = 0; i < kIters; ++i) {
+    const int T = i * (kThreads / 32) + warp;
+    const int r = (T >> 3) * 8 + (lane & 7), q = (T & 7) * 4 + (lane >> 3);
+    const uint32_t off = umma_kmajor_offset(r, 2 * q, kUmmaKChunk);
+    const float2 v = __half22float2(h[i]);
+    const float w0 = 1.f - al[i];
+    *reinterpret_cast<__half2*>(A0 + off) = __floats2half2_rn(w0 * v.x, w0 * v.y);
+    *reinterpret_cast<__half2*>(A1 + off) = __floats2half2_rn(al[i] * v.x, al[i] * v.y);
+  }
+}
 
 template <int Db>
 struct UmmaSmem {
@@ -54,18 +84,10 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
   const int tile = blockIdx.x;
   const int2 i01 = p.tile_i01[tile];
   const int pix = p.tile_pix[(size_t)tile * kUmmaTile + row];
-  const float al = p.tile_alpha[(size_t)tile * kUmmaTile + row];
   const float ac = p.tile_acut[(size_t)tile * kUmmaTile + row];
-  const __half2* prow = static_cast<const __half2*>(p.Phat) + (size_t)(pix >= 0 ? pix : 0) * p.F;
-  // this thread's frequencies of chunk kc: f = kc * 32 + half * 16 + q, q < 16
-  auto load_chunk = [&](int kc, __half2 (&h)[kPairsPerThread]) {
-    const int f0 = kc * (kUmmaKChunk / 2) + half * kPairsPerThread;
-#pragma unroll
-    for (int q = 0; q < kPairsPerThread; ++q)
-      h[q] = (pix >= 0 && f0 + q < p.F) ? prow[f0 + q] : __floats2half2_rn(0.f, 0.f);
-  };
-  __half2 hcur[kPairsPerThread], hnext[kPairsPerThread];
-  load_chunk(0, hcur);
+  const int* tpix = p.tile_pix + (size_t)tile * kUmmaTile;
+  const float* talpha = p.tile_alpha + (size_t)tile * kUmmaTile;
+  const __half2* Ph = static_cast<const __half2*>(p.Phat);
 
   if (warp == 0) tmem_alloc(&tbase, S::TMEM_COLS);
   if (tid == 0) {
@@ -92,20 +114,7 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
         bulk_load(B0, b0g + (size_t)kc * S::B_BYTES, S::B_BYTES, &bar_load);
         bulk_load(B1, b1g + (size_t)kc * S::B_BYTES, S::B_BYTES, &bar_load);
       }
-      // A chunk: frequency f as column pair (2 (f - kc * 32), + 1) = (Re, Im)
-      {
-        const float w0 = 1.f - al;
-#pragma unroll
-        for (int q = 0; q < kPairsPerThread; ++q) {
-          const int col = 2 * (half * kPairsPerThread + q);
-          const uint32_t off = umma_kmajor_offset(row, col, kUmmaKChunk);   // (col, col + 1) adjacent
-          const float2 v = __half22float2(hcur[q]);
-          *reinterpret_cast<__half2*>(A0 + off) = __floats2half2_rn(w0 * v.x, w0 * v.y);
-          *reinterpret_cast<__half2*>(A1 + off) = __floats2half2_rn(al * v.x, al * v.y);
-        }
-      }
-      // the next chunk's phasors are in flight while this chunk's MMAs run
-      load_chunk(kc + 1 < p.KC ? kc + 1 : 0, hnext);
+      build_a_chunk(A0, A1, Ph, p.F, tpix, talpha, kc, tid);
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -127,8 +136,6 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
       const bool done = mbar_wait_bounded(&bar_mma, phase, kWaitLimit);
       ok = __syncthreads_and(ok && done ? 1 : 0) != 0;
       phase ^= 1;
-#pragma unroll
-      for (int q = 0; q < kPairsPerThread; ++q) hcur[q] = hnext[q];
       if (!ok) break;
     }
     if (!ok) break;
@@ -169,6 +176,148 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
   tc_fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(dt, S::TMEM_COLS);
+}
+
+// Persistent, double-buffered form: one CTA per SM walks its tiles; the
+// operand buffers and the tensor-memory accumulator are doubled so that the
+// bulk copies and the A build of the next chunk overlap the MMAs of the
+// current one, and a tile's epilogue overlaps the next tile's first chunk.
+template <int Db>
+struct PipeSmem {
+  static constexpr int N = 2 * Db;
+  static constexpr uint32_t A_BYTES = kUmmaTile * kUmmaKChunk * 2;
+  static constexpr uint32_t B_BYTES = N * kUmmaKChunk * 2;
+  static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;        // A0 A1 B0 B1
+  static constexpr uint32_t TOTAL = 2 * STAGE;
+  static constexpr uint32_t ACC_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+};
+
+template <int Db>
+__global__ void __launch_bounds__(kThreads, 1) pf_umma_pipe_kernel(const PfUmmaParams p) {
+  using S = PipeSmem<Db>;
+  extern __shared__ __align__(128) unsigned char up_sm[];
+  __shared__ uint64_t bar_load[2], bar_mma[2];
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kUmmaTile - 1), half = tid >> 7;
+  auto A0 = [&](int st) { return up_sm + st * S::STAGE; };
+  auto A1 = [&](int st) { return up_sm + st * S::STAGE + S::A_BYTES; };
+  auto B0 = [&](int st) { return up_sm + st * S::STAGE + 2 * S::A_BYTES; };
+  auto B1 = [&](int st) { return up_sm + st * S::STAGE + 2 * S::A_BYTES + S::B_BYTES; };
+  if (warp == 0) tmem_alloc(&tbase, S::TMEM_COLS);
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_load[i], 1);
+      mbar_init(&bar_mma[i], 1);
+    }
+    mbar_fence_init();
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  tc_fence_after_sync();
+  const uint32_t tm = tbase;
+  const uint32_t idesc = umma_idesc_f16<false>(kUmmaTile, S::N);
+  const size_t blk_bytes = (size_t)p.KC * S::B_BYTES;
+  const unsigned char* Bg = static_cast<const unsigned char*>(p.B);
+  // this CTA's work: units (tile, depth block), each KC chunks
+  const int units = (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x * p.nblk;
+  const int G = units * p.KC;
+  auto unit_tile = [&](int u) { return (int)blockIdx.x + (u / p.nblk) * (int)gridDim.x; };
+  // chunk g: unit g / KC, chunk kc = g % KC; stage g & 1, k-th use of its stage: g >> 1
+  auto prepare = [&](int g) {               // bulk copies and A build of chunk g into stage g & 1
+    const int st = g & 1, u = g / p.KC, kc = g % p.KC;
+    const int tl = unit_tile(u), blk = u % p.nblk;
+    const int2 i01 = p.tile_i01[tl];
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(&bar_load[st], 2 * S::B_BYTES);
+      bulk_load(B0(st), Bg + ((size_t)i01.x * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BYTES, S::B_BYTES,
+                &bar_load[st]);
+      bulk_load(B1(st), Bg + ((size_t)i01.y * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BYTES, S::B_BYTES,
+                &bar_load[st]);
+    }
+    build_a_chunk(A0(st), A1(st), static_cast<const __half2*>(p.Phat), p.F, p.tile_pix + (size_t)tl * kUmmaTile,
+                  p.tile_alpha + (size_t)tl * kUmmaTile, kc, tid);
+    fence_proxy_async_smem();
+  };
+  bool ok = true;
+  if (G > 0) prepare(0);
+  for (int g = 0; g < G && ok; ++g) {
+    const int st = g & 1, use = g >> 1;
+    const int u = g / p.KC, kc = g % p.KC;
+    const uint32_t acc = tm + (uint32_t)((u & 1) * S::ACC_COLS);
+    __syncthreads();                          // chunk g's A is built by every thread
+    if (tid == 0) {
+      ok = mbar_wait_bounded(&bar_load[st], use & 1, kWaitLimit);
+      tc_fence_after_sync();
+      if (ok) {
+#pragma unroll
+        for (int kk = 0; kk < kUmmaKChunk / 16; ++kk) {
+          const uint32_t ko = kk * 256;
+          umma_f16(acc, umma_smem_desc(smem_u32(A0(st)) + ko, 128, 1024),
+                   umma_smem_desc(smem_u32(B0(st)) + ko, 128, 1024), idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+          umma_f16(acc, umma_smem_desc(smem_u32(A1(st)) + ko, 128, 1024),
+                   umma_smem_desc(smem_u32(B1(st)) + ko, 128, 1024), idesc, 1u);
+        }
+      }
+      umma_commit(&bar_mma[st]);
+    }
+    // stage st ^ 1 is free once chunk g - 1's MMAs are done; fill it with chunk g + 1
+    if (g + 1 < G) {
+      if (g >= 1) {
+        const bool d = mbar_wait_bounded(&bar_mma[st ^ 1], ((g - 1) >> 1) & 1, kWaitLimit);
+        if (!d) ok = false;
+      }
+      prepare(g + 1);
+    }
+    if (kc == p.KC - 1) {
+      // last chunk of unit u: its MMAs done, then read accumulator (u & 1)
+      const bool d = mbar_wait_bounded(&bar_mma[st], use & 1, kWaitLimit);
+      tc_fence_after_sync();
+      const int tl = unit_tile(u), blk = u % p.nblk;
+      const int pix = p.tile_pix[(size_t)tl * kUmmaTile + row];
+      const float ac = p.tile_acut[(size_t)tl * kUmmaTile + row];
+      __half2* crow = static_cast<__half2*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
+      const float gsc = p.scale * ac;
+      const uint32_t lane_base = acc + ((uint32_t)(32 * (warp & 3)) << 16);
+      constexpr int kCols = Db >= 32 ? Db / 2 : Db;
+      const int c0 = Db >= 32 ? half * kCols : 0;
+      const bool writer = Db >= 32 || half == 0;
+#pragma unroll
+      for (int c = c0; c < c0 + kCols; c += 16) {
+        uint32_t re[16], im[16];
+        tmem_ld16(lane_base + (uint32_t)c, re);
+        tmem_ld16(lane_base + (uint32_t)(Db + c), im);
+        tmem_wait_ld();
+        if (pix >= 0 && writer && d) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int dd = blk * Db + c + q;
+            if (dd < p.D) crow[c + q] = __floats2half2_rn(gsc * __uint_as_float(re[q]), gsc * __uint_as_float(im[q]));
+          }
+        }
+      }
+      if (!d) ok = false;
+      tc_fence_before_sync();
+    }
+    ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  }
+  if (!ok && tid == 0) {
+    if (p.err) atomicExch(p.err, kDevErrTmaTimeout);
+    for (int i = 0; i < 2; ++i) {               // bounded last chance for copies in flight
+      mbar_wait_bounded(&bar_load[i], 0, kWaitLimit);
+      mbar_wait_bounded(&bar_load[i], 1, kWaitLimit);
+    }
+  }
+  // every issued MMA has completed before the accumulator is freed
+  if (ok && G > 0 && tid == 0) {
+    mbar_wait_bounded(&bar_mma[(G - 1) & 1], ((G - 1) >> 1) & 1, kWaitLimit);
+    if (G > 1) mbar_wait_bounded(&bar_mma[(G - 2) & 1], ((G - 2) >> 1) & 1, kWaitLimit);
+  }
+  tc_fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tm, S::TMEM_COLS);
 }
 
 // B operand blocks from the float64 radial kernel: block (bin, blk), chunk kc,
@@ -218,15 +367,33 @@ cudaError_t launch_umma_db(const PfUmmaParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int Db>
+cudaError_t launch_pipe_db(const PfUmmaParams& p, cudaStream_t s) {
+  using S = PipeSmem<Db>;
+  auto k = pf_umma_pipe_kernel<Db>;
+  static int sms = 0;
+  if (sms == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::TOTAL);
+    if (e != cudaSuccess) return e;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int grid = p.ntiles < sms ? p.ntiles : sms;   // one persistent CTA per SM
+  k<<<grid, kThreads, S::TOTAL, s>>>(p);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_pf_umma(const PfUmmaParams& p, cudaStream_t s) {
+cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
   if (p.ntiles <= 0) return cudaSuccess;
   switch (p.Db) {
-    case 16: return launch_umma_db<16>(p, s);
-    case 32: return launch_umma_db<32>(p, s);
-    case 64: return launch_umma_db<64>(p, s);
-    case 128: return launch_umma_db<128>(p, s);
+    case 16: return pipelined ? launch_pipe_db<16>(p, s) : launch_umma_db<16>(p, s);
+    case 32: return pipelined ? launch_pipe_db<32>(p, s) : launch_umma_db<32>(p, s);
+    case 64: return pipelined ? launch_pipe_db<64>(p, s) : launch_umma_db<64>(p, s);
+    case 128: return pipelined ? launch_pipe_db<128>(p, s) : launch_umma_db<128>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -86,9 +86,10 @@ def test_pf_fp16_workload_128x128x1024():
 @pytest.mark.parametrize("depths", [40, 7, 150])
 def test_pf_fp16_tensor_core_and_ffma_depth_sums(depths):
     """FP16 phasor-field plans run the depth sum on the tensor cores (launch
-    shape 0 of the stage) or on FP32 FMAs (shape 1): both within 2e-3 of the
-    oracle and of each other, for depth counts below, inside and across the
-    128-depth blocks of the tensor-core form."""
+    shape 0: one CTA per tile; shape 2: persistent double-buffered CTAs) or
+    on FP32 FMAs (shape 1): all within 2e-3 of the oracle and of each other,
+    for depth counts below, inside and across the 128-depth blocks of the
+    tensor-core forms."""
     from paper_2608_28183_gb300 import nlos
     g = synth.Geometry(32, 32, 512, 16e-12, 1.0, 1.0)
     rng = np.random.default_rng(depths)
@@ -99,14 +100,15 @@ def test_pf_fp16_tensor_core_and_ffma_depth_sums(depths):
     stage = names.index("pf_depth_sum")
     x = to_device(cap.counts, torch.float16)
     out = {}
-    for v in (0, 1):
+    for v in (0, 1, 2):
         t = plan.tiles
         t[stage] = v
         plan.tiles = t
         out[v] = plan.reconstruct(x).cpu().numpy().astype(np.float64)
     op = pf.make_plan(32, 32, 512, 16e-12, 1.0, 1.0, depths, 0.4, 1.2)
     ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float16), op)
-    for v in (0, 1):
+    for v in (0, 1, 2):
         assert rel_l2(out[v], ref) <= 2e-3, (v, rel_l2(out[v], ref))
         assert same_peak(out[v], ref, rtol=2e-3)
     assert rel_l2(out[0], out[1]) <= 2e-3
+    assert rel_l2(out[2], out[0]) <= 1e-6      # same arithmetic, same order per tile
