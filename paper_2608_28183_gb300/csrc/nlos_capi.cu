@@ -778,7 +778,8 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
       up.KC = p->KC_u;
       up.scale = c3;
       up.err = err;
-      NLOS_CU(launch_pf_umma(up, p->tiles[sid] == 2, s), "pf depth sum (tensor cores)");
+      // launch shape 0: persistent warp-specialised schedule; 2: one CTA per tile
+      NLOS_CU(launch_pf_umma(up, p->tiles[sid] != 2, s), "pf depth sum (tensor cores)");
     } else {
     PfDepthParams dp{};
     dp.Phat = b2;
@@ -1319,7 +1320,7 @@ int stage_variants(const nlos_plan_s* p, size_t i) {
   if (p->stage_kind[i] == 1) return axis_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 2) return fk_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 3) return 3 * axis_ic_count(p->stage_len[i]);
-  if (p->stage_kind[i] == 4) return 3;   // tensor cores, FFMA, tensor cores pipelined
+  if (p->stage_kind[i] == 4) return 3;   // tensor cores (persistent), FFMA, tensor cores (CTA per tile)
   return 1;
 }
 }  // namespace

@@ -167,7 +167,7 @@ cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int st
 // 2 Db output columns x Kp inputs per depth block, f16, stored per plan in the
 // operand layout); C = scale * acut * (Y_re + i Y_im).
 constexpr int kUmmaTile = 128;           // pixels per tile (MMA M)
-constexpr int kUmmaKChunk = 64;          // K columns per shared-memory chunk
+constexpr int kUmmaKChunk = 32;          // K columns per shared-memory chunk (16 frequencies)
 struct PfUmmaParams {
   const void* Phat;            // [npix][F] half2
   const void* B;               // [n_rho][nblk][KC][2 Db x 64] f16, operand layout

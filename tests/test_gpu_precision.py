@@ -86,7 +86,7 @@ def test_pf_fp16_workload_128x128x1024():
 @pytest.mark.parametrize("depths", [40, 7, 150])
 def test_pf_fp16_tensor_core_and_ffma_depth_sums(depths):
     """FP16 phasor-field plans run the depth sum on the tensor cores (launch
-    shape 0: one CTA per tile; shape 2: persistent double-buffered CTAs) or
+    shape 0: persistent warp-specialised CTAs; shape 2: one CTA per tile) or
     on FP32 FMAs (shape 1): all within 2e-3 of the oracle and of each other,
     for depth counts below, inside and across the 128-depth blocks of the
     tensor-core forms."""
