@@ -391,6 +391,17 @@ def pf_bench(torch, nlos, synth, steps=200, with_oracle=True):
             rec["depth_sum_alu"]["frac"] = rec["depth_sum_alu"]["achieved_tflops"] / rec["depth_sum_alu"]["peak_tflops"]
         else:
             rec["rel_l2_vs_f32"] = float(np.linalg.norm(v.cpu().numpy() - vol32) / np.linalg.norm(vol32))
+            # tensor-core depth sum: two real products (A0 B0^T + A1 B1^T) per
+            # pixel inside the cutoff, K = 2F, N = 2 x planes
+            peaks, _ = measured_peaks()
+            tpeak = float(peaks.get("bf16_tflops", 0.0)) or 1900.0
+            npix = 4 * g.nx * g.ny
+            tflops = 2 * npix * (2 * 151) * (2 * 128) * 2
+            ms = rec["stages_ms"]["pf_depth_sum"]
+            rec["depth_sum_tensor"] = {"bound": "tensor", "flops": tflops,
+                                       "achieved_tflops": tflops / (ms * 1e-3) / 1e12, "peak_tflops": tpeak,
+                                       "peak_note": "measured dense bf16 (f16 runs at the same rate)",
+                                       "frac": tflops / (ms * 1e-3) / 1e12 / tpeak, "tiles_tuned": plan.tiles}
         out[storage] = rec
     # dense Fourier-domain kernel (Alg. 3) on the same workload: the depth sum
     # streams the whole kernel (4ab x F x D complex float32) once per volume

@@ -490,23 +490,23 @@ cudaError_t launch_axis_one(const AxisLaunch& l, cudaStream_t s) {
   }
 }
 
-// Each translation unit instantiates one length range (kAxisSmall: lengths
-// <= 256, kAxisLarge: >= 512) so the builds run in parallel. The range is a
-// template parameter, so the two units' dispatchers are distinct functions
-// (a macro alone would give two different bodies to one symbol).
-constexpr int kAxisSmall = 0, kAxisLarge = 1;
-
+// Each translation unit instantiates one length range (0: 16-64, 1: 128-256,
+// 2: 512-2048) so the builds run in parallel. The range is a template
+// parameter, so the units' dispatchers are distinct functions (a macro alone
+// would give different bodies to one symbol).
 template <int RANGE, int LD, int ST, class TS, bool kHalfIn, bool kHalfOut>
 cudaError_t launch_axis_len(const AxisLaunch& l, cudaStream_t s) {
   switch (l.L) {
-#if defined(AXIS_SMALL)
+#if defined(AXIS_RANGE) && AXIS_RANGE == 0
     case 16: return launch_axis_one<16, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 32: return launch_axis_one<32, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 64: return launch_axis_one<64, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
+#endif
+#if defined(AXIS_RANGE) && AXIS_RANGE == 1
     case 128: return launch_axis_one<128, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 256: return launch_axis_one<256, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
 #endif
-#if defined(AXIS_LARGE)
+#if defined(AXIS_RANGE) && AXIS_RANGE == 2
     case 512: return launch_axis_one<512, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 1024: return launch_axis_one<1024, LD, ST, TS, kHalfIn, kHalfOut>(l, s);
     case 2048: return launch_axis_one<2048, LD, ST, TS, kHalfIn, kHalfOut>(l, s);

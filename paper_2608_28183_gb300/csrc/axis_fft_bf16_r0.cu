@@ -1,0 +1,6 @@
+// Strided-axis FFT instantiations: bfloat16 storage, length range 0.
+#define AXIS_RANGE 0
+#include "axis_fft.cuh"
+namespace nlos {
+cudaError_t launch_axis_fft_bf16_r0(const AxisLaunch& l, cudaStream_t s) { return launch_axis_typed<__nv_bfloat162, 0>(l, s); }
+}  // namespace nlos

@@ -1,0 +1,6 @@
+// Strided-axis FFT instantiations: float2 storage, length range 2.
+#define AXIS_RANGE 2
+#include "axis_fft.cuh"
+namespace nlos {
+cudaError_t launch_axis_fft_f32_r2(const AxisLaunch& l, cudaStream_t s) { return launch_axis_typed<float2, 2>(l, s); }
+}  // namespace nlos

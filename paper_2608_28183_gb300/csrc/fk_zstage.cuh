@@ -69,7 +69,8 @@ __device__ __forceinline__ StoltCoord stolt_coord(float Ahi, float Alo, int m, i
 }
 
 // forward transform of the stored pencil; its upper half is zero padding
-template <int L, class TS>
+// (kGuard: the pencil is shorter than L / 2, loads past it read zero)
+template <int L, class TS, bool kGuard>
 struct FkFwdCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = false;
@@ -81,7 +82,7 @@ struct FkFwdCtx {
   float ldmul;
   int n_in;                  // stored samples of the pencil (the rest is zero padding)
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = (valid && l < n_in) ? cscale(Cpx<TS>::get(g + l), ldmul) : make_float2(0.f, 0.f);
+    x[0] = (valid && (!kGuard || l < n_in)) ? cscale(Cpx<TS>::get(g + l), ldmul) : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[pad16(l)] = x[0]; }
@@ -91,7 +92,7 @@ struct FkFwdCtx {
 // Hermitian partner; one Stolt coordinate per m feeds both. kAliasU: the
 // pencil's transform runs in U's own buffer, so the first pass must finish
 // reading U before it writes (kSmemInput adds that barrier).
-template <int L, class TS, bool kAliasU>
+template <int L, class TS, bool kAliasU, bool kGuard>
 struct FkInvCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = kAliasU;
@@ -122,7 +123,7 @@ struct FkInvCtx {
   }
   __device__ __forceinline__ float2* sm(int t) const { return t == 0 ? W0 : W1; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[2]) const {   // every l the schedule keeps
-    if (l >= n_out) return;
+    if (kGuard && l >= n_out) return;
     if (st0) Cpx<TS>::put(out0 + l, cscale(cconj(x[0]), stmul));
     if (st1) Cpx<TS>::put(out1 + l, cscale(cconj(x[1]), stmul));
   }
@@ -145,13 +146,17 @@ template <int L, int PPC_, bool kAlias = false> struct FkTile {
   static constexpr int THREADS = PPC * (L / 16);
   static constexpr int NBUF = kAlias ? 2 : 3;
   static constexpr size_t SMEM = sizeof(float2) * NBUF * PPC * FftShape<L>::SMEM;
-  static constexpr int MIN_BLOCKS = kAlias ? (65536 / (THREADS * 96) > 1 ? 65536 / (THREADS * 96) : 1) : 1;
+  static constexpr int MIN_BLOCKS_RAW = 65536 / (THREADS * 96);
+  static constexpr int MIN_BLOCKS = !kAlias ? 1 : MIN_BLOCKS_RAW < 1 ? 1 : MIN_BLOCKS_RAW > 16 ? 16 : MIN_BLOCKS_RAW;
 };
 
 // kPad2: the temporal axis is zero-padded to L >= 2n (the forward input's
 // upper half is zero and only z < n is kept); otherwise L = n and every
 // output is kept. Either way the Stolt source must stay below L/2.
-template <int L, int PPC, class TS, bool kPad2, bool kAlias>
+// kGuard: L > 2n (a time axis that is not a power of two): loads beyond the
+// pencil and stores beyond z = n are masked; otherwise the pruned passes
+// already stop there.
+template <int L, int PPC, class TS, bool kPad2, bool kAlias, bool kGuard>
 __global__ void __launch_bounds__(FkTile<L, PPC, kAlias>::THREADS, FkTile<L, PPC, kAlias>::MIN_BLOCKS)
 fk_zstage_kernel(const FkZParams p) {
   using S = FftShape<L>;
@@ -168,7 +173,7 @@ fk_zstage_kernel(const FkZParams p) {
   float2* W1 = fk_sm + ((kAlias ? 1 : 2) * PPC + w) * S::SMEM;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
-    FkFwdCtx<L, TS> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul, p.n};
+    FkFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul, p.n};
     fftn_run<L, 1, kPad2, false>(ctx, j0);
   }
   __syncthreads();
@@ -182,7 +187,7 @@ fk_zstage_kernel(const FkZParams p) {
   const int mky = (twob - ky) & (twob - 1);
   const long long o_mirror = ((long long)mkx * twob + mky) * p.n;
   // the partner is stored only where it is not itself a stored pencil
-  FkInvCtx<L, TS, kAlias> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, L / 2, A.x, A.y,
+  FkInvCtx<L, TS, kAlias, kGuard> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, L / 2, A.x, A.y,
                       valid, valid && kx > 0 && 2 * kx < p.a_pad, p.st_scale, p.n};
   fftn_run<L, 2, true, kPad2>(ctx, j0);
 }
@@ -190,7 +195,9 @@ fk_zstage_kernel(const FkZParams p) {
 template <int L, int PPC, class TS, bool kAlias>
 cudaError_t launch_fk_ppc(const FkZParams& p, cudaStream_t s) {
   using T = FkTile<L, PPC, kAlias>;
-  auto k = p.pad == 2 ? fk_zstage_kernel<L, PPC, TS, true, kAlias> : fk_zstage_kernel<L, PPC, TS, false, kAlias>;
+  auto k = p.pad != 2 ? fk_zstage_kernel<L, PPC, TS, false, kAlias, false>
+           : p.L == 2 * p.n ? fk_zstage_kernel<L, PPC, TS, true, kAlias, false>
+                            : fk_zstage_kernel<L, PPC, TS, true, kAlias, true>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -211,20 +218,28 @@ cudaError_t launch_fk_one(const FkZParams& p, int tile, cudaStream_t s) {
   }
 }
 
-template <class TS>
+// Each translation unit instantiates one length range (0: 16-256,
+// 1: 512-1024, 2: 2048-8192); RANGE keeps the units' dispatchers distinct.
+template <class TS, int RANGE>
 cudaError_t launch_fk_typed(const FkZParams& p, int tile, cudaStream_t s) {
   if (p.npencils <= 0) return cudaErrorInvalidValue;
   switch (p.L) {
+#if defined(FK_RANGE) && FK_RANGE == 0
     case 16: return launch_fk_one<16, TS>(p, tile, s);
     case 32: return launch_fk_one<32, TS>(p, tile, s);
     case 64: return launch_fk_one<64, TS>(p, tile, s);
     case 128: return launch_fk_one<128, TS>(p, tile, s);
     case 256: return launch_fk_one<256, TS>(p, tile, s);
+#endif
+#if defined(FK_RANGE) && FK_RANGE == 1
     case 512: return launch_fk_one<512, TS>(p, tile, s);
     case 1024: return launch_fk_one<1024, TS>(p, tile, s);
+#endif
+#if defined(FK_RANGE) && FK_RANGE == 2
     case 2048: return launch_fk_one<2048, TS>(p, tile, s);
     case 4096: return launch_fk_one<4096, TS>(p, tile, s);
     case 8192: return launch_fk_one<8192, TS>(p, tile, s);
+#endif
     default: return cudaErrorInvalidValue;
   }
 }

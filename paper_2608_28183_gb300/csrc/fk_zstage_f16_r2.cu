@@ -1,0 +1,6 @@
+// f-k temporal-frequency stage instantiations: IEEE half storage, length range 2.
+#define FK_RANGE 2
+#include "fk_zstage.cuh"
+namespace nlos {
+cudaError_t launch_fk_zstage_f16_r2(const FkZParams& p, int tile, cudaStream_t s) { return launch_fk_typed<__half2, 2>(p, tile, s); }
+}  // namespace nlos

@@ -19,33 +19,41 @@
 #include "nlos_internal.h"
 
 namespace nlos {
-cudaError_t launch_axis_fft_f32_small(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_axis_fft_f32_large(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_axis_fft_f16_small(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_axis_fft_f16_large(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_axis_fft_bf16_small(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_axis_fft_bf16_large(const AxisLaunch& l, cudaStream_t s);
-cudaError_t launch_fk_zstage_f32(const FkZParams& p, int tile, cudaStream_t s);
-cudaError_t launch_fk_zstage_f16(const FkZParams& p, int tile, cudaStream_t s);
-cudaError_t launch_fk_zstage_bf16(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_axis_fft_f32_r0(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f32_r1(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f32_r2(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f16_r0(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f16_r1(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_f16_r2(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_bf16_r0(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_bf16_r1(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_axis_fft_bf16_r2(const AxisLaunch& l, cudaStream_t s);
+cudaError_t launch_fk_zstage_f32_r0(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_f32_r1(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_f32_r2(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_f16_r0(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_f16_r1(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_f16_r2(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_bf16_r0(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_bf16_r1(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zstage_bf16_r2(const FkZParams& p, int tile, cudaStream_t s);
 
 cudaError_t launch_axis_fft(const AxisLaunch& l, cudaStream_t s) {
-  const bool small = l.L <= 256;
-  switch (l.storage) {
-    case kF32: return small ? launch_axis_fft_f32_small(l, s) : launch_axis_fft_f32_large(l, s);
-    case kF16: return small ? launch_axis_fft_f16_small(l, s) : launch_axis_fft_f16_large(l, s);
-    case kBF16: return small ? launch_axis_fft_bf16_small(l, s) : launch_axis_fft_bf16_large(l, s);
-    default: return cudaErrorInvalidValue;
-  }
+  static cudaError_t (*const fn[3][3])(const AxisLaunch&, cudaStream_t) = {
+      {launch_axis_fft_f32_r0, launch_axis_fft_f32_r1, launch_axis_fft_f32_r2},
+      {launch_axis_fft_f16_r0, launch_axis_fft_f16_r1, launch_axis_fft_f16_r2},
+      {launch_axis_fft_bf16_r0, launch_axis_fft_bf16_r1, launch_axis_fft_bf16_r2}};
+  if (l.storage < 0 || l.storage > 2) return cudaErrorInvalidValue;
+  return fn[l.storage][l.L <= 64 ? 0 : l.L <= 256 ? 1 : 2](l, s);
 }
 
 cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s) {
-  switch (storage) {
-    case kF32: return launch_fk_zstage_f32(p, tile, s);
-    case kF16: return launch_fk_zstage_f16(p, tile, s);
-    case kBF16: return launch_fk_zstage_bf16(p, tile, s);
-    default: return cudaErrorInvalidValue;
-  }
+  static cudaError_t (*const fn[3][3])(const FkZParams&, int, cudaStream_t) = {
+      {launch_fk_zstage_f32_r0, launch_fk_zstage_f32_r1, launch_fk_zstage_f32_r2},
+      {launch_fk_zstage_f16_r0, launch_fk_zstage_f16_r1, launch_fk_zstage_f16_r2},
+      {launch_fk_zstage_bf16_r0, launch_fk_zstage_bf16_r1, launch_fk_zstage_bf16_r2}};
+  if (storage < 0 || storage > 2) return cudaErrorInvalidValue;
+  return fn[storage][p.L <= 256 ? 0 : p.L <= 1024 ? 1 : 2](p, tile, s);
 }
 }  // namespace nlos
 
