@@ -144,7 +144,7 @@ struct nlos_plan_s {
   int* tu_pix = nullptr;
   float* tu_alpha = nullptr;
   float* tu_acut = nullptr;
-  int ntiles_u = 0, Db_u = 0, nblk_u = 0, KC_u = 0;
+  int ntiles_u = 0, Db_u = 0, nblk_u = 0, KC_u = 0, kind_u = 0;
   void* Kr = nullptr;
   int2* ch_i01 = nullptr;
   int* ch_pix = nullptr;
@@ -396,15 +396,20 @@ nlos_status_t build_pf(nlos_plan_s* p) {
     st = dalloc(p, &Kr, complex_bytes(p->kr_storage) * (size_t)n_rho * NFD, "radial kernel");
     if (st == NLOS_OK) e = launch_kr_store(dK64, Kr, (long long)n_rho * NFD, p->kr_storage, p->kr_scale, 0);
   }
-  if (e == cudaSuccess && st == NLOS_OK && p->storage == kF16) {
-    // the same kernel as tensor-core B operands: [Kr -Ki; Ki Kr] per bin and depth block
+  if (e == cudaSuccess && st == NLOS_OK && (p->storage == kF16 || p->storage == kF32)) {
+    // the same kernel as tensor-core B operands: [Kr -Ki; Ki Kr] per bin and
+    // depth block, f16 for 16-bit plans, tf32 (hi, lo) parts for float32 plans
+    p->kind_u = p->storage == kF16 ? kUmmaF16 : kUmmaTf32x3;
+    const int cols = umma_chunk_cols(p->kind_u);
     p->Db_u = p->D <= 16 ? 16 : p->D <= 32 ? 32 : p->D <= 64 ? 64 : 128;
     p->nblk_u = (p->D + p->Db_u - 1) / p->Db_u;
-    p->KC_u = (2 * p->F + kUmmaKChunk - 1) / kUmmaKChunk;
-    const size_t bbytes = (size_t)n_rho * p->nblk_u * p->KC_u * (2 * p->Db_u) * kUmmaKChunk * 2;
+    p->KC_u = (2 * p->F + cols - 1) / cols;
+    const size_t bbytes =
+        (size_t)n_rho * p->nblk_u * p->KC_u * umma_parts(p->kind_u) * (2 * p->Db_u) * kUmmaRowBytes;
     st = dalloc(p, &p->Bu, bbytes, "tensor-core kernel operands");
     if (st == NLOS_OK)
-      e = launch_kr_store_umma(dK64, p->Bu, n_rho, p->F, p->D, p->Db_u, p->nblk_u, p->KC_u, p->kr_scale, 0);
+      e = launch_kr_store_umma(dK64, p->Bu, p->kind_u, n_rho, p->F, p->D, p->Db_u, p->nblk_u, p->KC_u,
+                               p->kr_scale, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   free_tmp();
@@ -766,8 +771,9 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     PfDenseParams dp{static_cast<const float2*>(b2), p->Kd, static_cast<float2*>(b1), Nu * Nv, (int)F, (int)D};
     NLOS_CU(launch_pf_dense(dp, s), "pf dense depth sum");
   } else {
-    // PF3: depth sum (pixels beyond the cutoff stay zero); 16-bit plans run it
-    // on the tensor cores unless the stage's launch shape asks for the FFMA form
+    // PF3: depth sum (pixels beyond the cutoff stay zero); f16 and float32
+    // plans run it on the tensor cores (f16 operands / three tf32 products)
+    // unless the stage's launch shape asks for the FFMA form
     NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * Nu * Nv * D, s), "pf clear");
     if (p->Bu && p->tiles[sid] != 1) {
       PfUmmaParams up{};
@@ -784,6 +790,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
       up.Db = p->Db_u;
       up.nblk = p->nblk_u;
       up.KC = p->KC_u;
+      up.kind = p->kind_u;
       up.scale = c3;
       up.err = err;
       // launch shape 0: persistent warp-specialised schedule; 2: one CTA per tile
@@ -1024,7 +1031,8 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   else for (const char* nm : pf_names) p->stage_names.push_back(nm);
   for (const std::string& nm : p->stage_names) {
     const bool xs = nm.find("_x_") != std::string::npos, ys = nm.find("_y_") != std::string::npos;
-    const bool umma = nm == "pf_depth_sum" && desc->method == NLOS_PHASOR_RSD && desc->storage == NLOS_F16;
+    const bool umma = nm == "pf_depth_sum" && desc->method == NLOS_PHASOR_RSD &&
+                      (desc->storage == NLOS_F16 || desc->storage == NLOS_F32);
     p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : nm == "fk_stolt_z" ? 2 : umma ? 4 : 0);
     p->stage_len.push_back(xs ? p->Lx : ys ? p->Ly : nm == "fk_stolt_z" ? p->Lt : 0);
   }

@@ -160,31 +160,41 @@ cudaError_t launch_kr_build(const KrBuildParams& p, cudaStream_t s);
 cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int storage, double scale,
                             cudaStream_t s);
 
-// Tensor-core depth sum for 16-bit storage: per tile of up to 128 pixels that
-// share the radial pair (i0, i1), Y = A0 B(i0)^T + A1 B(i1)^T with
-// A0 = (1 - alpha) [Re Phat | Im Phat], A1 = alpha [Re Phat | Im Phat] (f16,
-// built in shared memory) and B(i) the real form of K_r[i] ([Kr -Ki; Ki Kr],
-// 2 Db output columns x Kp inputs per depth block, f16, stored per plan in the
-// operand layout); C = scale * acut * (Y_re + i Y_im).
+// Tensor-core depth sum: per tile of up to 128 pixels that share the radial
+// pair (i0, i1), Y = A0 B(i0)^T + A1 B(i1)^T with A0 = (1 - alpha) [Re Phat |
+// Im Phat], A1 = alpha [Re Phat | Im Phat] (built in shared memory) and B(i)
+// the real form of K_r[i] ([Kr -Ki; Ki Kr], 2 Db output columns per depth
+// block, stored per plan in the operand layout); C = scale * acut * (Y_re +
+// i Y_im). Two operand kinds:
+//  * kUmmaF16 (16-bit storage): f16 operands, kind::f16 MMAs, one product;
+//  * kUmmaTf32x3 (float32 storage): every operand x split into tf32 parts
+//    x_hi = tf32(x), x_lo = tf32(x - x_hi), and A B^T taken as
+//    A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (kind::tf32 MMAs; the dropped
+//    A_lo B_lo^T term is ~2^-22 of the product), fp32 accumulation.
+// Both kinds stage 64-byte operand rows per chunk: 32 f16 or 16 tf32 columns.
 constexpr int kUmmaTile = 128;           // pixels per tile (MMA M)
-constexpr int kUmmaKChunk = 32;          // K columns per shared-memory chunk (16 frequencies)
+constexpr int kUmmaRowBytes = 64;        // bytes of one operand row per chunk
+enum UmmaKind { kUmmaF16 = 0, kUmmaTf32x3 = 1 };
+__host__ __device__ constexpr int umma_chunk_cols(int kind) { return kind == kUmmaF16 ? 32 : 16; }
+__host__ __device__ constexpr int umma_parts(int kind) { return kind == kUmmaF16 ? 1 : 2; }
 struct PfUmmaParams {
-  const void* Phat;            // [npix][F] half2
-  const void* B;               // [n_rho][nblk][KC][2 Db x 64] f16, operand layout
-  void* C;                     // [npix][D] half2
+  const void* Phat;            // [npix][F] half2 (f16 kind) or float2 (tf32 kind)
+  const void* B;               // [n_rho][nblk][KC][parts][2 Db rows x 64 bytes], operand layout
+  void* C;                     // [npix][D] half2 or float2
   const int2* tile_i01;        // [ntiles]
   const int* tile_pix;         // [ntiles][128] pixel or -1
   const float* tile_alpha;     // [ntiles][128]
   const float* tile_acut;      // [ntiles][128]
   int ntiles, F, D, Db, nblk, KC;
+  int kind;                    // UmmaKind
   float scale;
   int* err;                    // device error word (bounded waits)
 };
-// pipelined: persistent double-buffered CTAs (one per SM) instead of one CTA per tile
+// pipelined: persistent warp-specialised CTAs (one per SM) instead of one CTA per tile
 cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s);
-// K_r (float64 [n_rho][F][D]) -> B operand blocks, scaled, f16
-cudaError_t launch_kr_store_umma(const double2* K64, void* B, int n_rho, int F, int D, int Db, int nblk, int KC,
-                                 double scale, cudaStream_t s);
+// K_r (float64 [n_rho][F][D]) -> B operand blocks of the given kind, scaled
+cudaError_t launch_kr_store_umma(const double2* K64, void* B, int kind, int n_rho, int F, int D, int Db, int nblk,
+                                 int KC, double scale, cudaStream_t s);
 
 // Dense phasor-field kernel (Alg. 3), spatial form on the signed padded grid:
 // k[x][y][f][d] = exp(i kappa_f (sigma_s R + sigma_t d + Delta)),

@@ -1,6 +1,6 @@
-// Phasor-field depth sum on the 5th-generation tensor cores (Eq. 7, Alg. 4,
-// 16-bit storage). Pixels that share the radial pair (i0, i1) form tiles of
-// up to 128 rows; for one tile the sum over the band frequencies of
+// Phasor-field depth sum on the 5th-generation tensor cores (Eq. 7, Alg. 4).
+// Pixels that share the radial pair (i0, i1) form tiles of up to 128 rows;
+// for one tile the sum over the band frequencies of
 // Phat * lerp(K_r[i0], K_r[i1], alpha) is two real matrix products with a
 // shared accumulator:
 //
@@ -11,17 +11,24 @@
 // (Kr, -Ki) per frequency, an Im output row (Ki, Kr)), so Y's first Db
 // columns are Re C and the next Db are Im C for a block of Db depths. A row of
 // A is a scaled copy of a phasor row, built in shared memory; B arrives by 1D
-// bulk copies in the operand layout the plan stored; kind::f16 MMAs
-// (M = 128, N = 2 Db, K = 16) accumulate in tensor memory; warps read the
-// accumulator back (warp w owns rows 32 (w % 4) .. + 31) to apply the taper
-// and scale. Inputs are f16 with their per-volume and per-pass scales, the
-// accumulator is f32.
+// bulk copies in the operand layout the plan stored; MMAs (M = 128, N = 2 Db)
+// accumulate in tensor memory; warps read the accumulator back (warp w owns
+// rows 32 (w % 4) .. + 31) to apply the taper and scale.
+//
+// Operand kinds (both stage 64-byte operand rows per chunk):
+//  * OpF16 (16-bit storage): f16 A and B, kind::f16 MMAs (K = 16), 32 columns
+//    (16 frequencies) per chunk;
+//  * OpTf32x3 (float32 storage): A and B split into tf32 parts hi = tf32(x),
+//    lo = tf32(x - hi); each product is A_hi B_hi^T + A_hi B_lo^T +
+//    A_lo B_hi^T in kind::tf32 MMAs (K = 8), 16 columns (8 frequencies) per
+//    chunk. The parts carry 22 significant bits of every operand, so the sum
+//    keeps float32 accuracy at three tf32 products per term.
 //
 // Two schedules:
 //  * pf_umma_ws_kernel: one persistent CTA per SM, warp-specialised - a
-//    producer warp keeps kStages operand stages in flight, four warps build A
-//    and run the epilogue, one thread issues the MMAs - with two accumulators
-//    so a tile's epilogue overlaps the next tile's MMAs;
+//    producer warp keeps up to four operand stages in flight, eight warps
+//    build A and run the epilogue, one thread issues the MMAs - with two
+//    accumulators so a tile's epilogue overlaps the next tile's MMAs;
 //  * pf_umma_kernel: one CTA per tile, one stage.
 #include <cuda_fp16.h>
 
@@ -33,71 +40,126 @@ namespace nlos {
 namespace {
 
 constexpr int kWaitLimit = 1 << 26;                    // probes of a barrier (a few hundred ms)
-constexpr int kQ = kUmmaKChunk / 2;                    // frequencies per chunk
-constexpr uint32_t kSbo = (kUmmaKChunk / 8) * 128;     // row-group stride of a chunk operand
+constexpr uint32_t kSbo = (kUmmaRowBytes / 16) * 128;  // row-group stride of a chunk operand
+constexpr uint32_t kABytes = kUmmaTile * kUmmaRowBytes;  // one A operand part of a chunk
+constexpr uint32_t kSmemBudget = 200 * 1024;           // dynamic shared memory of the stages
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// A chunk kc of a tile: element (row r, frequency f = kc * kQ + q) of
-// (1 - alpha_r) Phat / alpha_r Phat as the column pair (2q, 2q + 1). A warp
-// instruction covers 8 rows x 4 consecutive q: the 32 lanes hit 32 distinct
-// shared-memory banks and read 8 runs of 16 bytes of the phasor rows. NT
-// threads (a multiple of 32) share the chunk.
-template <int NT>
+// byte offset of the complex value of frequency q (within the chunk) of
+// operand row r: columns (2q, 2q + 1), elements of `elem` bytes, 64-byte rows
+// in 8 x 16-byte core matrices
+__host__ __device__ constexpr uint32_t chunk_offset(int r, int q, int elem) {
+  return (uint32_t)(((r >> 3) * (kUmmaRowBytes / 16) + ((2 * q * elem) >> 4)) * 128 + (r & 7) * 16 +
+                    ((2 * q * elem) & 15));
+}
+
+struct OpF16 {
+  using In = __half2;    // phasor element
+  using Out = __half2;   // depth-sum element
+  static constexpr int kKind = kUmmaF16, kElem = 2, kParts = 1, kSlab = 16;
+  static constexpr int kQ = kUmmaRowBytes / (2 * kElem);   // frequencies per chunk
+  __device__ static __forceinline__ float2 load(In v) { return __half22float2(v); }
+  __device__ static __forceinline__ In zero() { return __floats2half2_rn(0.f, 0.f); }
+  // A operand parts of one weight at byte offset off
+  __device__ static __forceinline__ void put(unsigned char* a, uint32_t off, float x, float y) {
+    *reinterpret_cast<__half2*>(a + off) = __floats2half2_rn(x, y);
+  }
+  __device__ static __forceinline__ uint32_t idesc(int N) { return umma_idesc_f16<false>(kUmmaTile, N); }
+  __device__ static __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    umma_f16(d, a, b, id, acc);
+  }
+  __device__ static __forceinline__ Out out(float x, float y) { return __floats2half2_rn(x, y); }
+};
+
+struct OpTf32x3 {
+  using In = float2;
+  using Out = float2;
+  static constexpr int kKind = kUmmaTf32x3, kElem = 4, kParts = 2, kSlab = 8;
+  static constexpr int kQ = kUmmaRowBytes / (2 * kElem);
+  __device__ static __forceinline__ float2 load(In v) { return v; }
+  __device__ static __forceinline__ In zero() { return make_float2(0.f, 0.f); }
+  __device__ static __forceinline__ void put(unsigned char* a, uint32_t off, float x, float y) {
+    const float hx = to_tf32(x), hy = to_tf32(y);
+    *reinterpret_cast<float2*>(a + off) = make_float2(hx, hy);
+    *reinterpret_cast<float2*>(a + kABytes + off) = make_float2(to_tf32(x - hx), to_tf32(y - hy));
+  }
+  __device__ static __forceinline__ uint32_t idesc(int N) { return umma_idesc_tf32(kUmmaTile, N); }
+  __device__ static __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    umma_tf32(d, a, b, id, acc);
+  }
+  __device__ static __forceinline__ Out out(float x, float y) { return make_float2(x, y); }
+};
+
+// Stage layout: A(w, part) for weights w = 0 (1 - alpha), 1 (alpha), then
+// B(bin, part) for bins i0, i1; the parts of one B block are contiguous in the
+// stage and in the plan's operand store, so one bulk copy brings a bin.
+template <class Op, int Db>
+struct Sizes {
+  static constexpr int N = 2 * Db;
+  static constexpr uint32_t B_BYTES = N * kUmmaRowBytes;                      // one B part of a chunk
+  static constexpr uint32_t B_BLOCK = Op::kParts * B_BYTES;                    // all parts of one bin
+  static constexpr uint32_t B_OFF = 2 * Op::kParts * kABytes;
+  static constexpr uint32_t STAGE = B_OFF + 2 * B_BLOCK;
+  static constexpr int STAGES = kSmemBudget / STAGE >= 4 ? 4 : (int)(kSmemBudget / STAGE);
+  static constexpr uint32_t ACC_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
+  static_assert(STAGES >= 1, "a stage must fit in shared memory");
+};
+
+// A chunk of a tile: frequency q of row r for thread t and iteration i. A
+// warp instruction covers 8 rows x 4 consecutive q: the 32 lanes hit 32
+// distinct shared-memory banks (f16) or two conflict-free 128-byte wavefronts
+// (tf32) and read 8 runs of 4 consecutive phasors. NT threads (a multiple of
+// 32) share the chunk.
+template <class Op, int NT>
 struct AChunk {
-  static constexpr int kBlocks = (kUmmaTile / 8) * (kQ / 4);
+  static constexpr int kBlocks = (kUmmaTile / 8) * (Op::kQ / 4);
   static constexpr int kIters = kBlocks / (NT / 32);
+  static_assert(kIters * (NT / 32) == kBlocks, "threads must divide the chunk");
   __device__ static __forceinline__ void coords(int i, int t, int& r, int& q) {
     const int T = i * (NT / 32) + (t >> 5);
-    r = (T / (kQ / 4)) * 8 + (t & 7);
-    q = (T % (kQ / 4)) * 4 + ((t & 31) >> 3);
+    r = (T / (Op::kQ / 4)) * 8 + (t & 7);
+    q = (T % (Op::kQ / 4)) * 4 + ((t & 31) >> 3);
   }
-  __device__ static __forceinline__ void load(__half2 (&h)[kIters], const __half2* Phat, int F, const int* spix,
-                                              int kc, int t) {
-#pragma unroll
-    for (int i = 0; i < kIters; ++i) {
-      int r, q;
-      coords(i, t, r, q);
-      const int f = kc * kQ + q;
-      const int pix = spix[r];
-      h[i] = (pix >= 0 && f < F) ? Phat[(size_t)pix * F + f] : __floats2half2_rn(0.f, 0.f);
-    }
-  }
-  __device__ static __forceinline__ void store(unsigned char* A0, unsigned char* A1, const __half2 (&h)[kIters],
-                                               const float* salpha, int t) {
-#pragma unroll
-    for (int i = 0; i < kIters; ++i) {
-      int r, q;
-      coords(i, t, r, q);
-      const uint32_t off = umma_kmajor_offset(r, 2 * q, kUmmaKChunk);
-      const float2 v = __half22float2(h[i]);
-      const float al = salpha[r], w0 = 1.f - al;
-      *reinterpret_cast<__half2*>(A0 + off) = __floats2half2_rn(w0 * v.x, w0 * v.y);
-      *reinterpret_cast<__half2*>(A1 + off) = __floats2half2_rn(al * v.x, al * v.y);
-    }
+  // value v of row r with weight alpha into both A operands
+  __device__ static __forceinline__ void put(unsigned char* stage, int r, int q, float2 v, float alpha) {
+    const uint32_t off = chunk_offset(r, q, Op::kElem);
+    const float w0 = 1.f - alpha;
+    Op::put(stage, off, w0 * v.x, w0 * v.y);
+    Op::put(stage + Op::kParts * kABytes, off, alpha * v.x, alpha * v.y);
   }
 };
 
 // MMAs of one chunk into accumulator `acc` (first: the chunk starts the sum)
-__device__ __forceinline__ void mma_chunk(uint32_t acc, uint32_t idesc, const unsigned char* A0,
-                                          const unsigned char* A1, const unsigned char* B0, const unsigned char* B1,
-                                          bool first) {
+template <class Op, int Db>
+__device__ __forceinline__ void mma_chunk(uint32_t acc, uint32_t idesc, const unsigned char* stage, bool first) {
+  using S = Sizes<Op, Db>;
+  const uint32_t s0 = smem_u32(stage);
 #pragma unroll
-  for (int kk = 0; kk < kUmmaKChunk / 16; ++kk) {
-    const uint32_t ko = kk * 256;     // two 8-column core matrices per K = 16 slab
-    umma_f16(acc, umma_smem_desc(smem_u32(A0) + ko, 128, kSbo), umma_smem_desc(smem_u32(B0) + ko, 128, kSbo), idesc,
-             (first && kk == 0) ? 0u : 1u);
-    umma_f16(acc, umma_smem_desc(smem_u32(A1) + ko, 128, kSbo), umma_smem_desc(smem_u32(B1) + ko, 128, kSbo), idesc,
-             1u);
+  for (int kk = 0; kk < kUmmaRowBytes / (Op::kElem * Op::kSlab); ++kk) {
+    const uint32_t ko = kk * 256;     // an MMA reads 32 bytes of K: two 16-byte core-matrix columns
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      const uint32_t a_hi = s0 + w * Op::kParts * kABytes + ko;
+      const uint32_t b_hi = s0 + S::B_OFF + w * S::B_BLOCK + ko;
+      Op::mma(acc, umma_smem_desc(a_hi, 128, kSbo), umma_smem_desc(b_hi, 128, kSbo), idesc,
+              (first && kk == 0 && w == 0) ? 0u : 1u);
+      if (Op::kParts == 2) {
+        Op::mma(acc, umma_smem_desc(a_hi, 128, kSbo), umma_smem_desc(b_hi + S::B_BYTES, 128, kSbo), idesc, 1u);
+        Op::mma(acc, umma_smem_desc(a_hi + kABytes, 128, kSbo), umma_smem_desc(b_hi, 128, kSbo), idesc, 1u);
+      }
+    }
   }
 }
 
 // accumulator rows of one warp -> C (taper and scale), columns [c0, c0 + ncols)
-template <int Db>
-__device__ __forceinline__ void epilogue_cols(uint32_t acc, int warp, int pix, float gsc, __half2* crow, int blk,
-                                              int D, int c0, int ncols) {
+template <class Op, int Db>
+__device__ __forceinline__ void epilogue_cols(uint32_t acc, int warp, int pix, float gsc, typename Op::Out* crow,
+                                              int blk, int D, int c0, int ncols) {
+  using Out = typename Op::Out;
+  constexpr int kVec = 16 / sizeof(Out);        // complex values per 16-byte store
   const uint32_t lane_base = acc + ((uint32_t)(32 * (warp & 3)) << 16);
   for (int c = c0; c < c0 + ncols; c += 16) {
     uint32_t re[16], im[16];
@@ -105,13 +167,13 @@ __device__ __forceinline__ void epilogue_cols(uint32_t acc, int warp, int pix, f
     tmem_ld16(lane_base + (uint32_t)(Db + c), im);
     tmem_wait_ld();
     if (pix >= 0) {
-      __half2 o[16];
+      Out o[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) o[q] = __floats2half2_rn(gsc * __uint_as_float(re[q]), gsc * __uint_as_float(im[q]));
+      for (int q = 0; q < 16; ++q) o[q] = Op::out(gsc * __uint_as_float(re[q]), gsc * __uint_as_float(im[q]));
       if (blk * Db + c + 16 <= D && (reinterpret_cast<uintptr_t>(crow + c) & 15) == 0) {
-        uint4* dst = reinterpret_cast<uint4*>(crow + c);          // 16-byte stores: 4 depths each
+        uint4* dst = reinterpret_cast<uint4*>(crow + c);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) dst[v] = reinterpret_cast<const uint4*>(o)[v];
+        for (int v = 0; v < 16 / kVec; ++v) dst[v] = reinterpret_cast<const uint4*>(o)[v];
       } else {
 #pragma unroll
         for (int q = 0; q < 16; ++q)
@@ -121,35 +183,26 @@ __device__ __forceinline__ void epilogue_cols(uint32_t acc, int warp, int pix, f
   }
 }
 
-template <int Db>
-struct Sizes {
-  static constexpr int N = 2 * Db;
-  static constexpr uint32_t A_BYTES = kUmmaTile * kUmmaKChunk * 2;   // one A operand chunk
-  static constexpr uint32_t B_BYTES = N * kUmmaKChunk * 2;           // one B operand chunk
-  static constexpr uint32_t STAGE = 2 * A_BYTES + 2 * B_BYTES;        // A0 A1 B0 B1
-  static constexpr uint32_t ACC_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
-};
-
 // ---------------------------------------------------------------------------
 // Warp-specialised persistent schedule
 // ---------------------------------------------------------------------------
-constexpr int kStages = 4;
+constexpr int kMaxStages = 4;
 constexpr int kWsBuilders = 256;                 // warps 0-7: A build, epilogue
 constexpr int kWsThreads = kWsBuilders + 64;     // warp 8: producer, warp 9: MMA issue
 constexpr int kProducerWarp = kWsBuilders / 32, kMmaWarp = kProducerWarp + 1;
 
-template <int Db>
+template <class Op, int Db>
 __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaParams p) {
-  using S = Sizes<Db>;
-  using A = AChunk<kWsBuilders>;
+  using S = Sizes<Op, Db>;
+  using A = AChunk<Op, kWsBuilders>;
+  using In = typename Op::In;
+  using Out = typename Op::Out;
+  constexpr int kStages = S::STAGES;
   extern __shared__ __align__(128) unsigned char ws_sm[];
-  __shared__ uint64_t full_b[kStages], full_a[kStages], empty[kStages], acc_full[2], acc_empty[2];
+  __shared__ uint64_t full_b[kMaxStages], full_a[kMaxStages], empty[kMaxStages], acc_full[2], acc_empty[2];
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  auto A0 = [&](int s) { return ws_sm + s * S::STAGE; };
-  auto A1 = [&](int s) { return ws_sm + s * S::STAGE + S::A_BYTES; };
-  auto B0 = [&](int s) { return ws_sm + s * S::STAGE + 2 * S::A_BYTES; };
-  auto B1 = [&](int s) { return ws_sm + s * S::STAGE + 2 * S::A_BYTES + S::B_BYTES; };
+  auto stage = [&](int s) { return ws_sm + s * S::STAGE; };
   if (warp == kMmaWarp) tmem_alloc(&tbase, 2 * S::ACC_COLS);
   if (tid == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -176,7 +229,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
   if (warp == kProducerWarp) {
     // producer: B operand stages, up to kStages chunks ahead of the MMAs
     if (lane == 0) {
-      const size_t blk_bytes = (size_t)p.KC * S::B_BYTES;
+      const size_t blk_bytes = (size_t)p.KC * S::B_BLOCK;
       const unsigned char* Bg = static_cast<const unsigned char*>(p.B);
       for (int g = 0; g < G && !err; ++g) {
         const int s = g % kStages, r = g / kStages, u = g / p.KC, kc = g % p.KC;
@@ -186,17 +239,18 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         }
         const int tl = unit_tile(u), blk = u % p.nblk;
         const int2 i01 = p.tile_i01[tl];
-        mbar_arrive_expect_tx(&full_b[s], 2 * S::B_BYTES);
-        bulk_load(B0(s), Bg + ((size_t)i01.x * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BYTES, S::B_BYTES,
+        unsigned char* b = stage(s) + S::B_OFF;
+        mbar_arrive_expect_tx(&full_b[s], 2 * S::B_BLOCK);
+        bulk_load(b, Bg + ((size_t)i01.x * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BLOCK, S::B_BLOCK,
                   &full_b[s]);
-        bulk_load(B1(s), Bg + ((size_t)i01.y * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BYTES, S::B_BYTES,
-                  &full_b[s]);
+        bulk_load(b + S::B_BLOCK, Bg + ((size_t)i01.y * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BLOCK,
+                  S::B_BLOCK, &full_b[s]);
       }
     }
   } else if (warp == kMmaWarp) {
     // MMA issue
     if (lane == 0) {
-      const uint32_t idesc = umma_idesc_f16<false>(kUmmaTile, S::N);
+      const uint32_t idesc = Op::idesc(S::N);
       for (int g = 0; g < G && !err; ++g) {
         const int s = g % kStages, r = g / kStages, u = g / p.KC, kc = g % p.KC;
         const int a = u & 1;
@@ -205,7 +259,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         if (!err && !mbar_spin_bounded(&full_a[s], r & 1, kWaitLimit)) err = 1;
         if (err) break;
         tc_fence_after_sync();
-        mma_chunk(tm + (uint32_t)(a * S::ACC_COLS), idesc, A0(s), A1(s), B0(s), B1(s), kc == 0);
+        mma_chunk<Op, Db>(tm + (uint32_t)(a * S::ACC_COLS), idesc, stage(s), kc == 0);
         umma_commit(&empty[s]);
         if (kc == p.KC - 1) umma_commit(&acc_full[a]);
       }
@@ -213,7 +267,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
   } else {
     // builders: A stages, then the epilogue of the previous unit
     const int t = tid;
-    const __half2* Ph = static_cast<const __half2*>(p.Phat);
+    const In* Ph = static_cast<const In*>(p.Phat);
     auto epilogue = [&](int u) {
       const int a = u & 1, tl = unit_tile(u), blk = u % p.nblk;
       if (!mbar_spin_bounded(&acc_full[a], (u >> 1) & 1, kWaitLimit)) err = 1;
@@ -222,11 +276,11 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
       const int row = t & (kUmmaTile - 1), half = t >> 7;
       const int pix = p.tile_pix[(size_t)tl * kUmmaTile + row];
       const float ac = p.tile_acut[(size_t)tl * kUmmaTile + row];
-      __half2* crow = static_cast<__half2*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
+      Out* crow = static_cast<Out*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
       const uint32_t acc = tm + (uint32_t)(a * S::ACC_COLS);
       if (!err) {
-        if (Db >= 32) epilogue_cols<Db>(acc, warp, pix, p.scale * ac, crow, blk, p.D, half * (Db / 2), Db / 2);
-        else if (half == 0) epilogue_cols<Db>(acc, warp, pix, p.scale * ac, crow, blk, p.D, 0, Db);
+        if (Db >= 32) epilogue_cols<Op, Db>(acc, warp, pix, p.scale * ac, crow, blk, p.D, half * (Db / 2), Db / 2);
+        else if (half == 0) epilogue_cols<Op, Db>(acc, warp, pix, p.scale * ac, crow, blk, p.D, 0, Db);
       }
       tc_fence_before_sync();
       mbar_arrive(&acc_empty[a]);
@@ -246,16 +300,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         ra[i] = p.tile_alpha[(size_t)tl * kUmmaTile + r];
       }
     };
-    auto load_h = [&](__half2 (&h)[A::kIters], int kc) {
+    auto load_h = [&](In (&h)[A::kIters], int kc) {
 #pragma unroll
       for (int i = 0; i < A::kIters; ++i) {
         int r, q;
         A::coords(i, t, r, q);
-        const int f = kc * kQ + q;
-        h[i] = (rp[i] >= 0 && f < p.F) ? Ph[(size_t)rp[i] * p.F + f] : __floats2half2_rn(0.f, 0.f);
+        const int f = kc * Op::kQ + q;
+        h[i] = (rp[i] >= 0 && f < p.F) ? Ph[(size_t)rp[i] * p.F + f] : Op::zero();
       }
     };
-    __half2 hc[A::kIters], hn[A::kIters];
+    In hc[A::kIters], hn[A::kIters];
     if (U > 0) {
       load_rows(0);
       load_h(hc, 0);
@@ -273,11 +327,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         for (int i = 0; i < A::kIters; ++i) {
           int rr, q;
           A::coords(i, t, rr, q);
-          const uint32_t off = umma_kmajor_offset(rr, 2 * q, kUmmaKChunk);
-          const float2 v = __half22float2(hc[i]);
-          const float w0 = 1.f - ra[i];
-          *reinterpret_cast<__half2*>(A0(s) + off) = __floats2half2_rn(w0 * v.x, w0 * v.y);
-          *reinterpret_cast<__half2*>(A1(s) + off) = __floats2half2_rn(ra[i] * v.x, ra[i] * v.y);
+          A::put(stage(s), rr, q, Op::load(hc[i]), ra[i]);
         }
         fence_proxy_async_smem();
         mbar_arrive(&full_a[s]);
@@ -309,19 +359,18 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
 // ---------------------------------------------------------------------------
 constexpr int kThreads = 256;
 
-template <int Db>
+template <class Op, int Db>
 __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p) {
-  using S = Sizes<Db>;
-  using A = AChunk<kThreads>;
+  using S = Sizes<Op, Db>;
+  using A = AChunk<Op, kThreads>;
+  using In = typename Op::In;
+  using Out = typename Op::Out;
   extern __shared__ __align__(128) unsigned char um_sm[];
   __shared__ uint64_t bar_load, bar_mma;
   __shared__ uint32_t tbase;
   __shared__ int spix[kUmmaTile];
   __shared__ float salpha[kUmmaTile];
-  unsigned char* A0 = um_sm;
-  unsigned char* A1 = um_sm + S::A_BYTES;
-  unsigned char* B0 = um_sm + 2 * S::A_BYTES;
-  unsigned char* B1 = B0 + S::B_BYTES;
+  unsigned char* B = um_sm + S::B_OFF;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & (kUmmaTile - 1), half = tid >> 7;
   const int tile = blockIdx.x;
@@ -332,7 +381,7 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
     spix[tid] = p.tile_pix[(size_t)tile * kUmmaTile + tid];
     salpha[tid] = p.tile_alpha[(size_t)tile * kUmmaTile + tid];
   }
-  const __half2* Ph = static_cast<const __half2*>(p.Phat);
+  const In* Ph = static_cast<const In*>(p.Phat);
   if (warp == 0) tmem_alloc(&tbase, S::ACC_COLS);
   if (tid == 0) {
     mbar_init(&bar_load, 1);
@@ -342,11 +391,21 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
   tc_fence_before_sync();
   __syncthreads();
   tc_fence_after_sync();
-  __half2 hcur[A::kIters], hnext[A::kIters];
-  A::load(hcur, Ph, p.F, spix, 0, tid);
+  auto load_h = [&](In (&h)[A::kIters], int kc) {
+#pragma unroll
+    for (int i = 0; i < A::kIters; ++i) {
+      int r, q;
+      A::coords(i, tid, r, q);
+      const int f = kc * Op::kQ + q;
+      const int px = spix[r];
+      h[i] = (px >= 0 && f < p.F) ? Ph[(size_t)px * p.F + f] : Op::zero();
+    }
+  };
+  In hcur[A::kIters], hnext[A::kIters];
+  load_h(hcur, 0);
   const uint32_t dt = tbase;
-  const uint32_t idesc = umma_idesc_f16<false>(kUmmaTile, S::N);
-  const size_t blk_bytes = (size_t)p.KC * S::B_BYTES;
+  const uint32_t idesc = Op::idesc(S::N);
+  const size_t blk_bytes = (size_t)p.KC * S::B_BLOCK;
   const unsigned char* Bg = static_cast<const unsigned char*>(p.B);
   int phase = 0;
   bool ok = true;
@@ -356,19 +415,24 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
     for (int kc = 0; kc < p.KC; ++kc) {
       if (tid == 0) {
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bar_load, 2 * S::B_BYTES);
-        bulk_load(B0, b0g + (size_t)kc * S::B_BYTES, S::B_BYTES, &bar_load);
-        bulk_load(B1, b1g + (size_t)kc * S::B_BYTES, S::B_BYTES, &bar_load);
+        mbar_arrive_expect_tx(&bar_load, 2 * S::B_BLOCK);
+        bulk_load(B, b0g + (size_t)kc * S::B_BLOCK, S::B_BLOCK, &bar_load);
+        bulk_load(B + S::B_BLOCK, b1g + (size_t)kc * S::B_BLOCK, S::B_BLOCK, &bar_load);
       }
-      A::store(A0, A1, hcur, salpha, tid);
+#pragma unroll
+      for (int i = 0; i < A::kIters; ++i) {
+        int r, q;
+        A::coords(i, tid, r, q);
+        A::put(um_sm, r, q, Op::load(hcur[i]), salpha[r]);
+      }
       // the next chunk's phasors are in flight while this chunk's MMAs run
-      A::load(hnext, Ph, p.F, spix, kc + 1 < p.KC ? kc + 1 : 0, tid);
+      load_h(hnext, kc + 1 < p.KC ? kc + 1 : 0);
       fence_proxy_async_smem();
       __syncthreads();
       if (tid == 0) {
         ok = mbar_spin_bounded(&bar_load, phase, kWaitLimit);
         tc_fence_after_sync();
-        if (ok) mma_chunk(dt, idesc, A0, A1, B0, B1, kc == 0);
+        if (ok) mma_chunk<Op, Db>(dt, idesc, um_sm, kc == 0);
         umma_commit(&bar_mma);
       }
       // the MMAs read A and B; they finish before the next chunk overwrites them
@@ -382,9 +446,9 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
     if (!ok) break;
     // epilogue: warps w and w + 4 share the rows of lane quarter w % 4
     tc_fence_after_sync();
-    __half2* crow = static_cast<__half2*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
-    if (Db >= 32) epilogue_cols<Db>(dt, warp, pix, p.scale * ac, crow, blk, p.D, half * (Db / 2), Db / 2);
-    else if (half == 0) epilogue_cols<Db>(dt, warp, pix, p.scale * ac, crow, blk, p.D, 0, Db);
+    Out* crow = static_cast<Out*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
+    if (Db >= 32) epilogue_cols<Op, Db>(dt, warp, pix, p.scale * ac, crow, blk, p.D, half * (Db / 2), Db / 2);
+    else if (half == 0) epilogue_cols<Op, Db>(dt, warp, pix, p.scale * ac, crow, blk, p.D, 0, Db);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
@@ -401,42 +465,57 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
 }
 
 // B operand blocks from the float64 radial kernel: block (bin, blk), chunk kc,
-// row n (output column: Re of depth blk Db + n for n < Db, Im of depth
-// blk Db + n - Db otherwise), column k = 2 f + part (part 0 multiplies Re Phat,
-// part 1 Im Phat):
+// part, row n (output column: Re of depth blk Db + n for n < Db, Im of depth
+// blk Db + n - Db otherwise), column k = 2 f + c (c = 0 multiplies Re Phat,
+// c = 1 Im Phat):
 //   Re row: (Kr, -Ki),  Im row: (Ki, Kr),  zero beyond F and beyond D.
-__global__ void kr_store_umma_kernel(const double2* K64, __half* B, int n_rho, int F, int D, int Db, int nblk,
+// f16 kind: one part, the scaled value; tf32 kind: parts hi = tf32(v),
+// lo = tf32(v - hi) of the float32 value v.
+template <class Op>
+__global__ void kr_store_umma_kernel(const double2* K64, unsigned char* B, int n_rho, int F, int D, int Db, int nblk,
                                      int KC, double scale) {
+  constexpr int kCols = kUmmaRowBytes / Op::kElem;
   const long long N = 2LL * Db;
-  const long long per_chunk = N * kUmmaKChunk;
+  const long long per_chunk = N * kCols;
   const long long total = (long long)n_rho * nblk * KC * per_chunk;
+  const size_t part_bytes = (size_t)N * kUmmaRowBytes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long chunk = i / per_chunk;
     const int e = (int)(i % per_chunk);
-    const int n = e / kUmmaKChunk, kj = e % kUmmaKChunk;
+    const int n = e / kCols, kj = e % kCols;
     const int kc = (int)(chunk % KC);
     const int blk = (int)((chunk / KC) % nblk);
     const int bin = (int)(chunk / ((long long)KC * nblk));
-    const int k = kc * kUmmaKChunk + kj;
+    const int k = kc * kCols + kj;
     const bool im_row = n >= Db;
     const int d = blk * Db + (im_row ? n - Db : n);
     double v = 0.0;
-    const int f = k >> 1, part = k & 1;
+    const int f = k >> 1, c = k & 1;
     if (d < D && f < F) {
       const double2 kv = K64[((size_t)bin * F + f) * D + d];
-      if (!im_row) v = part == 0 ? kv.x : -kv.y;
-      else v = part == 0 ? kv.y : kv.x;
+      if (!im_row) v = c == 0 ? kv.x : -kv.y;
+      else v = c == 0 ? kv.y : kv.x;
     }
-    const size_t off = (size_t)chunk * per_chunk * 2 + umma_kmajor_offset(n, kj, kUmmaKChunk);   // bytes
-    B[off / 2] = __double2half(v * scale);
+    // element (n, kj) of a 64-byte-row operand: core matrix (n / 8, byte column / 16)
+    const int bc = kj * Op::kElem;
+    const size_t off = ((size_t)(n >> 3) * (kUmmaRowBytes / 16) + (bc >> 4)) * 128 + (n & 7) * 16 + (bc & 15);
+    unsigned char* base = B + (size_t)chunk * Op::kParts * part_bytes;
+    if (Op::kKind == kUmmaF16) {
+      *reinterpret_cast<__half*>(base + off) = __double2half(v * scale);
+    } else {
+      const float x = (float)(v * scale);
+      const float hi = to_tf32(x);
+      *reinterpret_cast<float*>(base + off) = hi;
+      *reinterpret_cast<float*>(base + part_bytes + off) = to_tf32(x - hi);
+    }
   }
 }
 
-template <int Db>
+template <class Op, int Db>
 cudaError_t launch_simple(const PfUmmaParams& p, cudaStream_t s) {
-  constexpr uint32_t smem = 2 * Sizes<Db>::A_BYTES + 2 * Sizes<Db>::B_BYTES;
-  auto k = pf_umma_kernel<Db>;
+  constexpr uint32_t smem = Sizes<Op, Db>::STAGE;
+  auto k = pf_umma_kernel<Op, Db>;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -447,10 +526,10 @@ cudaError_t launch_simple(const PfUmmaParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int Db>
+template <class Op, int Db>
 cudaError_t launch_ws(const PfUmmaParams& p, cudaStream_t s) {
-  constexpr uint32_t smem = kStages * Sizes<Db>::STAGE;
-  auto k = pf_umma_ws_kernel<Db>;
+  constexpr uint32_t smem = Sizes<Op, Db>::STAGES * Sizes<Op, Db>::STAGE;
+  auto k = pf_umma_ws_kernel<Op, Db>;
   static int sms = 0;
   if (sms == 0) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -465,22 +544,35 @@ cudaError_t launch_ws(const PfUmmaParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-}  // namespace
-
-cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
-  if (p.ntiles <= 0) return cudaSuccess;
+template <class Op>
+cudaError_t launch_kind(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
   switch (p.Db) {
-    case 16: return pipelined ? launch_ws<16>(p, s) : launch_simple<16>(p, s);
-    case 32: return pipelined ? launch_ws<32>(p, s) : launch_simple<32>(p, s);
-    case 64: return pipelined ? launch_ws<64>(p, s) : launch_simple<64>(p, s);
-    case 128: return pipelined ? launch_ws<128>(p, s) : launch_simple<128>(p, s);
+    case 16: return pipelined ? launch_ws<Op, 16>(p, s) : launch_simple<Op, 16>(p, s);
+    case 32: return pipelined ? launch_ws<Op, 32>(p, s) : launch_simple<Op, 32>(p, s);
+    case 64: return pipelined ? launch_ws<Op, 64>(p, s) : launch_simple<Op, 64>(p, s);
+    case 128: return pipelined ? launch_ws<Op, 128>(p, s) : launch_simple<Op, 128>(p, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_kr_store_umma(const double2* K64, void* B, int n_rho, int F, int D, int Db, int nblk, int KC,
-                                 double scale, cudaStream_t s) {
-  kr_store_umma_kernel<<<152 * 8, 256, 0, s>>>(K64, static_cast<__half*>(B), n_rho, F, D, Db, nblk, KC, scale);
+}  // namespace
+
+cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
+  if (p.ntiles <= 0) return cudaSuccess;
+  if (p.kind == kUmmaF16) return launch_kind<OpF16>(p, pipelined, s);
+  if (p.kind == kUmmaTf32x3) return launch_kind<OpTf32x3>(p, pipelined, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_kr_store_umma(const double2* K64, void* B, int kind, int n_rho, int F, int D, int Db, int nblk,
+                                 int KC, double scale, cudaStream_t s) {
+  unsigned char* b = static_cast<unsigned char*>(B);
+  if (kind == kUmmaF16)
+    kr_store_umma_kernel<OpF16><<<152 * 8, 256, 0, s>>>(K64, b, n_rho, F, D, Db, nblk, KC, scale);
+  else if (kind == kUmmaTf32x3)
+    kr_store_umma_kernel<OpTf32x3><<<152 * 8, 256, 0, s>>>(K64, b, n_rho, F, D, Db, nblk, KC, scale);
+  else
+    return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

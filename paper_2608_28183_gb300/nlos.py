@@ -31,7 +31,8 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_server_stats", "nlos_server_destroy", "nlos_workspace_check", "nlos_selftest_bounded_wait",
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
             "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
-            "nlos_reconstruct_host_many", "nlos_debug_fail_allocation", "nlos_selftest_umma"]
+            "nlos_reconstruct_host_many", "nlos_debug_fail_allocation", "nlos_selftest_umma",
+            "nlos_selftest_umma_kind"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -115,6 +116,8 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_debug_fail_allocation.restype = None
     lib.nlos_selftest_umma.argtypes = [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
     lib.nlos_selftest_umma.restype = ctypes.c_int
+    lib.nlos_selftest_umma_kind.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
+    lib.nlos_selftest_umma_kind.restype = ctypes.c_int
     for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda", "nlos_bin_transient",
                  "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors", "nlos_reconstruct_host_many"):
         getattr(lib, name).restype = ctypes.c_int

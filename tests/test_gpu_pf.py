@@ -99,3 +99,29 @@ def test_pf_parity_any_size(geom, depths, zr):
     ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float32), oplan)
     assert rel_l2(got, ref) <= 1e-5
     assert same_peak(got, ref)
+
+
+@pytest.mark.parametrize("depths", [40, 7, 150])
+def test_pf_fp32_tensor_core_and_ffma_depth_sums(depths):
+    """FP32 plans run the depth sum as three tf32 tensor-core products per
+    term (launch shape 0: persistent warp-specialised CTAs; shape 2: one CTA
+    per tile) or on FP32 FMAs (shape 1): each within 1e-5 of the FP64
+    oracle with the same peak voxel, for depth counts below, inside and
+    across the 128-depth blocks of the tensor-core forms."""
+    from paper_2608_28183_gb300 import nlos
+    g = synth.Geometry(32, 32, 512, 16e-12, 1.0, 1.0)
+    plan, oplan = _pair(g, (depths, 0.4, 1.2))
+    cap = _capture(g, seed=depths, zr=(0.5, 1.1))
+    names = [nlos.load_library().nlos_plan_stage_name(plan.handle, i).decode() for i in range(len(plan.tiles))]
+    stage = names.index("pf_depth_sum")
+    out = {}
+    for v in (0, 1, 2):
+        t = plan.tiles
+        t[stage] = v
+        plan.tiles = t
+        out[v] = _gpu(plan, cap.counts)
+    ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float32), oplan)
+    for v in (0, 1, 2):
+        assert rel_l2(out[v], ref) <= 1e-5, (v, rel_l2(out[v], ref))
+        assert same_peak(out[v], ref)
+    assert rel_l2(out[2], out[0]) <= 1e-7      # same arithmetic, same order per tile
