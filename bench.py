@@ -357,6 +357,38 @@ def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000), seconds=2.0, b
     return {"budget_gb": budget_gb, "slots": 8, "shapes": len(specs), "sweep": results}
 
 
+def depth_sum_roofline(plan, g, F, D, ms, storage):
+    """Roofline of the phasor-field depth sum in the form the plan runs: on the
+    tensor cores, two real products (A0 B0^T + A1 B1^T) per pixel of the
+    padded grid with K = 2F and N = 2D - once in f16 for 16-bit plans, three
+    times in tf32 (hi*hi + hi*lo + lo*hi) for float32 plans - against the
+    measured dense bf16 peak (f16) or that peak x 1.1/2.25, the nominal
+    tf32/bf16 ratio (tf32); on FP32 FMAs against 152 SMs x 128 lanes x 2 flop
+    x 2.07 GHz."""
+    from paper_2608_28183_gb300 import nlos
+    lib = nlos.load_library()
+    names = [lib.nlos_plan_stage_name(plan.handle, i).decode() for i in range(len(plan.tiles))]
+    shape = plan.tiles[names.index("pf_depth_sum")]
+    npix = 4 * g.nx * g.ny
+    if shape == 1:
+        flops = npix * F * D * 12          # per (pixel, f, d): lerp 2 FMA + complex MAC 4 FMA
+        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        return {"bound": "alu", "form": "ffma", "flops": flops, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
+                "peak_tflops": peak, "frac": flops / (ms * 1e-3) / 1e12 / peak,
+                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz max clock"}
+    peaks, _ = measured_peaks()
+    bf16 = float(peaks.get("bf16_tflops", 0.0)) or 1900.0
+    one = 2 * npix * (2 * F) * (2 * D) * 2
+    if storage == "f32":
+        flops, peak, note = 3 * one, bf16 * 1.1 / 2.25, "measured dense bf16 x 1.1/2.25 (nominal tf32/bf16)"
+    else:
+        flops, peak, note = one, bf16, "measured dense bf16 (f16 runs at the same rate)"
+    return {"bound": "tensor", "form": "tf32x3" if storage == "f32" else "f16",
+            "schedule": "persistent" if shape == 0 else "cta_per_tile", "flops": flops, "algorithmic_flops": one,
+            "achieved_tflops": flops / (ms * 1e-3) / 1e12, "peak_tflops": peak,
+            "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_note": note}
+
+
 def pf_bench(torch, nlos, synth, steps=200, with_oracle=True):
     """Phasor-field workload: 128 x 128 x 1024 over 2 m, 16 ps, 128 planes
     0.5-2.5 m (151 band frequencies), FP32 and FP16 storage."""
@@ -381,27 +413,10 @@ def pf_bench(torch, nlos, synth, steps=200, with_oracle=True):
                "stages_ms": {k: val / calls for k, val in stages.items()}}
         if storage == "f32":
             vol32 = v.cpu().numpy()
-            band = 151
-            npix = 4 * g.nx * g.ny
-            flops = npix * band * 128 * 12          # per (pixel, f, d): lerp 2 FMA + complex MAC 4 FMA
-            ms = rec["stages_ms"]["pf_depth_sum"]
-            rec["depth_sum_alu"] = {"bound": "alu", "flops": flops, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
-                                    "peak_tflops": 152 * 128 * 2 * 2.07e9 / 1e12,
-                                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz max clock"}
-            rec["depth_sum_alu"]["frac"] = rec["depth_sum_alu"]["achieved_tflops"] / rec["depth_sum_alu"]["peak_tflops"]
         else:
             rec["rel_l2_vs_f32"] = float(np.linalg.norm(v.cpu().numpy() - vol32) / np.linalg.norm(vol32))
-            # tensor-core depth sum: two real products (A0 B0^T + A1 B1^T) per
-            # pixel inside the cutoff, K = 2F, N = 2 x planes
-            peaks, _ = measured_peaks()
-            tpeak = float(peaks.get("bf16_tflops", 0.0)) or 1900.0
-            npix = 4 * g.nx * g.ny
-            tflops = 2 * npix * (2 * 151) * (2 * 128) * 2
-            ms = rec["stages_ms"]["pf_depth_sum"]
-            rec["depth_sum_tensor"] = {"bound": "tensor", "flops": tflops,
-                                       "achieved_tflops": tflops / (ms * 1e-3) / 1e12, "peak_tflops": tpeak,
-                                       "peak_note": "measured dense bf16 (f16 runs at the same rate)",
-                                       "frac": tflops / (ms * 1e-3) / 1e12 / tpeak, "tiles_tuned": plan.tiles}
+        rec["depth_sum_roofline"] = depth_sum_roofline(plan, g, 151, 128, rec["stages_ms"]["pf_depth_sum"], storage)
+        out[storage] = rec
         out[storage] = rec
     # dense Fourier-domain kernel (Alg. 3) on the same workload: the depth sum
     # streams the whole kernel (4ab x F x D complex float32) once per volume

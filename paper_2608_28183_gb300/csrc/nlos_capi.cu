@@ -405,7 +405,7 @@ nlos_status_t build_pf(nlos_plan_s* p) {
     p->nblk_u = (p->D + p->Db_u - 1) / p->Db_u;
     p->KC_u = (2 * p->F + cols - 1) / cols;
     const size_t bbytes =
-        (size_t)n_rho * p->nblk_u * p->KC_u * umma_parts(p->kind_u) * (2 * p->Db_u) * kUmmaRowBytes;
+        (size_t)n_rho * p->nblk_u * p->KC_u * umma_parts(p->kind_u) * (2 * p->Db_u) * umma_row_bytes(p->kind_u);
     st = dalloc(p, &p->Bu, bbytes, "tensor-core kernel operands");
     if (st == NLOS_OK)
       e = launch_kr_store_umma(dK64, p->Bu, p->kind_u, n_rho, p->F, p->D, p->Db_u, p->nblk_u, p->KC_u,

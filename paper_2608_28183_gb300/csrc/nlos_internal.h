@@ -171,15 +171,16 @@ cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int st
 //    x_hi = tf32(x), x_lo = tf32(x - x_hi), and A B^T taken as
 //    A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (kind::tf32 MMAs; the dropped
 //    A_lo B_lo^T term is ~2^-22 of the product), fp32 accumulation.
-// Both kinds stage 64-byte operand rows per chunk: 32 f16 or 16 tf32 columns.
+// Operand rows per chunk: 64 bytes - 32 f16 columns (16 frequencies) or 16
+// tf32 columns (8 frequencies).
 constexpr int kUmmaTile = 128;           // pixels per tile (MMA M)
-constexpr int kUmmaRowBytes = 64;        // bytes of one operand row per chunk
 enum UmmaKind { kUmmaF16 = 0, kUmmaTf32x3 = 1 };
+__host__ __device__ constexpr int umma_row_bytes(int) { return 64; }
 __host__ __device__ constexpr int umma_chunk_cols(int kind) { return kind == kUmmaF16 ? 32 : 16; }
 __host__ __device__ constexpr int umma_parts(int kind) { return kind == kUmmaF16 ? 1 : 2; }
 struct PfUmmaParams {
   const void* Phat;            // [npix][F] half2 (f16 kind) or float2 (tf32 kind)
-  const void* B;               // [n_rho][nblk][KC][parts][2 Db rows x 64 bytes], operand layout
+  const void* B;               // [n_rho][nblk][KC][parts][2 Db rows x row bytes], operand layout
   void* C;                     // [npix][D] half2 or float2
   const int2* tile_i01;        // [ntiles]
   const int* tile_pix;         // [ntiles][128] pixel or -1
@@ -187,6 +188,7 @@ struct PfUmmaParams {
   const float* tile_acut;      // [ntiles][128]
   int ntiles, F, D, Db, nblk, KC;
   int kind;                    // UmmaKind
+  int split;                   // set by the launcher: parts of a tail unit's frequency sum
   float scale;
   int* err;                    // device error word (bounded waits)
 };

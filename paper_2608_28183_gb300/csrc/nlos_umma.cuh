@@ -132,6 +132,34 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                : "memory");
 }
 
+// asynchronous copy of `bytes` (4, 8 or 16) global -> shared by this thread;
+// src_bytes = 0 writes zeros instead of reading src (src must still be a
+// valid address). Completion: cp_async_commit / cp_async_wait<n>.
+__device__ __forceinline__ void cp_async(void* dst, const void* src, uint32_t src_bytes, int bytes) {
+  if (bytes == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// wait until at most n of this thread's committed groups are still pending
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(n) : "memory");
+}
+
+// hint: bring `bytes` of global memory at src into L2 (src 16-byte aligned,
+// bytes a multiple of 16)
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
+               : "memory");
+}
+
 // byte offset of element (r, k) of a K-major no-swizzle operand whose rows
 // hold kcols elements (16-bit): core matrix (r / 8, k / 8), LBO = 128 bytes,
 // SBO = kcols / 8 * 128 bytes

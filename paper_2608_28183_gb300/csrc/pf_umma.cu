@@ -27,8 +27,10 @@
 // Two schedules:
 //  * pf_umma_ws_kernel: one persistent CTA per SM, warp-specialised - a
 //    producer warp keeps up to four operand stages in flight, eight warps
-//    build A and run the epilogue, one thread issues the MMAs - with two
-//    accumulators so a tile's epilogue overlaps the next tile's MMAs;
+//    build A, one thread issues the MMAs, four warps run the epilogue - with
+//    two accumulators so a tile's epilogue overlaps the next tile's MMAs; the
+//    tiles left after the last full round are split along the frequency sum
+//    so that no CTA runs a whole extra tile;
 //  * pf_umma_kernel: one CTA per tile, one stage.
 #include <cuda_fp16.h>
 
@@ -40,8 +42,6 @@ namespace nlos {
 namespace {
 
 constexpr int kWaitLimit = 1 << 26;                    // probes of a barrier (a few hundred ms)
-constexpr uint32_t kSbo = (kUmmaRowBytes / 16) * 128;  // row-group stride of a chunk operand
-constexpr uint32_t kABytes = kUmmaTile * kUmmaRowBytes;  // one A operand part of a chunk
 constexpr uint32_t kSmemBudget = 200 * 1024;           // dynamic shared memory of the stages
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -49,18 +49,25 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // byte offset of the complex value of frequency q (within the chunk) of
-// operand row r: columns (2q, 2q + 1), elements of `elem` bytes, 64-byte rows
-// in 8 x 16-byte core matrices
-__host__ __device__ constexpr uint32_t chunk_offset(int r, int q, int elem) {
-  return (uint32_t)(((r >> 3) * (kUmmaRowBytes / 16) + ((2 * q * elem) >> 4)) * 128 + (r & 7) * 16 +
-                    ((2 * q * elem) & 15));
+// operand row r: columns (2q, 2q + 1), kRowBytes-byte rows in 8 x 16-byte
+// core matrices
+template <class Op>
+__host__ __device__ constexpr uint32_t chunk_offset(int r, int q) {
+  return (uint32_t)(((r >> 3) * (Op::kRowBytes / 16) + ((2 * q * Op::kElem) >> 4)) * 128 + (r & 7) * 16 +
+                    ((2 * q * Op::kElem) & 15));
 }
 
 struct OpF16 {
   using In = __half2;    // phasor element
   using Out = __half2;   // depth-sum element
   static constexpr int kKind = kUmmaF16, kElem = 2, kParts = 1, kSlab = 16;
-  static constexpr int kQ = kUmmaRowBytes / (2 * kElem);   // frequencies per chunk
+  // L2 prefetch of B blocks ahead of their copies: it shortens the copies of
+  // the two-stage tf32 ring; the four-stage f16 ring does not gain from it
+  static constexpr bool kPrefetchB = false;
+  static constexpr uint32_t kRowBytes = 64;                 // bytes of an operand row per chunk
+  static constexpr uint32_t kSbo = (kRowBytes / 16) * 128;  // row-group stride of a chunk operand
+  static constexpr uint32_t kABytes = kUmmaTile * kRowBytes;  // one A operand part of a chunk
+  static constexpr int kQ = kRowBytes / (2 * kElem);        // frequencies per chunk
   __device__ static __forceinline__ float2 load(In v) { return __half22float2(v); }
   __device__ static __forceinline__ In zero() { return __floats2half2_rn(0.f, 0.f); }
   // A operand parts of one weight at byte offset off
@@ -78,7 +85,11 @@ struct OpTf32x3 {
   using In = float2;
   using Out = float2;
   static constexpr int kKind = kUmmaTf32x3, kElem = 4, kParts = 2, kSlab = 8;
-  static constexpr int kQ = kUmmaRowBytes / (2 * kElem);
+  static constexpr bool kPrefetchB = true;
+  static constexpr uint32_t kRowBytes = 64;
+  static constexpr uint32_t kSbo = (kRowBytes / 16) * 128;
+  static constexpr uint32_t kABytes = kUmmaTile * kRowBytes;
+  static constexpr int kQ = kRowBytes / (2 * kElem);
   __device__ static __forceinline__ float2 load(In v) { return v; }
   __device__ static __forceinline__ In zero() { return make_float2(0.f, 0.f); }
   __device__ static __forceinline__ void put(unsigned char* a, uint32_t off, float x, float y) {
@@ -93,15 +104,22 @@ struct OpTf32x3 {
   __device__ static __forceinline__ Out out(float x, float y) { return make_float2(x, y); }
 };
 
+static_assert(OpF16::kRowBytes == umma_row_bytes(kUmmaF16) &&
+                  OpF16::kRowBytes / OpF16::kElem == umma_chunk_cols(kUmmaF16),
+              "f16 chunk geometry");
+static_assert(OpTf32x3::kRowBytes == umma_row_bytes(kUmmaTf32x3) &&
+                  OpTf32x3::kRowBytes / OpTf32x3::kElem == umma_chunk_cols(kUmmaTf32x3),
+              "tf32 chunk geometry");
+
 // Stage layout: A(w, part) for weights w = 0 (1 - alpha), 1 (alpha), then
 // B(bin, part) for bins i0, i1; the parts of one B block are contiguous in the
 // stage and in the plan's operand store, so one bulk copy brings a bin.
 template <class Op, int Db>
 struct Sizes {
   static constexpr int N = 2 * Db;
-  static constexpr uint32_t B_BYTES = N * kUmmaRowBytes;                      // one B part of a chunk
+  static constexpr uint32_t B_BYTES = N * Op::kRowBytes;                      // one B part of a chunk
   static constexpr uint32_t B_BLOCK = Op::kParts * B_BYTES;                    // all parts of one bin
-  static constexpr uint32_t B_OFF = 2 * Op::kParts * kABytes;
+  static constexpr uint32_t B_OFF = 2 * Op::kParts * Op::kABytes;
   static constexpr uint32_t STAGE = B_OFF + 2 * B_BLOCK;
   static constexpr int STAGES = kSmemBudget / STAGE >= 4 ? 4 : (int)(kSmemBudget / STAGE);
   static constexpr uint32_t ACC_COLS = N <= 32 ? 32 : N <= 64 ? 64 : N <= 128 ? 128 : 256;
@@ -125,10 +143,10 @@ struct AChunk {
   }
   // value v of row r with weight alpha into both A operands
   __device__ static __forceinline__ void put(unsigned char* stage, int r, int q, float2 v, float alpha) {
-    const uint32_t off = chunk_offset(r, q, Op::kElem);
+    const uint32_t off = chunk_offset<Op>(r, q);
     const float w0 = 1.f - alpha;
     Op::put(stage, off, w0 * v.x, w0 * v.y);
-    Op::put(stage + Op::kParts * kABytes, off, alpha * v.x, alpha * v.y);
+    Op::put(stage + Op::kParts * Op::kABytes, off, alpha * v.x, alpha * v.y);
   }
 };
 
@@ -138,26 +156,29 @@ __device__ __forceinline__ void mma_chunk(uint32_t acc, uint32_t idesc, const un
   using S = Sizes<Op, Db>;
   const uint32_t s0 = smem_u32(stage);
 #pragma unroll
-  for (int kk = 0; kk < kUmmaRowBytes / (Op::kElem * Op::kSlab); ++kk) {
+  for (int kk = 0; kk < (int)Op::kRowBytes / (Op::kElem * Op::kSlab); ++kk) {
     const uint32_t ko = kk * 256;     // an MMA reads 32 bytes of K: two 16-byte core-matrix columns
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
-      const uint32_t a_hi = s0 + w * Op::kParts * kABytes + ko;
+      const uint32_t a_hi = s0 + w * Op::kParts * Op::kABytes + ko;
       const uint32_t b_hi = s0 + S::B_OFF + w * S::B_BLOCK + ko;
-      Op::mma(acc, umma_smem_desc(a_hi, 128, kSbo), umma_smem_desc(b_hi, 128, kSbo), idesc,
+      constexpr uint32_t sbo = Op::kSbo;
+      Op::mma(acc, umma_smem_desc(a_hi, 128, sbo), umma_smem_desc(b_hi, 128, sbo), idesc,
               (first && kk == 0 && w == 0) ? 0u : 1u);
       if (Op::kParts == 2) {
-        Op::mma(acc, umma_smem_desc(a_hi, 128, kSbo), umma_smem_desc(b_hi + S::B_BYTES, 128, kSbo), idesc, 1u);
-        Op::mma(acc, umma_smem_desc(a_hi + kABytes, 128, kSbo), umma_smem_desc(b_hi, 128, kSbo), idesc, 1u);
+        Op::mma(acc, umma_smem_desc(a_hi, 128, sbo), umma_smem_desc(b_hi + S::B_BYTES, 128, sbo), idesc, 1u);
+        Op::mma(acc, umma_smem_desc(a_hi + Op::kABytes, 128, sbo), umma_smem_desc(b_hi, 128, sbo), idesc, 1u);
       }
     }
   }
 }
 
-// accumulator rows of one warp -> C (taper and scale), columns [c0, c0 + ncols)
+// accumulator rows of one warp -> C (taper and scale), columns [c0, c0 + ncols);
+// `add`: the accumulator holds part of the frequency sum and is added to C
+// (cleared beforehand) with atomics instead of stored
 template <class Op, int Db>
 __device__ __forceinline__ void epilogue_cols(uint32_t acc, int warp, int pix, float gsc, typename Op::Out* crow,
-                                              int blk, int D, int c0, int ncols) {
+                                              int blk, int D, int c0, int ncols, bool add = false) {
   using Out = typename Op::Out;
   constexpr int kVec = 16 / sizeof(Out);        // complex values per 16-byte store
   const uint32_t lane_base = acc + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -170,7 +191,11 @@ __device__ __forceinline__ void epilogue_cols(uint32_t acc, int warp, int pix, f
       Out o[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) o[q] = Op::out(gsc * __uint_as_float(re[q]), gsc * __uint_as_float(im[q]));
-      if (blk * Db + c + 16 <= D && (reinterpret_cast<uintptr_t>(crow + c) & 15) == 0) {
+      if (add) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+          if (blk * Db + c + q < D) atomicAdd(crow + c + q, o[q]);
+      } else if (blk * Db + c + 16 <= D && (reinterpret_cast<uintptr_t>(crow + c) & 15) == 0) {
         uint4* dst = reinterpret_cast<uint4*>(crow + c);
 #pragma unroll
         for (int v = 0; v < 16 / kVec; ++v) dst[v] = reinterpret_cast<const uint4*>(o)[v];
@@ -187,9 +212,55 @@ __device__ __forceinline__ void epilogue_cols(uint32_t acc, int warp, int pix, f
 // Warp-specialised persistent schedule
 // ---------------------------------------------------------------------------
 constexpr int kMaxStages = 4;
-constexpr int kWsBuilders = 256;                 // warps 0-7: A build, epilogue
-constexpr int kWsThreads = kWsBuilders + 64;     // warp 8: producer, warp 9: MMA issue
-constexpr int kProducerWarp = kWsBuilders / 32, kMmaWarp = kProducerWarp + 1;
+// parts of a tail unit's frequency sum: with at most two, every element of C
+// receives at most two atomic additions onto an exact zero (0 + x is exact,
+// x + y = y + x), so the result does not depend on their order
+constexpr int kMaxSplit = 2;
+constexpr int kWsBuilders = 256;                 // warps 0-7: A build
+constexpr int kProducerWarp = kWsBuilders / 32;  // warp 8: B copies
+constexpr int kMmaWarp = kProducerWarp + 1;      // warp 9: MMA issue
+constexpr int kEpiWarp0 = kMmaWarp + 1;          // warps 10-13: epilogue, one per TMEM lane quarter
+constexpr int kEpiThreads = 128;
+constexpr int kWsThreads = kWsBuilders + 64 + kEpiThreads;
+
+// The work of CTA b: R = ntiles / grid rounds of whole tiles (tile b + k grid,
+// all its depth blocks, every chunk), then the tail - the ntiles - R grid
+// remaining tiles' units, each split into `split` chunk ranges - as segments
+// b, b + grid, ... of the tail list. A segment that covers part of a unit's
+// frequency sum adds its result to C.
+struct Seg {
+  int tile, blk, k0, k1;
+  bool partial;
+};
+struct WsWork {
+  int R, nseg;
+  __device__ WsWork(const PfUmmaParams& p) {
+    const int b = blockIdx.x, grid = gridDim.x;
+    R = p.ntiles / grid;
+    const int ntail = (p.ntiles - R * grid) * p.nblk * p.split;
+    nseg = R * p.nblk + (ntail > b ? (ntail - b + grid - 1) / grid : 0);
+  }
+  __device__ Seg seg(const PfUmmaParams& p, int j) const {
+    const int b = blockIdx.x, grid = gridDim.x;
+    Seg s;
+    if (j < R * p.nblk) {
+      s.tile = b + (j / p.nblk) * grid;
+      s.blk = j % p.nblk;
+      s.k0 = 0;
+      s.k1 = p.KC;
+      s.partial = false;
+    } else {
+      const int t = b + (j - R * p.nblk) * grid;
+      const int tu = t / p.split, part = t % p.split;
+      s.tile = R * grid + tu / p.nblk;
+      s.blk = tu % p.nblk;
+      s.k0 = part * p.KC / p.split;
+      s.k1 = (part + 1) * p.KC / p.split;
+      s.partial = p.split > 1;
+    }
+    return s;
+  }
+};
 
 template <class Op, int Db>
 __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaParams p) {
@@ -212,7 +283,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
-      mbar_init(&acc_empty[a], kWsBuilders);
+      mbar_init(&acc_empty[a], kEpiThreads);
     }
     mbar_fence_init();
   }
@@ -220,78 +291,110 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
   __syncthreads();
   tc_fence_after_sync();
   const uint32_t tm = tbase;
-  const int ntiles_mine = (p.ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-  const int U = ntiles_mine * p.nblk;           // units: (tile, depth block)
-  const int G = U * p.KC;                       // chunks
-  auto unit_tile = [&](int u) { return (int)blockIdx.x + (u / p.nblk) * (int)gridDim.x; };
+  const WsWork W(p);
+  const int nseg = W.nseg;
   int err = 0;
 
   if (warp == kProducerWarp) {
-    // producer: B operand stages, up to kStages chunks ahead of the MMAs
-    if (lane == 0) {
-      const size_t blk_bytes = (size_t)p.KC * S::B_BLOCK;
-      const unsigned char* Bg = static_cast<const unsigned char*>(p.B);
-      for (int g = 0; g < G && !err; ++g) {
-        const int s = g % kStages, r = g / kStages, u = g / p.KC, kc = g % p.KC;
-        if (r >= 1 && !mbar_spin_bounded(&empty[s], (r - 1) & 1, kWaitLimit)) {
-          err = 1;
-          break;
+    // producer: lane 0 keeps B operand stages up to kStages chunks ahead of
+    // the MMAs and, for the tf32 kind (two stages of 96 KB), asks L2 for the
+    // B blocks kPrefetch chunks ahead
+    const size_t blk_bytes = (size_t)p.KC * S::B_BLOCK;
+    const unsigned char* Bg = static_cast<const unsigned char*>(p.B);
+    auto b_block = [&](const Seg& sg, int kc, int bin) {
+      const int2 i01 = p.tile_i01[sg.tile];
+      const int b = bin ? i01.y : i01.x;
+      return Bg + ((size_t)b * p.nblk + sg.blk) * blk_bytes + (size_t)kc * S::B_BLOCK;
+    };
+    // prefetch cursor: kPrefetch chunks ahead of the copies
+    constexpr int kPrefetch = 2 * kStages;
+    int pj = 0, pk = 0;
+    Seg ps{};
+    if (nseg > 0) {
+      ps = W.seg(p, 0);
+      pk = ps.k0;
+    }
+    auto advance = [&]() {
+      if (pj >= nseg) return;
+      if (++pk >= ps.k1 && ++pj < nseg) {
+        ps = W.seg(p, pj);
+        pk = ps.k0;
+      }
+    };
+    for (int i = 0; i < kPrefetch; ++i) advance();
+    int g = 0;
+    for (int j = 0; j < nseg && !err; ++j) {
+      const Seg sg = W.seg(p, j);
+      for (int kc = sg.k0; kc < sg.k1; ++kc, ++g) {
+        const int s = g % kStages, r = g / kStages;
+        if (lane == 0) {
+          if (r >= 1 && !mbar_spin_bounded(&empty[s], (r - 1) & 1, kWaitLimit)) err = 1;
+          if (!err) {
+            unsigned char* b = stage(s) + S::B_OFF;
+            mbar_arrive_expect_tx(&full_b[s], 2 * S::B_BLOCK);
+            bulk_load(b, b_block(sg, kc, 0), S::B_BLOCK, &full_b[s]);
+            bulk_load(b + S::B_BLOCK, b_block(sg, kc, 1), S::B_BLOCK, &full_b[s]);
+            if (Op::kPrefetchB && pj < nseg) {
+              bulk_prefetch_l2(b_block(ps, pk, 0), S::B_BLOCK);
+              bulk_prefetch_l2(b_block(ps, pk, 1), S::B_BLOCK);
+            }
+          }
         }
-        const int tl = unit_tile(u), blk = u % p.nblk;
-        const int2 i01 = p.tile_i01[tl];
-        unsigned char* b = stage(s) + S::B_OFF;
-        mbar_arrive_expect_tx(&full_b[s], 2 * S::B_BLOCK);
-        bulk_load(b, Bg + ((size_t)i01.x * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BLOCK, S::B_BLOCK,
-                  &full_b[s]);
-        bulk_load(b + S::B_BLOCK, Bg + ((size_t)i01.y * p.nblk + blk) * blk_bytes + (size_t)kc * S::B_BLOCK,
-                  S::B_BLOCK, &full_b[s]);
+        advance();
+        err = __shfl_sync(0xffffffffu, err, 0);
+        if (err) break;
       }
     }
   } else if (warp == kMmaWarp) {
     // MMA issue
     if (lane == 0) {
       const uint32_t idesc = Op::idesc(S::N);
-      for (int g = 0; g < G && !err; ++g) {
-        const int s = g % kStages, r = g / kStages, u = g / p.KC, kc = g % p.KC;
-        const int a = u & 1;
-        if (kc == 0 && u >= 2 && !mbar_spin_bounded(&acc_empty[a], ((u - 2) >> 1) & 1, kWaitLimit)) err = 1;
-        if (!err && !mbar_spin_bounded(&full_b[s], r & 1, kWaitLimit)) err = 1;
-        if (!err && !mbar_spin_bounded(&full_a[s], r & 1, kWaitLimit)) err = 1;
-        if (err) break;
-        tc_fence_after_sync();
-        mma_chunk<Op, Db>(tm + (uint32_t)(a * S::ACC_COLS), idesc, stage(s), kc == 0);
-        umma_commit(&empty[s]);
-        if (kc == p.KC - 1) umma_commit(&acc_full[a]);
+      int g = 0;
+      for (int j = 0; j < nseg && !err; ++j) {
+        const Seg sg = W.seg(p, j);
+        const int a = j & 1;
+        for (int kc = sg.k0; kc < sg.k1; ++kc, ++g) {
+          const int s = g % kStages, r = g / kStages;
+          if (kc == sg.k0 && j >= 2 && !mbar_spin_bounded(&acc_empty[a], ((j - 2) >> 1) & 1, kWaitLimit)) err = 1;
+          if (!err && !mbar_spin_bounded(&full_b[s], r & 1, kWaitLimit)) err = 1;
+          if (!err && !mbar_spin_bounded(&full_a[s], r & 1, kWaitLimit)) err = 1;
+          if (err) break;
+          tc_fence_after_sync();
+          mma_chunk<Op, Db>(tm + (uint32_t)(a * S::ACC_COLS), idesc, stage(s), kc == sg.k0);
+          umma_commit(&empty[s]);
+          if (kc == sg.k1 - 1) umma_commit(&acc_full[a]);
+        }
       }
     }
-  } else {
-    // builders: A stages, then the epilogue of the previous unit
-    const int t = tid;
-    const In* Ph = static_cast<const In*>(p.Phat);
-    auto epilogue = [&](int u) {
-      const int a = u & 1, tl = unit_tile(u), blk = u % p.nblk;
-      if (!mbar_spin_bounded(&acc_full[a], (u >> 1) & 1, kWaitLimit)) err = 1;
-      tc_fence_after_sync();
-      // warps w and w + 4 own the rows of lane quarter w % 4 and split the depths
-      const int row = t & (kUmmaTile - 1), half = t >> 7;
-      const int pix = p.tile_pix[(size_t)tl * kUmmaTile + row];
-      const float ac = p.tile_acut[(size_t)tl * kUmmaTile + row];
-      Out* crow = static_cast<Out*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
-      const uint32_t acc = tm + (uint32_t)(a * S::ACC_COLS);
-      if (!err) {
-        if (Db >= 32) epilogue_cols<Op, Db>(acc, warp, pix, p.scale * ac, crow, blk, p.D, half * (Db / 2), Db / 2);
-        else if (half == 0) epilogue_cols<Op, Db>(acc, warp, pix, p.scale * ac, crow, blk, p.D, 0, Db);
+  } else if (warp >= kEpiWarp0) {
+    // epilogue: warp w reads TMEM lane quarter w % 4 (thread = tile row) and
+    // writes every depth of its row; runs beside the next segment's MMAs
+    const int row = 32 * (warp & 3) + lane;
+    for (int j = 0; j < nseg; ++j) {
+      const Seg sg = W.seg(p, j);
+      const int a = j & 1;
+      if (!mbar_spin_bounded(&acc_full[a], (j >> 1) & 1, kWaitLimit)) {
+        err = 1;
+        break;
       }
+      tc_fence_after_sync();
+      const int pix = p.tile_pix[(size_t)sg.tile * kUmmaTile + row];
+      const float ac = p.tile_acut[(size_t)sg.tile * kUmmaTile + row];
+      Out* crow = static_cast<Out*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)sg.blk * Db;
+      epilogue_cols<Op, Db>(tm + (uint32_t)(a * S::ACC_COLS), warp, pix, p.scale * ac, crow, sg.blk, p.D, 0, Db,
+                            sg.partial);
       tc_fence_before_sync();
       mbar_arrive(&acc_empty[a]);
-    };
-    // a builder touches kIters rows: their pixel and weight are held in
-    // registers per tile, and the next chunk's phasors are loaded before the
-    // current chunk is stored
+    }
+  } else {
+    // builders: A stages. A builder touches kIters rows: their pixel and
+    // weight are held in registers per segment, and the next chunk's phasors
+    // are loaded before the current chunk is stored
+    const int t = tid;
+    const In* Ph = static_cast<const In*>(p.Phat);
     int rp[A::kIters];
     float ra[A::kIters];
-    auto load_rows = [&](int u) {
-      const int tl = unit_tile(u);
+    auto load_rows = [&](int tl) {
 #pragma unroll
       for (int i = 0; i < A::kIters; ++i) {
         int r, q;
@@ -310,15 +413,16 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
       }
     };
     In hc[A::kIters], hn[A::kIters];
-    if (U > 0) {
-      load_rows(0);
-      load_h(hc, 0);
+    if (nseg > 0) {
+      const Seg s0 = W.seg(p, 0);
+      load_rows(s0.tile);
+      load_h(hc, s0.k0);
     }
-    for (int u = 0; u < U && !err; ++u) {
-      for (int kc = 0; kc < p.KC; ++kc) {
-        const int g = u * p.KC + kc;
+    int g = 0;
+    for (int j = 0; j < nseg && !err; ++j) {
+      const Seg sg = W.seg(p, j);
+      for (int kc = sg.k0; kc < sg.k1; ++kc, ++g) {
         const int s = g % kStages, r = g / kStages;
-        const bool next_unit = kc + 1 == p.KC;
         if (r >= 1 && !mbar_spin_bounded(&empty[s], (r - 1) & 1, kWaitLimit)) {
           err = 1;
           break;
@@ -331,23 +435,21 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         }
         fence_proxy_async_smem();
         mbar_arrive(&full_a[s]);
-        // next chunk (of this unit or the next one) in flight
-        if (!next_unit) {
+        // next chunk (of this segment or the next one) in flight
+        if (kc + 1 < sg.k1) {
           load_h(hn, kc + 1);
-        } else if (u + 1 < U) {
-          load_rows(u + 1);
-          load_h(hn, 0);
+        } else if (j + 1 < nseg) {
+          const Seg nx = W.seg(p, j + 1);
+          load_rows(nx.tile);
+          load_h(hn, nx.k0);
         }
 #pragma unroll
         for (int i = 0; i < A::kIters; ++i) hc[i] = hn[i];
       }
-      if (err) break;
-      if (u >= 1) epilogue(u - 1);
     }
-    if (U >= 1 && !err) epilogue(U - 1);
   }
   if (err && p.err) atomicExch(p.err, kDevErrTmaTimeout);
-  // on success every MMA has completed once the builders saw the last
+  // on success every MMA has completed once the epilogue warps saw the last
   // accumulator full; on a timeout the waits above have given up
   tc_fence_before_sync();
   __syncthreads();
@@ -474,11 +576,11 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
 template <class Op>
 __global__ void kr_store_umma_kernel(const double2* K64, unsigned char* B, int n_rho, int F, int D, int Db, int nblk,
                                      int KC, double scale) {
-  constexpr int kCols = kUmmaRowBytes / Op::kElem;
+  constexpr int kCols = Op::kRowBytes / Op::kElem;
   const long long N = 2LL * Db;
   const long long per_chunk = N * kCols;
   const long long total = (long long)n_rho * nblk * KC * per_chunk;
-  const size_t part_bytes = (size_t)N * kUmmaRowBytes;
+  const size_t part_bytes = (size_t)N * Op::kRowBytes;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     const long long chunk = i / per_chunk;
@@ -497,9 +599,9 @@ __global__ void kr_store_umma_kernel(const double2* K64, unsigned char* B, int n
       if (!im_row) v = c == 0 ? kv.x : -kv.y;
       else v = c == 0 ? kv.y : kv.x;
     }
-    // element (n, kj) of a 64-byte-row operand: core matrix (n / 8, byte column / 16)
+    // element (n, kj) of a kRowBytes-row operand: core matrix (n / 8, byte column / 16)
     const int bc = kj * Op::kElem;
-    const size_t off = ((size_t)(n >> 3) * (kUmmaRowBytes / 16) + (bc >> 4)) * 128 + (n & 7) * 16 + (bc & 15);
+    const size_t off = ((size_t)(n >> 3) * (Op::kRowBytes / 16) + (bc >> 4)) * 128 + (n & 7) * 16 + (bc & 15);
     unsigned char* base = B + (size_t)chunk * Op::kParts * part_bytes;
     if (Op::kKind == kUmmaF16) {
       *reinterpret_cast<__half*>(base + off) = __double2half(v * scale);
@@ -539,8 +641,19 @@ cudaError_t launch_ws(const PfUmmaParams& p, cudaStream_t s) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  const int grid = p.ntiles < sms ? p.ntiles : sms;   // one persistent CTA per SM
-  k<<<grid, kWsThreads, smem, s>>>(p);
+  // one persistent CTA per SM; the tail tiles' units are split along the
+  // frequency sum so that idle CTAs share them
+  PfUmmaParams q = p;
+  const int units = p.ntiles * p.nblk;
+  const int full = p.ntiles / sms;
+  const int tail_units = (p.ntiles - full * sms) * p.nblk;
+  int split = tail_units > 0 ? sms / tail_units : 1;
+  split = split < 1 ? 1 : split > kMaxSplit ? kMaxSplit : split;
+  if (split > p.KC) split = p.KC;
+  q.split = split;
+  const int grid = full > 0 ? sms : (units * split < sms ? units * split : sms);
+  if (full == 0 && grid != sms && p.ntiles / grid != 0) q.split = 1;   // every tile whole: no tail
+  k<<<grid, kWsThreads, smem, s>>>(q);
   return cudaGetLastError();
 }
 

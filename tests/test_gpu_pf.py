@@ -124,4 +124,6 @@ def test_pf_fp32_tensor_core_and_ffma_depth_sums(depths):
     for v in (0, 1, 2):
         assert rel_l2(out[v], ref) <= 1e-5, (v, rel_l2(out[v], ref))
         assert same_peak(out[v], ref)
-    assert rel_l2(out[2], out[0]) <= 1e-7      # same arithmetic, same order per tile
+    # same products; the persistent form adds the parts of split tail tiles
+    # with float32 atomics
+    assert rel_l2(out[2], out[0]) <= 1e-6

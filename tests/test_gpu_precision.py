@@ -111,4 +111,5 @@ def test_pf_fp16_tensor_core_and_ffma_depth_sums(depths):
         assert rel_l2(out[v], ref) <= 2e-3, (v, rel_l2(out[v], ref))
         assert same_peak(out[v], ref, rtol=2e-3)
     assert rel_l2(out[0], out[1]) <= 2e-3
-    assert rel_l2(out[2], out[0]) <= 1e-6      # same arithmetic, same order per tile
+    # the persistent form adds the parts of split tail tiles with f16 atomics
+    assert rel_l2(out[2], out[0]) <= 1e-3
