@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -357,6 +358,19 @@ def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000), seconds=2.0, b
     return {"budget_gb": budget_gb, "slots": 8, "shapes": len(specs), "sweep": results}
 
 
+_FFMA = []
+
+
+def ffma_peak():
+    """FP32 FMA peak in TFLOP/s measured on this GPU by the library's FMA-chain
+    probe (once per run), with the nominal figure as a note."""
+    from paper_2608_28183_gb300 import nlos
+    if not _FFMA:
+        _FFMA.append(nlos.ffma_rate())
+    nominal = 152 * 128 * 2 * 2.07e9 / 1e12
+    return _FFMA[0], f"measured FP32 FMA chains (nominal 152 SMs x 128 lanes x 2 flop x 2.07 GHz = {nominal:.1f})"
+
+
 def depth_sum_roofline(plan, g, F, D, ms, storage):
     """Roofline of the phasor-field depth sum in the form the plan runs: on the
     tensor cores, two real products (A0 B0^T + A1 B1^T) per pixel of the
@@ -372,10 +386,9 @@ def depth_sum_roofline(plan, g, F, D, ms, storage):
     npix = 4 * g.nx * g.ny
     if shape == 1:
         flops = npix * F * D * 12          # per (pixel, f, d): lerp 2 FMA + complex MAC 4 FMA
-        peak = 152 * 128 * 2 * 2.07e9 / 1e12
+        peak, note = ffma_peak()
         return {"bound": "alu", "form": "ffma", "flops": flops, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
-                "peak_tflops": peak, "frac": flops / (ms * 1e-3) / 1e12 / peak,
-                "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x 2.07 GHz max clock"}
+                "peak_tflops": peak, "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_note": note}
     peaks, _ = measured_peaks()
     bf16 = float(peaks.get("bf16_tflops", 0.0)) or 1900.0
     one = 2 * npix * (2 * F) * (2 * D) * 2
@@ -602,6 +615,39 @@ def moe_bench(torch, nlos, synth, reps=20):
             "two_streams_ms": _event_ms(torch, concurrent, reps)}
 
 
+def small_fk_bench(torch, nlos, synth, steps=400, with_oracle=True):
+    """The 32 x 32 x 256 f-k workload (1 m wall, 32 ps, padded 64 x 64 x 512):
+    its whole working set sits in L2, so it is reported as latency and
+    volumes/s (no roofline), next to the oracle on one host thread and on all
+    of them."""
+    import numpy as np
+    cap = synth.make_capture("fk_32x32x256", 0)
+    g = cap.geometry
+    plan = nlos.plan_for_capture(g, "fk", "f32")
+    plan.autotune()
+    x = torch.as_tensor(cap.counts, dtype=torch.float32).cuda()
+    v = plan.empty_volume()
+    for _ in range(10):
+        plan.reconstruct(x, v)
+    tot, st = time_plan(plan, x, v, steps, torch)
+    out = {"workload": "fk_32x32x256", "grid": [g.nx, g.ny, g.nt], "steps": steps,
+           "volumes_per_s": steps / (tot * 1e-3), "ms_per_volume": tot / steps,
+           "p50_ms": st[len(st) // 2], "p99_ms": st[min(len(st) - 1, int(0.99 * (len(st) - 1) + 0.5))]}
+    if with_oracle:
+        from oracle import fk
+        H = np.asarray(cap.counts, dtype=np.float32).astype(np.float64)
+        for workers, key in ((1, "oracle_1_thread"), (os.cpu_count(), "oracle_all_threads")):
+            fk.fk_reconstruct(H, g.bin_width_s, g.wall_w_m, g.wall_h_m, workers=workers)
+            t = time.perf_counter()
+            reps = 0
+            while reps < 3 or time.perf_counter() - t < 2.0:
+                R = fk.fk_reconstruct(H, g.bin_width_s, g.wall_w_m, g.wall_h_m, workers=workers)
+                reps += 1
+            out[key] = {"volumes_per_s": reps / (time.perf_counter() - t), "threads": workers}
+        out["rel_l2_vs_oracle"] = rel_l2(v.cpu().numpy(), R)
+    return out
+
+
 def cufft_reference(torch, g, reps=10):
     """cuFFT (through torch.fft) on the same padded volume, as a reference
     point only: one 3D complex forward and one inverse transform of
@@ -762,6 +808,17 @@ def main():
     pipe_bytes = pipeline_bytes(g.nx, g.ny, g.nt, args.storage)
     step_mean_ms = total_ms / K
     pipe_achieved = pipe_bytes / (step_mean_ms * 1e-3) / 1e9
+    # the Stolt stage against the FP32 FMA peak as well: per stored pencil
+    # (a + 1 of the 2a kx planes x 2b) one forward and two inverse length-2n
+    # transforms at 5 N log2 N flop (the interpolation is not counted)
+    stolt_alu = None
+    if "fk_stolt_z" in per_launch_ms:
+        Lt = 2 * g.nt
+        fl = (g.nx + 1) * 2 * g.ny * 3 * 5 * Lt * math.log2(Lt)
+        fpk, fnote = ffma_peak()
+        ach = fl / (per_launch_ms["fk_stolt_z"] * 1e-3) / 1e12
+        stolt_alu = {"kernel": "fk_stolt_z", "bound": "alu", "flops": fl, "flops_model": "3 x 5 N log2 N per stored pencil",
+                     "achieved_tflops": ach, "peak_tflops": fpk, "frac": ach / fpk, "peak_note": fnote}
 
     def pct(q, xs=None):
         xs = step_ms if xs is None else xs
@@ -787,6 +844,7 @@ def main():
     if world == 1 and not args.no_extras and not args.grid:
         for name, fn in (("batch", batch_bench), ("serving", serving_bench),
                          ("phasor_field", lambda t, n, sy: pf_bench(t, n, sy, with_oracle=not args.no_cpu_baseline)),
+                         ("fk_small", lambda t, n, sy: small_fk_bench(t, n, sy, with_oracle=not args.no_cpu_baseline)),
                          ("binning", binning_bench), ("post", post_bench), ("moe", moe_bench),
                          ("cufft_reference", lambda t, n, sy: cufft_reference(t, g))):
             try:
@@ -837,6 +895,8 @@ def main():
         "post": extras.get("post"),
         "moe": extras.get("moe"),
         "cufft_reference": extras.get("cufft_reference"),
+        "fk_small": extras.get("fk_small"),
+        "roofline_alu": stolt_alu,
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": Ke,
                 "h2d_bytes_per_step": plan.input_bytes, "d2h_bytes_per_step": plan.output_bytes,
                 "path": "nlos_reconstruct_host_many (copies in/out overlap reconstruction), pinned host buffers",

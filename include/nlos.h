@@ -423,6 +423,16 @@ nlos_status_t nlos_selftest_umma(int n_cols, float* out, int* code);
  * K = 32 as four K = 8 MMAs). */
 nlos_status_t nlos_selftest_umma_kind(int kind, int n_cols, float* out, int* code);
 
+/* FP32 FMA throughput probe (the denominator of the rooflines of FMA-bound
+ * kernels): launches `blocks` CTAs of 256 threads on `stream`, each thread
+ * running 8 independent chains of x <- x * params[0] + params[1] (starting
+ * near params[2]) for 16 * iters steps. params: device, 3 floats; sink:
+ * device, blocks * 256 floats, written only in a case that cannot occur.
+ * *flops receives the flops the launch executes; the caller times it.
+ * Asynchronous; INVALID_ARG on NULL pointers or non-positive counts. */
+nlos_status_t nlos_ffma_rate_launch(const float* params, float* sink, int blocks, int iters, double* flops,
+                                    void* stream);
+
 /* Testing hook for the failure path (fault injection on the host): the k-th
  * device allocation that plan creation or host staging makes from now on
  * (k >= 1) fails as if the device were out of memory, and the call returns

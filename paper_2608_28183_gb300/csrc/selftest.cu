@@ -200,3 +200,42 @@ extern "C" nlos_status_t nlos_selftest_umma_kind(int kind, int n_cols, float* ou
   if (v) return set_error(NLOS_ERR_TIMEOUT, "tensor-core MMA did not complete within the wait limit");
   return NLOS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// FP32 FMA throughput: every thread runs 8 independent chains of
+// x <- x * b + c, 16 steps per chain per iteration. The chains' sum is written
+// only if it equals a value it cannot reach, so nothing is stored but the
+// compiler keeps every FMA. The host times the launch with events; the
+// measured rate is the denominator of the rooflines of FMA-bound kernels.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void __launch_bounds__(256) ffma_rate_kernel(const float* in, float* out, int iters) {
+  const float b = in[0], c = in[1];
+  float x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = in[2] + 1e-3f * (float)(threadIdx.x + k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], b, c);
+    }
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == -1.2345e30f) out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+}  // namespace
+
+extern "C" nlos_status_t nlos_ffma_rate_launch(const float* params, float* sink, int blocks, int iters,
+                                               double* flops, void* stream) {
+  using namespace nlos;
+  if (!params || !sink || !flops || blocks <= 0 || iters <= 0)
+    return set_error(NLOS_ERR_INVALID_ARG, "params/sink/flops non-NULL; blocks and iters > 0");
+  ffma_rate_kernel<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(params, sink, iters);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(NLOS_ERR_CUDA, cudaGetErrorString(e));
+  *flops = 2.0 * 8 * 16 * (double)iters * blocks * 256;
+  return NLOS_OK;
+}

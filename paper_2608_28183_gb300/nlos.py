@@ -32,7 +32,7 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
             "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
             "nlos_reconstruct_host_many", "nlos_debug_fail_allocation", "nlos_selftest_umma",
-            "nlos_selftest_umma_kind"]
+            "nlos_selftest_umma_kind", "nlos_ffma_rate_launch"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -118,6 +118,8 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_selftest_umma.restype = ctypes.c_int
     lib.nlos_selftest_umma_kind.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
     lib.nlos_selftest_umma_kind.restype = ctypes.c_int
+    lib.nlos_ffma_rate_launch.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
+    lib.nlos_ffma_rate_launch.restype = ctypes.c_int
     for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda", "nlos_bin_transient",
                  "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors", "nlos_reconstruct_host_many"):
         getattr(lib, name).restype = ctypes.c_int
@@ -570,3 +572,25 @@ def bin_transient(pixel, ticks, nx: int, ny: int, nt: int, t0_ticks: int, ticks_
                                    pixel.numel(), nx, ny, nt, t0_ticks, ticks_per_bin, int(bool(accumulate)),
                                    ctypes.c_void_p(transient.data_ptr()), _stream_ptr(stream)))
     return transient
+
+
+def ffma_rate(blocks: int = 152 * 8, iters: int = 2048, repeats: int = 5, stream=None) -> float:
+    """Measured FP32 FMA throughput in TFLOP/s: best of `repeats` launches of
+    the library's FMA-chain probe, timed with CUDA events on `stream`."""
+    torch = _torch()
+    load_library()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    params = torch.tensor([0.9999, 1e-4, 1.0], dtype=torch.float32, device="cuda")
+    sink = torch.empty(blocks * 256, dtype=torch.float32, device="cuda")
+    flops = ctypes.c_double(0.0)
+    best = 0.0
+    for _ in range(repeats + 1):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(s)
+        _check(_lib.nlos_ffma_rate_launch(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(sink.data_ptr()),
+                                          blocks, iters, ctypes.byref(flops), ctypes.c_void_p(s.cuda_stream)))
+        t1.record(s)
+        t1.synchronize()
+        best = max(best, flops.value / (t0.elapsed_time(t1) * 1e-3) / 1e12)
+    return best

@@ -45,3 +45,11 @@ def test_umma_tf32_product_is_exact(lib, n_cols):
     st = lib.nlos_selftest_umma_kind(1, n_cols, ctypes.c_void_p(out.data_ptr()), ctypes.byref(code))
     assert st == 0 and code.value == 0, lib.nlos_last_error()
     np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), A @ B.T)
+
+
+def test_ffma_rate_is_plausible(lib):
+    """The FMA-chain probe runs and reports a rate between a tenth of and the
+    nominal FP32 FMA peak of 152 SMs x 128 lanes x 2 flop x 2.07 GHz."""
+    from paper_2608_28183_gb300 import nlos
+    rate = nlos.ffma_rate(blocks=152 * 4, iters=256, repeats=2)
+    assert 0.1 * 80.5 < rate < 1.02 * 80.5, rate
