@@ -374,11 +374,10 @@ def ffma_peak():
 def depth_sum_roofline(plan, g, F, D, ms, storage):
     """Roofline of the phasor-field depth sum in the form the plan runs: on the
     tensor cores, two real products (A0 B0^T + A1 B1^T) per pixel of the
-    padded grid with K = 2F and N = 2D - once in f16 for 16-bit plans, three
-    times in tf32 (hi*hi + hi*lo + lo*hi) for float32 plans - against the
-    measured dense bf16 peak (f16) or that peak x 1.1/2.25, the nominal
-    tf32/bf16 ratio (tf32); on FP32 FMAs against 152 SMs x 128 lanes x 2 flop
-    x 2.07 GHz."""
+    padded grid with K = 2F and N = 2D in kind::f16 MMAs - once for 16-bit
+    plans, three times (products of f16 hi/lo parts) for float32 plans -
+    against the measured dense bf16 peak (f16 runs at the same rate); on FP32
+    FMAs against the measured FMA peak."""
     from paper_2608_28183_gb300 import nlos
     lib = nlos.load_library()
     names = [lib.nlos_plan_stage_name(plan.handle, i).decode() for i in range(len(plan.tiles))]
@@ -390,16 +389,14 @@ def depth_sum_roofline(plan, g, F, D, ms, storage):
         return {"bound": "alu", "form": "ffma", "flops": flops, "achieved_tflops": flops / (ms * 1e-3) / 1e12,
                 "peak_tflops": peak, "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_note": note}
     peaks, _ = measured_peaks()
-    bf16 = float(peaks.get("bf16_tflops", 0.0)) or 1900.0
+    peak = float(peaks.get("bf16_tflops", 0.0)) or 1900.0
     one = 2 * npix * (2 * F) * (2 * D) * 2
-    if storage == "f32":
-        flops, peak, note = 3 * one, bf16 * 1.1 / 2.25, "measured dense bf16 x 1.1/2.25 (nominal tf32/bf16)"
-    else:
-        flops, peak, note = one, bf16, "measured dense bf16 (f16 runs at the same rate)"
-    return {"bound": "tensor", "form": "tf32x3" if storage == "f32" else "f16",
+    flops = 3 * one if storage == "f32" else one
+    return {"bound": "tensor", "form": "f16x3" if storage == "f32" else "f16",
             "schedule": "persistent" if shape == 0 else "cta_per_tile", "flops": flops, "algorithmic_flops": one,
             "achieved_tflops": flops / (ms * 1e-3) / 1e12, "peak_tflops": peak,
-            "frac": flops / (ms * 1e-3) / 1e12 / peak, "peak_note": note}
+            "frac": flops / (ms * 1e-3) / 1e12 / peak,
+            "peak_note": "measured dense bf16 (f16 runs at the same rate)"}
 
 
 def pf_bench(torch, nlos, synth, steps=200, with_oracle=True):

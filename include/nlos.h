@@ -419,9 +419,6 @@ nlos_status_t nlos_dda(const float* const* frames, int nw, long long nxy, int nz
  * *code receives the device error word (non-zero: the MMA completion wait
  * gave up, NLOS_ERR_TIMEOUT). Synchronous. n_cols: multiple of 16 in [16, 256]. */
 nlos_status_t nlos_selftest_umma(int n_cols, float* out, int* code);
-/* The same check for kind 0 (f16 operands, K = 64) or kind 1 (tf32 operands,
- * K = 32 as four K = 8 MMAs). */
-nlos_status_t nlos_selftest_umma_kind(int kind, int n_cols, float* out, int* code);
 
 /* FP32 FMA throughput probe (the denominator of the rooflines of FMA-bound
  * kernels): launches `blocks` CTAs of 256 threads on `stream`, each thread

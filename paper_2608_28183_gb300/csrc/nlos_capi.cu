@@ -68,6 +68,7 @@ constexpr float kVolumeTarget = 4096.0f;   // ||scaled input||_2 for reduced-pre
 constexpr int kScalePartials = 2048;
 constexpr int kBatchStreams = 8;
 constexpr size_t kErrOffset = 64;    // device error word inside the workspace's scalar area
+constexpr size_t kAmaxOffset = 128;  // max |component| of the compact phasors (f16x3 depth sum)
 
 thread_local std::string g_err;
 
@@ -151,6 +152,7 @@ struct nlos_plan_s {
   float* ch_alpha = nullptr;
   float* ch_acut = nullptr;
   double kr_scale = 1.0;
+  double bu_scale = 1.0;          // power-of-two scale of the tensor-core B operands
   // workspace layout: up to three complex buffers + scale scalars + partials
   size_t off[3] = {0, 0, 0};
   size_t off_scal = 0, off_part = 0;
@@ -398,8 +400,11 @@ nlos_status_t build_pf(nlos_plan_s* p) {
   }
   if (e == cudaSuccess && st == NLOS_OK && (p->storage == kF16 || p->storage == kF32)) {
     // the same kernel as tensor-core B operands: [Kr -Ki; Ki Kr] per bin and
-    // depth block, f16 for 16-bit plans, tf32 (hi, lo) parts for float32 plans
-    p->kind_u = p->storage == kF16 ? kUmmaF16 : kUmmaTf32x3;
+    // depth block, f16 for 16-bit plans, f16 (hi, lo) parts for float32 plans;
+    // both scaled into f16 range by a power of two
+    p->kind_u = p->storage == kF16 ? kUmmaF16 : kUmmaF16x3;
+    p->bu_scale = p->storage == kF16 ? p->kr_scale
+                                     : ldexp(1.0, (int)floor(log2(16384.0 / (kPi * r_max * r_max))));
     const int cols = umma_chunk_cols(p->kind_u);
     p->Db_u = p->D <= 16 ? 16 : p->D <= 32 ? 32 : p->D <= 64 ? 64 : 128;
     p->nblk_u = (p->D + p->Db_u - 1) / p->Db_u;
@@ -409,7 +414,7 @@ nlos_status_t build_pf(nlos_plan_s* p) {
     st = dalloc(p, &p->Bu, bbytes, "tensor-core kernel operands");
     if (st == NLOS_OK)
       e = launch_kr_store_umma(dK64, p->Bu, p->kind_u, n_rho, p->F, p->D, p->Db_u, p->nblk_u, p->KC_u,
-                               p->kr_scale, 0);
+                               p->bu_scale, 0);
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   free_tmp();
@@ -772,7 +777,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     NLOS_CU(launch_pf_dense(dp, s), "pf dense depth sum");
   } else {
     // PF3: depth sum (pixels beyond the cutoff stay zero); f16 and float32
-    // plans run it on the tensor cores (f16 operands / three tf32 products)
+    // plans run it on the tensor cores (f16 operands / three products of f16 parts)
     // unless the stage's launch shape asks for the FFMA form
     NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * Nu * Nv * D, s), "pf clear");
     if (p->Bu && p->tiles[sid] != 1) {
@@ -791,7 +796,18 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
       up.nblk = p->nblk_u;
       up.KC = p->KC_u;
       up.kind = p->kind_u;
-      up.scale = c3;
+      up.scale = p->kind_u == kUmmaF16 ? c3 : (float)(c3_data / p->bu_scale);
+      if (p->kind_u == kUmmaF16x3) {
+        // bound on |Phat|: the 2D transforms sum a x b phasors of modulus
+        // <= sqrt(2) max|component| (times the passes' scales)
+        unsigned* amax = reinterpret_cast<unsigned*>(ws + p->off_scal + kAmaxOffset);
+        NLOS_CU(cudaMemsetAsync(amax, 0, sizeof(unsigned), s), "phasor bound clear");
+        NLOS_CU(launch_absmax(static_cast<const float*>(P), 2 * a * b * F, amax, s), "phasor bound");
+        int e2 = 0;
+        frexp(1.5 * (double)a * b * g2a * g2b, &e2);
+        up.amax = amax;
+        up.abound_exp = e2;
+      }
       up.err = err;
       // launch shape 0: persistent warp-specialised schedule; 2: one CTA per tile
       NLOS_CU(launch_pf_umma(up, p->tiles[sid] != 2, s), "pf depth sum (tensor cores)");

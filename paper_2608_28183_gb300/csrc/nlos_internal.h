@@ -165,21 +165,22 @@ cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int st
 // Im Phat], A1 = alpha [Re Phat | Im Phat] (built in shared memory) and B(i)
 // the real form of K_r[i] ([Kr -Ki; Ki Kr], 2 Db output columns per depth
 // block, stored per plan in the operand layout); C = scale * acut * (Y_re +
-// i Y_im). Two operand kinds:
-//  * kUmmaF16 (16-bit storage): f16 operands, kind::f16 MMAs, one product;
-//  * kUmmaTf32x3 (float32 storage): every operand x split into tf32 parts
-//    x_hi = tf32(x), x_lo = tf32(x - x_hi), and A B^T taken as
-//    A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (kind::tf32 MMAs; the dropped
-//    A_lo B_lo^T term is ~2^-22 of the product), fp32 accumulation.
-// Operand rows per chunk: 64 bytes - 32 f16 columns (16 frequencies) or 16
-// tf32 columns (8 frequencies).
+// i Y_im). Two operand kinds, both kind::f16 MMAs:
+//  * kUmmaF16 (16-bit storage): f16 operands, one product;
+//  * kUmmaF16x3 (float32 storage): every operand x split into f16 parts
+//    x_hi = f16(x), x_lo = f16(x - x_hi), and A B^T taken as
+//    A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the dropped A_lo B_lo^T term is
+//    ~2^-22 of the product), fp32 accumulation. A is scaled into f16 range by
+//    a power of two derived from a bound on |Phat| (amax, abound_exp below),
+//    B by the plan's power-of-two scale; the epilogue removes both.
+// Operand rows per chunk: 64 bytes - 32 f16 columns (16 frequencies).
 constexpr int kUmmaTile = 128;           // pixels per tile (MMA M)
-enum UmmaKind { kUmmaF16 = 0, kUmmaTf32x3 = 1 };
+enum UmmaKind { kUmmaF16 = 0, kUmmaF16x3 = 1 };
 __host__ __device__ constexpr int umma_row_bytes(int) { return 64; }
-__host__ __device__ constexpr int umma_chunk_cols(int kind) { return kind == kUmmaF16 ? 32 : 16; }
+__host__ __device__ constexpr int umma_chunk_cols(int) { return 32; }
 __host__ __device__ constexpr int umma_parts(int kind) { return kind == kUmmaF16 ? 1 : 2; }
 struct PfUmmaParams {
-  const void* Phat;            // [npix][F] half2 (f16 kind) or float2 (tf32 kind)
+  const void* Phat;            // [npix][F] half2 (f16 kind) or float2 (f16x3 kind)
   const void* B;               // [n_rho][nblk][KC][parts][2 Db rows x row bytes], operand layout
   void* C;                     // [npix][D] half2 or float2
   const int2* tile_i01;        // [ntiles]
@@ -189,11 +190,19 @@ struct PfUmmaParams {
   int ntiles, F, D, Db, nblk, KC;
   int kind;                    // UmmaKind
   int split;                   // set by the launcher: parts of a tail unit's frequency sum
+  // kUmmaF16x3 only: *amax (float bits) bounds |Re|, |Im| of the compact
+  // phasors and every |Phat| component is below *amax * 2^abound_exp; A is
+  // scaled by 2^(15 - e(*amax) - abound_exp) with *amax < 2^e(*amax)
+  const unsigned* amax;
+  int abound_exp;
   float scale;
   int* err;                    // device error word (bounded waits)
 };
 // pipelined: persistent warp-specialised CTAs (one per SM) instead of one CTA per tile
 cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s);
+// max |x| over `count` floats into *out (float bits, atomicMax; *out must be
+// cleared beforehand)
+cudaError_t launch_absmax(const float* x, long long count, unsigned* out, cudaStream_t s);
 // K_r (float64 [n_rho][F][D]) -> B operand blocks of the given kind, scaled
 cudaError_t launch_kr_store_umma(const double2* K64, void* B, int kind, int n_rho, int F, int D, int Db, int nblk,
                                  int KC, double scale, cudaStream_t s);

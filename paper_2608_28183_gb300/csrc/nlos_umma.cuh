@@ -63,12 +63,6 @@ __host__ __device__ constexpr uint32_t umma_idesc_f16(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);               // M / 16
 }
 
-// Instruction descriptor of a kind::tf32 MMA: fp32 accumulator, tf32 A and B
-// (32-bit containers), both K-major, shape M x N (x 8).
-__host__ __device__ constexpr uint32_t umma_idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
 // ---- MMA ------------------------------------------------------------------------
 // D[tmem] (+)= A[smem] * B[smem]^T for one K = 16 slab; issued by one thread.
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
@@ -81,27 +75,6 @@ __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint6
       "}\n" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
-}
-
-// D[tmem] (+)= A[smem] * B[smem]^T for one K = 8 slab of tf32 operands
-__device__ __forceinline__ void umma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n"
-      " .reg .pred p;\n"
-      " setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
-      "}\n" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// float rounded to the nearest tf32 value (10 mantissa bits), kept in a
-// 32-bit container: the tensor core then reads it without further loss
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
 }
 
 // arrive on an mbarrier once every MMA this thread issued before has completed
@@ -165,10 +138,6 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src, uint32_t bytes
 // SBO = kcols / 8 * 128 bytes
 __host__ __device__ constexpr uint32_t umma_kmajor_offset(int r, int k, int kcols) {
   return (uint32_t)(((r >> 3) * (kcols >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
-}
-// the same for 32-bit elements: core matrix (r / 8, k / 4), SBO = kcols / 4 * 128
-__host__ __device__ constexpr uint32_t umma_kmajor_offset32(int r, int k, int kcols) {
-  return (uint32_t)(((r >> 3) * (kcols >> 2) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
 }
 
 }  // namespace nlos

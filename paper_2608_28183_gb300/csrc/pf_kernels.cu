@@ -452,6 +452,34 @@ __global__ void __launch_bounds__(128) pf_dense_kernel(const PfDenseParams p) {
   }
 }
 
+// max |x| of a float array: grid-stride 16-byte loads when the array is
+// 16-byte aligned (a scalar tail covers the rest), warp maximum, one atomicMax
+// of the float bits per warp (bits of non-negative floats order like the values)
+__global__ void absmax_kernel(const float* x, long long count, bool aligned, unsigned* out) {
+  float m = 0.f;
+  const long long n4 = aligned ? count / 4 : 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const float4* x4 = reinterpret_cast<const float4*>(x);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 v = x4[i];
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+  for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += stride)
+    m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+cudaError_t launch_absmax(const float* x, long long count, unsigned* out, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  const long long blocks = (count / 4 + 255) / 256;
+  const bool aligned = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  absmax_kernel<<<(unsigned)(blocks < 152 * 4 ? (blocks < 1 ? 1 : blocks) : 152 * 4), 256, 0, s>>>(x, count, aligned,
+                                                                                                   out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pf_dense(const PfDenseParams& p, cudaStream_t s) {
   if (p.npix <= 0 || p.F <= 0 || p.D <= 0) return cudaErrorInvalidValue;
   const int threads = p.D <= 64 ? 64 : 128;

@@ -15,14 +15,16 @@
 // accumulate in tensor memory; warps read the accumulator back (warp w owns
 // rows 32 (w % 4) .. + 31) to apply the taper and scale.
 //
-// Operand kinds (both stage 64-byte operand rows per chunk):
-//  * OpF16 (16-bit storage): f16 A and B, kind::f16 MMAs (K = 16), 32 columns
-//    (16 frequencies) per chunk;
-//  * OpTf32x3 (float32 storage): A and B split into tf32 parts hi = tf32(x),
-//    lo = tf32(x - hi); each product is A_hi B_hi^T + A_hi B_lo^T +
-//    A_lo B_hi^T in kind::tf32 MMAs (K = 8), 16 columns (8 frequencies) per
-//    chunk. The parts carry 22 significant bits of every operand, so the sum
-//    keeps float32 accuracy at three tf32 products per term.
+// Operand kinds (both stage 64-byte operand rows per chunk: 32 f16 columns,
+// 16 frequencies; kind::f16 MMAs, K = 16):
+//  * OpF16 (16-bit storage): f16 A and B, one product;
+//  * OpF16x3 (float32 storage): A and B split into f16 parts hi = f16(x),
+//    lo = f16(x - hi), each product taken as A_hi B_hi^T + A_hi B_lo^T +
+//    A_lo B_hi^T. The parts carry 22 significant bits of every operand, so
+//    the sum keeps float32 accuracy (the dropped A_lo B_lo^T is ~2^-22 of
+//    it) at three f16 products per term. A is scaled into f16 range per
+//    volume by a power of two from a bound on |Phat|, B per plan; the
+//    epilogue removes both.
 //
 // Two schedules:
 //  * pf_umma_ws_kernel: one persistent CTA per SM, warp-specialised - a
@@ -61,8 +63,9 @@ struct OpF16 {
   using In = __half2;    // phasor element
   using Out = __half2;   // depth-sum element
   static constexpr int kKind = kUmmaF16, kElem = 2, kParts = 1, kSlab = 16;
+  static constexpr bool kScaled = false;     // A scaled per volume by a bound on |Phat|
   // L2 prefetch of B blocks ahead of their copies: it shortens the copies of
-  // the two-stage tf32 ring; the four-stage f16 ring does not gain from it
+  // the two-stage f16x3 ring; the four-stage f16 ring does not gain from it
   static constexpr bool kPrefetchB = false;
   static constexpr uint32_t kRowBytes = 64;                 // bytes of an operand row per chunk
   static constexpr uint32_t kSbo = (kRowBytes / 16) * 128;  // row-group stride of a chunk operand
@@ -81,10 +84,11 @@ struct OpF16 {
   __device__ static __forceinline__ Out out(float x, float y) { return __floats2half2_rn(x, y); }
 };
 
-struct OpTf32x3 {
+struct OpF16x3 {
   using In = float2;
   using Out = float2;
-  static constexpr int kKind = kUmmaTf32x3, kElem = 4, kParts = 2, kSlab = 8;
+  static constexpr int kKind = kUmmaF16x3, kElem = 2, kParts = 2, kSlab = 16;
+  static constexpr bool kScaled = true;
   static constexpr bool kPrefetchB = true;
   static constexpr uint32_t kRowBytes = 64;
   static constexpr uint32_t kSbo = (kRowBytes / 16) * 128;
@@ -92,24 +96,43 @@ struct OpTf32x3 {
   static constexpr int kQ = kRowBytes / (2 * kElem);
   __device__ static __forceinline__ float2 load(In v) { return v; }
   __device__ static __forceinline__ In zero() { return make_float2(0.f, 0.f); }
+  // x, y already scaled into f16 range: hi = f16(x), lo = f16(x - hi)
   __device__ static __forceinline__ void put(unsigned char* a, uint32_t off, float x, float y) {
-    const float hx = to_tf32(x), hy = to_tf32(y);
-    *reinterpret_cast<float2*>(a + off) = make_float2(hx, hy);
-    *reinterpret_cast<float2*>(a + kABytes + off) = make_float2(to_tf32(x - hx), to_tf32(y - hy));
+    const __half2 hi = __floats2half2_rn(x, y);
+    const float2 h = __half22float2(hi);
+    *reinterpret_cast<__half2*>(a + off) = hi;
+    *reinterpret_cast<__half2*>(a + kABytes + off) = __floats2half2_rn(x - h.x, y - h.y);
   }
-  __device__ static __forceinline__ uint32_t idesc(int N) { return umma_idesc_tf32(kUmmaTile, N); }
+  __device__ static __forceinline__ uint32_t idesc(int N) { return umma_idesc_f16<false>(kUmmaTile, N); }
   __device__ static __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    umma_tf32(d, a, b, id, acc);
+    umma_f16(d, a, b, id, acc);
   }
   __device__ static __forceinline__ Out out(float x, float y) { return make_float2(x, y); }
 };
 
+// Scale of the A operand of a scaled kind: 2^(15 - e(amax) - abound_exp)
+// keeps |A| < 2^15 (f16 holds 65504); 1 when the phasors are all zero. sa
+// and its inverse are exact powers of two.
+template <class Op>
+__device__ __forceinline__ void a_scale(const PfUmmaParams& p, float& sa, float& inv_sa) {
+  sa = inv_sa = 1.f;
+  if (!Op::kScaled) return;
+  const float m = __uint_as_float(*p.amax);
+  if (!(m > 0.f)) return;
+  int e;
+  frexpf(m, &e);                                  // m < 2^e
+  int k = 15 - e - p.abound_exp;
+  k = k < -120 ? -120 : k > 120 ? 120 : k;
+  sa = ldexpf(1.f, k);
+  inv_sa = ldexpf(1.f, -k);
+}
+
 static_assert(OpF16::kRowBytes == umma_row_bytes(kUmmaF16) &&
                   OpF16::kRowBytes / OpF16::kElem == umma_chunk_cols(kUmmaF16),
               "f16 chunk geometry");
-static_assert(OpTf32x3::kRowBytes == umma_row_bytes(kUmmaTf32x3) &&
-                  OpTf32x3::kRowBytes / OpTf32x3::kElem == umma_chunk_cols(kUmmaTf32x3),
-              "tf32 chunk geometry");
+static_assert(OpF16x3::kRowBytes == umma_row_bytes(kUmmaF16x3) &&
+                  OpF16x3::kRowBytes / OpF16x3::kElem == umma_chunk_cols(kUmmaF16x3),
+              "f16x3 chunk geometry");
 
 // Stage layout: A(w, part) for weights w = 0 (1 - alpha), 1 (alpha), then
 // B(bin, part) for bins i0, i1; the parts of one B block are contiguous in the
@@ -128,8 +151,7 @@ struct Sizes {
 
 // A chunk of a tile: frequency q of row r for thread t and iteration i. A
 // warp instruction covers 8 rows x 4 consecutive q: the 32 lanes hit 32
-// distinct shared-memory banks (f16) or two conflict-free 128-byte wavefronts
-// (tf32) and read 8 runs of 4 consecutive phasors. NT threads (a multiple of
+// distinct shared-memory banks and read 8 runs of 4 consecutive phasors. NT threads (a multiple of
 // 32) share the chunk.
 template <class Op, int NT>
 struct AChunk {
@@ -141,12 +163,12 @@ struct AChunk {
     r = (T / (Op::kQ / 4)) * 8 + (t & 7);
     q = (T % (Op::kQ / 4)) * 4 + ((t & 31) >> 3);
   }
-  // value v of row r with weight alpha into both A operands
-  __device__ static __forceinline__ void put(unsigned char* stage, int r, int q, float2 v, float alpha) {
+  // value v of row r with weights (1 - alpha) sa, alpha sa into both A operands
+  __device__ static __forceinline__ void put(unsigned char* stage, int r, int q, float2 v, float alpha, float sa) {
     const uint32_t off = chunk_offset<Op>(r, q);
-    const float w0 = 1.f - alpha;
+    const float w0 = (1.f - alpha) * sa, w1 = alpha * sa;
     Op::put(stage, off, w0 * v.x, w0 * v.y);
-    Op::put(stage + Op::kParts * Op::kABytes, off, alpha * v.x, alpha * v.y);
+    Op::put(stage + Op::kParts * Op::kABytes, off, w1 * v.x, w1 * v.y);
   }
 };
 
@@ -292,12 +314,14 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
   tc_fence_after_sync();
   const uint32_t tm = tbase;
   const WsWork W(p);
+  float sa, inv_sa;
+  a_scale<Op>(p, sa, inv_sa);
   const int nseg = W.nseg;
   int err = 0;
 
   if (warp == kProducerWarp) {
     // producer: lane 0 keeps B operand stages up to kStages chunks ahead of
-    // the MMAs and, for the tf32 kind (two stages of 96 KB), asks L2 for the
+    // the MMAs and, for the f16x3 kind (two stages of 96 KB), asks L2 for the
     // B blocks kPrefetch chunks ahead
     const size_t blk_bytes = (size_t)p.KC * S::B_BLOCK;
     const unsigned char* Bg = static_cast<const unsigned char*>(p.B);
@@ -381,7 +405,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
       const int pix = p.tile_pix[(size_t)sg.tile * kUmmaTile + row];
       const float ac = p.tile_acut[(size_t)sg.tile * kUmmaTile + row];
       Out* crow = static_cast<Out*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)sg.blk * Db;
-      epilogue_cols<Op, Db>(tm + (uint32_t)(a * S::ACC_COLS), warp, pix, p.scale * ac, crow, sg.blk, p.D, 0, Db,
+      epilogue_cols<Op, Db>(tm + (uint32_t)(a * S::ACC_COLS), warp, pix, p.scale * inv_sa * ac, crow, sg.blk, p.D, 0, Db,
                             sg.partial);
       tc_fence_before_sync();
       mbar_arrive(&acc_empty[a]);
@@ -431,7 +455,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         for (int i = 0; i < A::kIters; ++i) {
           int rr, q;
           A::coords(i, t, rr, q);
-          A::put(stage(s), rr, q, Op::load(hc[i]), ra[i]);
+          A::put(stage(s), rr, q, Op::load(hc[i]), ra[i], sa);
         }
         fence_proxy_async_smem();
         mbar_arrive(&full_a[s]);
@@ -505,6 +529,8 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
   };
   In hcur[A::kIters], hnext[A::kIters];
   load_h(hcur, 0);
+  float sa, inv_sa;
+  a_scale<Op>(p, sa, inv_sa);
   const uint32_t dt = tbase;
   const uint32_t idesc = Op::idesc(S::N);
   const size_t blk_bytes = (size_t)p.KC * S::B_BLOCK;
@@ -525,7 +551,7 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
       for (int i = 0; i < A::kIters; ++i) {
         int r, q;
         A::coords(i, tid, r, q);
-        A::put(um_sm, r, q, Op::load(hcur[i]), salpha[r]);
+        A::put(um_sm, r, q, Op::load(hcur[i]), salpha[r], sa);
       }
       // the next chunk's phasors are in flight while this chunk's MMAs run
       load_h(hnext, kc + 1 < p.KC ? kc + 1 : 0);
@@ -549,8 +575,8 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
     // epilogue: warps w and w + 4 share the rows of lane quarter w % 4
     tc_fence_after_sync();
     Out* crow = static_cast<Out*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)blk * Db;
-    if (Db >= 32) epilogue_cols<Op, Db>(dt, warp, pix, p.scale * ac, crow, blk, p.D, half * (Db / 2), Db / 2);
-    else if (half == 0) epilogue_cols<Op, Db>(dt, warp, pix, p.scale * ac, crow, blk, p.D, 0, Db);
+    if (Db >= 32) epilogue_cols<Op, Db>(dt, warp, pix, p.scale * inv_sa * ac, crow, blk, p.D, half * (Db / 2), Db / 2);
+    else if (half == 0) epilogue_cols<Op, Db>(dt, warp, pix, p.scale * inv_sa * ac, crow, blk, p.D, 0, Db);
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
@@ -571,8 +597,8 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
 // blk Db + n - Db otherwise), column k = 2 f + c (c = 0 multiplies Re Phat,
 // c = 1 Im Phat):
 //   Re row: (Kr, -Ki),  Im row: (Ki, Kr),  zero beyond F and beyond D.
-// f16 kind: one part, the scaled value; tf32 kind: parts hi = tf32(v),
-// lo = tf32(v - hi) of the float32 value v.
+// f16 kind: one part, the scaled value; f16x3 kind: parts hi = f16(v),
+// lo = f16(v - hi) of the scaled value.
 template <class Op>
 __global__ void kr_store_umma_kernel(const double2* K64, unsigned char* B, int n_rho, int F, int D, int Db, int nblk,
                                      int KC, double scale) {
@@ -606,10 +632,9 @@ __global__ void kr_store_umma_kernel(const double2* K64, unsigned char* B, int n
     if (Op::kKind == kUmmaF16) {
       *reinterpret_cast<__half*>(base + off) = __double2half(v * scale);
     } else {
-      const float x = (float)(v * scale);
-      const float hi = to_tf32(x);
-      *reinterpret_cast<float*>(base + off) = hi;
-      *reinterpret_cast<float*>(base + part_bytes + off) = to_tf32(x - hi);
+      const __half hi = __double2half(v * scale);
+      *reinterpret_cast<__half*>(base + off) = hi;
+      *reinterpret_cast<__half*>(base + part_bytes + off) = __double2half(v * scale - (double)__half2float(hi));
     }
   }
 }
@@ -673,7 +698,7 @@ cudaError_t launch_kind(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
 cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
   if (p.ntiles <= 0) return cudaSuccess;
   if (p.kind == kUmmaF16) return launch_kind<OpF16>(p, pipelined, s);
-  if (p.kind == kUmmaTf32x3) return launch_kind<OpTf32x3>(p, pipelined, s);
+  if (p.kind == kUmmaF16x3) return launch_kind<OpF16x3>(p, pipelined, s);
   return cudaErrorInvalidValue;
 }
 
@@ -682,8 +707,8 @@ cudaError_t launch_kr_store_umma(const double2* K64, void* B, int kind, int n_rh
   unsigned char* b = static_cast<unsigned char*>(B);
   if (kind == kUmmaF16)
     kr_store_umma_kernel<OpF16><<<152 * 8, 256, 0, s>>>(K64, b, n_rho, F, D, Db, nblk, KC, scale);
-  else if (kind == kUmmaTf32x3)
-    kr_store_umma_kernel<OpTf32x3><<<152 * 8, 256, 0, s>>>(K64, b, n_rho, F, D, Db, nblk, KC, scale);
+  else if (kind == kUmmaF16x3)
+    kr_store_umma_kernel<OpF16x3><<<152 * 8, 256, 0, s>>>(K64, b, n_rho, F, D, Db, nblk, KC, scale);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

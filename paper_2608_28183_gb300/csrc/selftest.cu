@@ -56,59 +56,6 @@ constexpr int kUmmaM = 128, kUmmaK = 64;
 __device__ __forceinline__ float umma_probe_a(int r, int k) { return (float)((r * 3 + k * 5) % 7 - 3); }
 __device__ __forceinline__ float umma_probe_b(int n, int k) { return (float)((n * 2 + k * 7) % 5 - 2); }
 
-// kind::tf32 variant: K = 32 as 4 slabs of 8, operands in 32-bit containers
-__global__ void __launch_bounds__(128) umma_probe_tf32_kernel(int N, float* out, int* err) {
-  using namespace nlos;
-  extern __shared__ __align__(128) unsigned char ut_sm[];
-  __shared__ uint64_t bar;
-  __shared__ uint32_t tbase;
-  constexpr int K = 32;
-  unsigned char* A = ut_sm;
-  unsigned char* B = ut_sm + kUmmaM * K * 4;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  for (int i = tid; i < kUmmaM * K; i += blockDim.x) {
-    const int r = i / K, k = i % K;
-    *reinterpret_cast<float*>(A + umma_kmajor_offset32(r, k, K)) = umma_probe_a(r, k);
-  }
-  for (int i = tid; i < N * K; i += blockDim.x) {
-    const int n = i / K, k = i % K;
-    *reinterpret_cast<float*>(B + umma_kmajor_offset32(n, k, K)) = umma_probe_b(n, k);
-  }
-  fence_proxy_async_smem();
-  if (warp == 0) tmem_alloc(&tbase, 256);
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    mbar_fence_init();
-  }
-  tc_fence_before_sync();
-  __syncthreads();
-  tc_fence_after_sync();
-  const uint32_t d = tbase;
-  if (tid == 0) {
-    const uint32_t idesc = umma_idesc_tf32(kUmmaM, N);
-    for (int kk = 0; kk < K / 8; ++kk) {
-      const uint64_t ad = umma_smem_desc(smem_u32(A) + kk * 256, 128, (K / 4) * 128);
-      const uint64_t bd = umma_smem_desc(smem_u32(B) + kk * 256, 128, (K / 4) * 128);
-      umma_tf32(d, ad, bd, idesc, kk > 0);
-    }
-    umma_commit(&bar);
-  }
-  const bool ok = mbar_wait_bounded(&bar, 0, 1 << 20);
-  tc_fence_after_sync();
-  for (int c = 0; c < N; c += 16) {
-    uint32_t v[16];
-    tmem_ld16(d + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
-    tmem_wait_ld();
-    const int row = 32 * warp + lane;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) out[row * N + c + j] = __uint_as_float(v[j]);
-  }
-  tc_fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(d, 256);
-  if (!ok && tid == 0) atomicExch(err, nlos::kDevErrTmaTimeout);
-}
-
 __global__ void __launch_bounds__(128) umma_probe_kernel(int N, float* out, int* err) {
   using namespace nlos;
   extern __shared__ __align__(128) unsigned char ub_sm[];
@@ -161,35 +108,18 @@ __global__ void __launch_bounds__(128) umma_probe_kernel(int N, float* out, int*
 }
 }  // namespace
 
-extern "C" nlos_status_t nlos_selftest_umma_kind(int kind, int n_cols, float* out, int* code);
-
 extern "C" nlos_status_t nlos_selftest_umma(int n_cols, float* out, int* code) {
-  return nlos_selftest_umma_kind(0, n_cols, out, code);
-}
-
-extern "C" nlos_status_t nlos_selftest_umma_kind(int kind, int n_cols, float* out, int* code) {
   using namespace nlos;
-  if (!out || !code || n_cols < 16 || n_cols > 256 || n_cols % 16 || (kind != 0 && kind != 1))
-    return set_error(NLOS_ERR_INVALID_ARG,
-                     "kind 0 or 1; n_cols a multiple of 16 in [16, 256]; out/code non-NULL");
+  if (!out || !code || n_cols < 16 || n_cols > 256 || n_cols % 16)
+    return set_error(NLOS_ERR_INVALID_ARG, "n_cols must be a multiple of 16 in [16, 256]; out/code non-NULL");
   int* d = nullptr;
   if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return set_error(NLOS_ERR_OUT_OF_MEMORY, "self-test word");
   cudaMemset(d, 0, sizeof(int));
-  cudaError_t e;
-  if (kind == 0) {
-    const int smem = (kUmmaM + n_cols) * kUmmaK * 2;
-    e = cudaFuncSetAttribute(umma_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) {
-      umma_probe_kernel<<<1, 128, smem>>>(n_cols, out, d);
-      e = cudaGetLastError();
-    }
-  } else {
-    const int smem = (kUmmaM + n_cols) * 32 * 4;
-    e = cudaFuncSetAttribute(umma_probe_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) {
-      umma_probe_tf32_kernel<<<1, 128, smem>>>(n_cols, out, d);
-      e = cudaGetLastError();
-    }
+  const int smem = (kUmmaM + n_cols) * kUmmaK * 2;
+  cudaError_t e = cudaFuncSetAttribute(umma_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) {
+    umma_probe_kernel<<<1, 128, smem>>>(n_cols, out, d);
+    e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   int v = 0;

@@ -32,7 +32,7 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
             "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
             "nlos_reconstruct_host_many", "nlos_debug_fail_allocation", "nlos_selftest_umma",
-            "nlos_selftest_umma_kind", "nlos_ffma_rate_launch"]
+            "nlos_ffma_rate_launch"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -116,8 +116,6 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_debug_fail_allocation.restype = None
     lib.nlos_selftest_umma.argtypes = [ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
     lib.nlos_selftest_umma.restype = ctypes.c_int
-    lib.nlos_selftest_umma_kind.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
-    lib.nlos_selftest_umma_kind.restype = ctypes.c_int
     lib.nlos_ffma_rate_launch.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.nlos_ffma_rate_launch.restype = ctypes.c_int
     for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda", "nlos_bin_transient",

@@ -80,4 +80,3 @@ def test_null_arguments(lib):
     assert lib.nlos_reconstruct_batch(None, None, None, None, -1, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, 0, None) == 0
     assert lib.nlos_ffma_rate_launch(None, None, 1, 1, None, None) == 1
-    assert lib.nlos_selftest_umma_kind(2, 16, None, None) == 1

@@ -103,8 +103,8 @@ def test_pf_parity_any_size(geom, depths, zr):
 
 @pytest.mark.parametrize("depths", [40, 7, 150])
 def test_pf_fp32_tensor_core_and_ffma_depth_sums(depths):
-    """FP32 plans run the depth sum as three tf32 tensor-core products per
-    term (launch shape 0: persistent warp-specialised CTAs; shape 2: one CTA
+    """FP32 plans run the depth sum as three tensor-core products of f16
+    parts per term (launch shape 0: persistent warp-specialised CTAs; shape 2: one CTA
     per tile) or on FP32 FMAs (shape 1): each within 1e-5 of the FP64
     oracle with the same peak voxel, for depth counts below, inside and
     across the 128-depth blocks of the tensor-core forms."""

@@ -33,20 +33,6 @@ def test_umma_product_is_exact(lib, n_cols):
     np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), A @ B.T)
 
 
-@pytest.mark.parametrize("n_cols", [16, 256])
-def test_umma_tf32_product_is_exact(lib, n_cols):
-    r = np.arange(128)[:, None]
-    n = np.arange(n_cols)[:, None]
-    k = np.arange(32)[None, :]
-    A = ((r * 3 + k * 5) % 7 - 3).astype(np.float64)
-    B = ((n * 2 + k * 7) % 5 - 2).astype(np.float64)
-    out = torch.full((128, n_cols), float("nan"), device="cuda")
-    code = ctypes.c_int(-1)
-    st = lib.nlos_selftest_umma_kind(1, n_cols, ctypes.c_void_p(out.data_ptr()), ctypes.byref(code))
-    assert st == 0 and code.value == 0, lib.nlos_last_error()
-    np.testing.assert_array_equal(out.cpu().numpy().astype(np.float64), A @ B.T)
-
-
 def test_ffma_rate_is_plausible(lib):
     """The FMA-chain probe runs and reports a rate between a tenth of and the
     nominal FP32 FMA peak of 152 SMs x 128 lanes x 2 flop x 2.07 GHz."""
