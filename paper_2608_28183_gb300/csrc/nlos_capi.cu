@@ -145,6 +145,8 @@ struct nlos_plan_s {
   int* tu_pix = nullptr;
   float* tu_alpha = nullptr;
   float* tu_acut = nullptr;
+  int* clr_pix = nullptr;          // pixels of the padded grid outside every tile (depth sum writes none)
+  int nclr = 0;
   int ntiles_u = 0, Db_u = 0, nblk_u = 0, KC_u = 0, kind_u = 0;
   void* Kr = nullptr;
   int2* ch_i01 = nullptr;
@@ -438,6 +440,16 @@ nlos_status_t build_pf(nlos_plan_s* p) {
       const int i1 = std::min(i0 + 1, i_c);
       px.push_back({i0, i1, kx * Nv + ky, (float)(rb - i0), (float)ac});
     }
+  }
+  {
+    // pixels beyond the cutoff: their depth-sum output is zero
+    std::vector<char> inside((size_t)Nu * Nv, 0);
+    for (const Pix& q : px) inside[q.pix] = 1;
+    std::vector<int> outside;
+    for (int k = 0; k < Nu * Nv; ++k)
+      if (!inside[k]) outside.push_back(k);
+    p->nclr = (int)outside.size();
+    if (p->nclr > 0 && (st = upload(p, &p->clr_pix, outside, "cutoff list")) != NLOS_OK) return st;
   }
   std::stable_sort(px.begin(), px.end(), [](const Pix& u, const Pix& v) {
     return u.i0 != v.i0 ? u.i0 < v.i0 : u.i1 < v.i1;
@@ -779,7 +791,10 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     // PF3: depth sum (pixels beyond the cutoff stay zero); f16 and float32
     // plans run it on the tensor cores (f16 operands / three products of f16 parts)
     // unless the stage's launch shape asks for the FFMA form
-    NLOS_CU(cudaMemsetAsync(b1, 0, complex_bytes(st) * Nu * Nv * D, s), "pf clear");
+    // rows the depth sum does not store: pixels beyond the cutoff, and the
+    // rows of tiles whose frequency sum is split (their parts are added)
+    const size_t row_bytes = complex_bytes(st) * D;
+    NLOS_CU(launch_clear_rows(b1, p->clr_pix, p->nclr, row_bytes, s), "pf clear");
     if (p->Bu && p->tiles[sid] != 1) {
       PfUmmaParams up{};
       up.Phat = b2;
@@ -810,7 +825,15 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
       }
       up.err = err;
       // launch shape 0: persistent warp-specialised schedule; 2: one CTA per tile
-      NLOS_CU(launch_pf_umma(up, p->tiles[sid] != 2, s), "pf depth sum (tensor cores)");
+      const bool ws_sched = p->tiles[sid] != 2;
+      if (ws_sched) {
+        const int t0 = pf_umma_first_split_tile(up);
+        if (t0 < up.ntiles)
+          NLOS_CU(launch_clear_rows(b1, p->tu_pix + (size_t)t0 * kUmmaTile, (long long)(up.ntiles - t0) * kUmmaTile,
+                                    row_bytes, s),
+                  "pf clear (split tiles)");
+      }
+      NLOS_CU(launch_pf_umma(up, ws_sched, s), "pf depth sum (tensor cores)");
     } else {
     PfDepthParams dp{};
     dp.Phat = b2;

@@ -200,6 +200,12 @@ struct PfUmmaParams {
 };
 // pipelined: persistent warp-specialised CTAs (one per SM) instead of one CTA per tile
 cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s);
+// first tile whose frequency sum the persistent schedule splits (its parts
+// are added into C, which must be zero there); ntiles when none is split
+int pf_umma_first_split_tile(const PfUmmaParams& p);
+// zero `row_bytes` (a multiple of 4) at C + pix * row_bytes for every
+// pix = list[i] >= 0, i < n
+cudaError_t launch_clear_rows(void* C, const int* list, long long n, size_t row_bytes, cudaStream_t s);
 // max |x| over `count` floats into *out (float bits, atomicMax; *out must be
 // cleared beforehand)
 cudaError_t launch_absmax(const float* x, long long count, unsigned* out, cudaStream_t s);

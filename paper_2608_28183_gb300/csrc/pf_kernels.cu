@@ -480,6 +480,26 @@ cudaError_t launch_absmax(const float* x, long long count, unsigned* out, cudaSt
   return cudaGetLastError();
 }
 
+// one warp per listed row: 4-byte stores across the lanes
+__global__ void clear_rows_kernel(unsigned* C, const int* list, long long n, long long row_words) {
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= n) return;
+  const int pix = list[w];
+  if (pix < 0) return;
+  unsigned* row = C + (long long)pix * row_words;
+  for (long long i = lane; i < row_words; i += 32) row[i] = 0u;
+}
+
+cudaError_t launch_clear_rows(void* C, const int* list, long long n, size_t row_bytes, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  if (!C || !list || row_bytes % 4) return cudaErrorInvalidValue;
+  const long long threads = n * 32;
+  clear_rows_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(static_cast<unsigned*>(C), list, n,
+                                                                     (long long)(row_bytes / 4));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pf_dense(const PfDenseParams& p, cudaStream_t s) {
   if (p.npix <= 0 || p.F <= 0 || p.D <= 0) return cudaErrorInvalidValue;
   const int threads = p.D <= 64 ? 64 : 128;

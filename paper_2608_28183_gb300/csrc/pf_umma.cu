@@ -653,32 +653,53 @@ cudaError_t launch_simple(const PfUmmaParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <class Op, int Db>
-cudaError_t launch_ws(const PfUmmaParams& p, cudaStream_t s) {
-  constexpr uint32_t smem = Sizes<Op, Db>::STAGES * Sizes<Op, Db>::STAGE;
-  auto k = pf_umma_ws_kernel<Op, Db>;
+int sm_count() {
   static int sms = 0;
   if (sms == 0) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  // one persistent CTA per SM; the tail tiles' units are split along the
-  // frequency sum so that idle CTAs share them
-  PfUmmaParams q = p;
+  return sms;
+}
+
+// Grid and split of the persistent schedule: one CTA per SM; the tiles left
+// after the last full round have their units split along the frequency sum
+// (at most kMaxSplit parts, at most KC) so that idle CTAs share them.
+struct WsShape {
+  int grid, split, first_split_tile;
+};
+WsShape ws_shape(const PfUmmaParams& p) {
+  const int sms = sm_count();
   const int units = p.ntiles * p.nblk;
   const int full = p.ntiles / sms;
   const int tail_units = (p.ntiles - full * sms) * p.nblk;
   int split = tail_units > 0 ? sms / tail_units : 1;
   split = split < 1 ? 1 : split > kMaxSplit ? kMaxSplit : split;
   if (split > p.KC) split = p.KC;
-  q.split = split;
-  const int grid = full > 0 ? sms : (units * split < sms ? units * split : sms);
-  if (full == 0 && grid != sms && p.ntiles / grid != 0) q.split = 1;   // every tile whole: no tail
-  k<<<grid, kWsThreads, smem, s>>>(q);
+  WsShape w;
+  w.grid = full > 0 ? sms : (units * split < sms ? units * split : sms);
+  const int R = p.ntiles / w.grid;                     // full rounds the kernel runs
+  w.split = R * w.grid == p.ntiles ? 1 : split;        // every tile whole: no tail
+  w.first_split_tile = w.split > 1 ? R * w.grid : p.ntiles;
+  return w;
+}
+
+template <class Op, int Db>
+cudaError_t launch_ws(const PfUmmaParams& p, cudaStream_t s) {
+  constexpr uint32_t smem = Sizes<Op, Db>::STAGES * Sizes<Op, Db>::STAGE;
+  auto k = pf_umma_ws_kernel<Op, Db>;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const WsShape w = ws_shape(p);
+  PfUmmaParams q = p;
+  q.split = w.split;
+  k<<<w.grid, kWsThreads, smem, s>>>(q);
   return cudaGetLastError();
 }
 
@@ -694,6 +715,11 @@ cudaError_t launch_kind(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
 }
 
 }  // namespace
+
+int pf_umma_first_split_tile(const PfUmmaParams& p) {
+  if (p.ntiles <= 0) return 0;
+  return ws_shape(p).first_split_tile;
+}
 
 cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s) {
   if (p.ntiles <= 0) return cudaSuccess;

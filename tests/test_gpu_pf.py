@@ -127,3 +127,24 @@ def test_pf_fp32_tensor_core_and_ffma_depth_sums(depths):
     # same products; the persistent form adds the parts of split tail tiles
     # with float32 atomics
     assert rel_l2(out[2], out[0]) <= 1e-6
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_pf_reused_plan_clears_what_the_depth_sum_skips(storage):
+    """The depth sum clears only the rows it does not store (pixels beyond
+    the cutoff, tiles whose frequency sum is split). A plan run on one
+    capture and then on another must give, bit for bit, what a fresh plan
+    (zeroed workspace) gives on the second: here the cutoff lies below
+    rho_max (non-confocal) and every tile is split."""
+    from paper_2608_28183_gb300 import nlos
+    geom = synth.Geometry(16, 16, 256, 24e-12, 0.6, 0.6)
+    kw = dict(n_depths=10, depth_min_m=0.3, depth_max_m=0.9, sigma_s=1, sigma_t=1, delta_m=0.05)
+    dt = torch.float32 if storage == "f32" else torch.float16
+    a = to_device(_capture(geom, seed=1, zr=(0.4, 0.8)).counts, dt)
+    b = to_device(_capture(geom, seed=2, zr=(0.4, 0.8)).counts, dt)
+    used = nlos.plan_for_capture(geom, "pf", storage, **kw)
+    used.reconstruct(a)
+    got = used.reconstruct(b).clone()
+    fresh = nlos.plan_for_capture(geom, "pf", storage, **kw).reconstruct(b)
+    torch.cuda.synchronize()
+    assert torch.equal(got, fresh)
