@@ -794,7 +794,6 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     // rows the depth sum does not store: pixels beyond the cutoff, and the
     // rows of tiles whose frequency sum is split (their parts are added)
     const size_t row_bytes = complex_bytes(st) * D;
-    NLOS_CU(launch_clear_rows(b1, p->clr_pix, p->nclr, row_bytes, s), "pf clear");
     if (p->Bu && p->tiles[sid] != 1) {
       PfUmmaParams up{};
       up.Phat = b2;
@@ -826,15 +825,13 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
       up.err = err;
       // launch shape 0: persistent warp-specialised schedule; 2: one CTA per tile
       const bool ws_sched = p->tiles[sid] != 2;
-      if (ws_sched) {
-        const int t0 = pf_umma_first_split_tile(up);
-        if (t0 < up.ntiles)
-          NLOS_CU(launch_clear_rows(b1, p->tu_pix + (size_t)t0 * kUmmaTile, (long long)(up.ntiles - t0) * kUmmaTile,
-                                    row_bytes, s),
-                  "pf clear (split tiles)");
-      }
+      const int t0 = ws_sched ? pf_umma_first_split_tile(up) : up.ntiles;
+      NLOS_CU(launch_clear_rows2(b1, p->clr_pix, p->nclr, p->tu_pix + (size_t)t0 * kUmmaTile,
+                                 (long long)(up.ntiles - t0) * kUmmaTile, row_bytes, s),
+              "pf clear");
       NLOS_CU(launch_pf_umma(up, ws_sched, s), "pf depth sum (tensor cores)");
     } else {
+    NLOS_CU(launch_clear_rows(b1, p->clr_pix, p->nclr, row_bytes, s), "pf clear");
     PfDepthParams dp{};
     dp.Phat = b2;
     dp.K = p->Kr;

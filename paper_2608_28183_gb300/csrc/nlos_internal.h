@@ -206,6 +206,9 @@ int pf_umma_first_split_tile(const PfUmmaParams& p);
 // zero `row_bytes` (a multiple of 4) at C + pix * row_bytes for every
 // pix = list[i] >= 0, i < n
 cudaError_t launch_clear_rows(void* C, const int* list, long long n, size_t row_bytes, cudaStream_t s);
+// the same for the entries of two lists in one launch
+cudaError_t launch_clear_rows2(void* C, const int* l1, long long n1, const int* l2, long long n2, size_t row_bytes,
+                               cudaStream_t s);
 // max |x| over `count` floats into *out (float bits, atomicMax; *out must be
 // cleared beforehand)
 cudaError_t launch_absmax(const float* x, long long count, unsigned* out, cudaStream_t s);

@@ -329,36 +329,84 @@ cudaError_t launch_kr_store(const double2* K64, void* K, long long count, int st
 // Per-volume scale for reduced-precision storage (two-stage, deterministic).
 // ---------------------------------------------------------------------------
 // eight consecutive elements per thread and iteration (n is a multiple of 8,
-// so they share one pencil and their ramp is t0 .. t0 + 7)
-template <class TR>
-__global__ void sumsq_partial_kernel(const TR* H, long long count, int n, float t_scale, float* partial) {
-  __shared__ float red[256];
-  float acc = 0.f;
-  const long long chunks = count / 8;
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < chunks;
-       q += (long long)gridDim.x * blockDim.x) {
-    const long long i0 = q * 8;
-    const int t0 = (int)(i0 % n);
+// so they share one pencil and their ramp is t0 .. t0 + 7), read as one
+// 16-byte vector (two for float) when the array is 16-byte aligned; the ramp
+// index advances by the grid stride modulo n instead of a division per step
+template <class TR> struct Eight;
+template <> struct Eight<float> {
+  static __device__ __forceinline__ void get(const float* p, bool vec, float (&v)[8]) {
+    if (vec) {
+      const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      float v = Real<TR>::get(H + i0 + k);
-      if (t_scale != 0.f) v *= (float)(t0 + k) * t_scale;
-      acc = fmaf(v, v, acc);
+      for (int k = 0; k < 8; ++k) v[k] = p[k];
     }
   }
-  red[threadIdx.x] = acc;
-  __syncthreads();
-  for (int sft = 128; sft > 0; sft >>= 1) {
-    if (threadIdx.x < sft) red[threadIdx.x] += red[threadIdx.x + sft];
-    __syncthreads();
+};
+template <class T2, class TR> struct EightHalf {
+  static __device__ __forceinline__ void get(const TR* p, bool vec, float (&v)[8]) {
+    if (vec) {
+      const uint4 u = reinterpret_cast<const uint4*>(p)[0];
+      const T2* h = reinterpret_cast<const T2*>(&u);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = Cpx<T2>::get(h + k);
+        v[2 * k] = f.x;
+        v[2 * k + 1] = f.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = Real<TR>::get(p + k);
+    }
   }
-  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
-}
+};
+template <> struct Eight<__half> : EightHalf<__half2, __half> {};
+template <> struct Eight<__nv_bfloat16> : EightHalf<__nv_bfloat162, __nv_bfloat16> {};
 
-__global__ void sumsq_final_kernel(const float* partial, int npartial, float target, float* out) {
-  __shared__ double red[256];
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < npartial; i += blockDim.x) acc += partial[i];
+// The last CTA to finish (a counter in the partials' array, reset by that
+// CTA) sums the partials in index order and writes the scale, its inverse
+// and the inverse square: the result does not depend on CTA timing.
+template <class TR>
+__global__ void sumsq_partial_kernel(const TR* H, long long count, int n, float t_scale, bool vec, float* partial,
+                                     unsigned* counter, float target, float* out) {
+  __shared__ float red[256];
+  __shared__ double dred[256];
+  __shared__ bool last;
+  float acc = 0.f;
+  const long long chunks = count / 8;
+  const long long q0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int t0 = (int)((q0 * 8) % n);
+  const int step = (int)((stride * 8) % n);
+  constexpr int U = 4;                       // independent loads in flight per thread
+  long long q = q0;
+  for (; q + (U - 1) * stride < chunks; q += U * stride) {
+    float v[U][8];
+#pragma unroll
+    for (int u = 0; u < U; ++u) Eight<TR>::get(H + (q + u * stride) * 8, vec, v[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float x = t_scale != 0.f ? v[u][k] * ((float)(t0 + k) * t_scale) : v[u][k];
+        acc = fmaf(x, x, acc);
+      }
+      t0 += step;
+      if (t0 >= n) t0 -= n;
+    }
+  }
+  for (; q < chunks; q += stride) {
+    float v[8];
+    Eight<TR>::get(H + q * 8, vec, v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float x = t_scale != 0.f ? v[k] * ((float)(t0 + k) * t_scale) : v[k];
+      acc = fmaf(x, x, acc);
+    }
+    t0 += step;
+    if (t0 >= n) t0 -= n;
+  }
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int sft = 128; sft > 0; sft >>= 1) {
@@ -366,7 +414,23 @@ __global__ void sumsq_final_kernel(const float* partial, int npartial, float tar
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const double nrm = sqrt(red[0]);
+    partial[blockIdx.x] = red[0];
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double dacc = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) dacc += ((volatile float*)partial)[i];
+  dred[threadIdx.x] = dacc;
+  __syncthreads();
+  for (int sft = 128; sft > 0; sft >>= 1) {
+    if (threadIdx.x < sft) dred[threadIdx.x] += dred[threadIdx.x + sft];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(dred[0]);
     const float sc = nrm > 0.0 ? (float)(target / nrm) : 1.0f;
     out[0] = sc;
     out[1] = 1.0f / sc;
@@ -376,17 +440,31 @@ __global__ void sumsq_final_kernel(const float* partial, int npartial, float tar
 
 cudaError_t launch_volume_scale(const void* H, long long count, int n, float t_scale, int storage,
                                 float target, float* partial, int npartial, float* out, cudaStream_t s) {
+  // four CTAs per SM (enough bytes in flight with 16-byte loads); the count
+  // of partials only changes the summation tree, not determinism. The last
+  // partial slot holds the CTAs' completion counter.
+  int blocks = npartial - 1 < 152 * 4 ? npartial - 1 : 152 * 4;
+  if (blocks < 1) return cudaErrorInvalidValue;
+  unsigned* counter = reinterpret_cast<unsigned*>(partial + npartial - 1);
+  // a caller's workspace may hold anything there on its first use
+  cudaError_t e0 = cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
+  if (e0 != cudaSuccess) return e0;
+  const bool vec = (reinterpret_cast<uintptr_t>(H) & 15) == 0;
   switch (storage) {
-    case kF32: sumsq_partial_kernel<float><<<npartial, 256, 0, s>>>(static_cast<const float*>(H), count, n, t_scale, partial); break;
-    case kF16: sumsq_partial_kernel<__half><<<npartial, 256, 0, s>>>(static_cast<const __half*>(H), count, n, t_scale, partial); break;
+    case kF32:
+      sumsq_partial_kernel<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(H), count, n, t_scale, vec, partial,
+                                                         counter, target, out);
+      break;
+    case kF16:
+      sumsq_partial_kernel<__half><<<blocks, 256, 0, s>>>(static_cast<const __half*>(H), count, n, t_scale, vec,
+                                                          partial, counter, target, out);
+      break;
     case kBF16:
-      sumsq_partial_kernel<__nv_bfloat16><<<npartial, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(H), count, n, t_scale, partial);
+      sumsq_partial_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(H), count, n,
+                                                                 t_scale, vec, partial, counter, target, out);
       break;
     default: return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  sumsq_final_kernel<<<1, 256, 0, s>>>(partial, npartial, target, out);
   return cudaGetLastError();
 }
 
@@ -480,24 +558,32 @@ cudaError_t launch_absmax(const float* x, long long count, unsigned* out, cudaSt
   return cudaGetLastError();
 }
 
-// one warp per listed row: 4-byte stores across the lanes
-__global__ void clear_rows_kernel(unsigned* C, const int* list, long long n, long long row_words) {
+
+// one warp per listed row (first list, then second): 4-byte stores across the lanes
+__global__ void clear_rows2_kernel(unsigned* C, const int* l1, long long n1, const int* l2, long long n2,
+                                   long long row_words) {
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= n) return;
-  const int pix = list[w];
+  if (w >= n1 + n2) return;
+  const int pix = w < n1 ? l1[w] : l2[w - n1];
   if (pix < 0) return;
   unsigned* row = C + (long long)pix * row_words;
   for (long long i = lane; i < row_words; i += 32) row[i] = 0u;
 }
 
-cudaError_t launch_clear_rows(void* C, const int* list, long long n, size_t row_bytes, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  if (!C || !list || row_bytes % 4) return cudaErrorInvalidValue;
-  const long long threads = n * 32;
-  clear_rows_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(static_cast<unsigned*>(C), list, n,
-                                                                     (long long)(row_bytes / 4));
+cudaError_t launch_clear_rows2(void* C, const int* l1, long long n1, const int* l2, long long n2, size_t row_bytes,
+                               cudaStream_t s) {
+  if (n1 < 0 || n2 < 0) return cudaErrorInvalidValue;
+  if (n1 + n2 == 0) return cudaSuccess;
+  if (!C || (n1 && !l1) || (n2 && !l2) || row_bytes % 4) return cudaErrorInvalidValue;
+  const long long threads = (n1 + n2) * 32;
+  clear_rows2_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(static_cast<unsigned*>(C), l1, n1, l2, n2,
+                                                                      (long long)(row_bytes / 4));
   return cudaGetLastError();
+}
+
+cudaError_t launch_clear_rows(void* C, const int* list, long long n, size_t row_bytes, cudaStream_t s) {
+  return launch_clear_rows2(C, list, n, nullptr, 0, row_bytes, s);
 }
 
 cudaError_t launch_pf_dense(const PfDenseParams& p, cudaStream_t s) {
