@@ -148,3 +148,28 @@ def test_pf_reused_plan_clears_what_the_depth_sum_skips(storage):
     fresh = nlos.plan_for_capture(geom, "pf", storage, **kw).reconstruct(b)
     torch.cuda.synchronize()
     assert torch.equal(got, fresh)
+
+
+@pytest.mark.parametrize("factor", [0.0, 2.0 ** -30, 2.0 ** 30])
+def test_pf_fp32_depth_sum_scale_follows_the_data(factor):
+    """The float32 depth sum scales its phasors into f16 range per volume by
+    a power of two from their maximum. Reconstruction is linear and a power
+    of two commutes with every rounding, so a capture multiplied by 2^k must
+    give exactly 2^k times the volume (zero for zero), far outside the f16
+    range either way, on the persistent and the one-CTA-per-tile schedules."""
+    from paper_2608_28183_gb300 import nlos
+    geom = synth.Geometry(32, 32, 512, 16e-12, 1.0, 1.0)
+    plan, _ = _pair(geom, (40, 0.4, 1.2))
+    cap = _capture(geom, seed=17, zr=(0.5, 1.1))
+    names = [nlos.load_library().nlos_plan_stage_name(plan.handle, i).decode() for i in range(len(plan.tiles))]
+    stage = names.index("pf_depth_sum")
+    for v in (0, 2):
+        t = plan.tiles
+        t[stage] = v
+        plan.tiles = t
+        base = _gpu(plan, cap.counts)
+        got = _gpu(plan, cap.counts * factor)
+        if factor == 0.0:
+            assert not got.any()
+        else:
+            assert np.array_equal(got, base * factor), (v, factor, rel_l2(got / factor, base))
