@@ -59,15 +59,21 @@ typedef struct nlos_server_s* nlos_server_t;
  * Capture and method description (problem statement of Sec. 3: confocal
  * transient H(x_s, x_s, t) sampled on an nx x ny wall grid over a
  * wall_w_m x wall_h_m relay wall, nt bins of bin_width_s).
- *   nx, ny        scan grid; powers of two in [8, 1024]
- *   nt            time bins; power of two in [16, 2048] for f-k, [16, 4096] for phasor
+ *   nx, ny        scan grid in [8, 1024] (any size: padded axes run at the
+ *                 smallest power of two >= 2x the size)
+ *   nt            time bins in [16, 4096] (the f-k time axis padded like x, y;
+ *                 the phasor band transform runs at the next power of two >= nt)
  *   bin_width_s   time-bin width dt (> 0)
  *   wall_w_m/h_m  scanned wall extent along x / y (> 0); wall samples are cell centres
  *   method        nlos_method_t
  *   storage       nlos_storage_t of the input and of stored intermediates;
  *                 reduced precision uses a per-volume scale, arithmetic is float32
+ *                 (the phasor depth sum runs on tensor cores: f16 operands for
+ *                 16-bit storage; for float32 storage every operand split into
+ *                 two f16 parts, three exact products per term, float32 sums)
  *   pad_factor    2: zero padding x2 on every axis (Sec. 4.2); 1: unpadded f-k
- *                 (Sec. 4.2's Pad x1 variant; nx, ny >= 16); other values INVALID_ARG
+ *                 (Sec. 4.2's Pad x1 variant; nx, ny >= 16, powers of two);
+ *                 other values INVALID_ARG
  *   output        NLOS_OUT_MAGNITUDE: float32 volume, |Psi|^2 for f-k (Alg. 1)
  *                 and |I| for phasor fields (Alg. 4); NLOS_OUT_COMPLEX: the
  *                 complex field itself (Psi, or I) as interleaved float32
@@ -107,8 +113,9 @@ void nlos_plan_desc_default(nlos_plan_desc_t* desc);
  * allocates the default workspace. Synchronous. *out receives an opaque
  * handle owned by the caller until nlos_plan_destroy.
  * Errors: INVALID_ARG (null pointer, sizes, extents <= 0, empty band),
- * UNSUPPORTED (unpadded phasor fields, non-power-of-two sizes, 16-bit dense phasor
- * fields), OUT_OF_MEMORY, CUDA.
+ * UNSUPPORTED (sizes outside the ranges above, unpadded phasor fields,
+ * unpadded f-k of non-power-of-two sizes, 16-bit dense phasor fields),
+ * OUT_OF_MEMORY, CUDA.
  */
 nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out);
 
@@ -196,14 +203,17 @@ nlos_status_t nlos_reconstruct_noalloc(nlos_plan_t plan, const void* transient, 
 
 /*
  * Autotune the plan's launch shapes: for every stage with more than one
- * kernel variant (column tiles of the x/y transforms, pencils per CTA of the
- * f-k temporal stage) time the whole reconstruction with each variant on a
+ * kernel variant (column tiles and TMA staging of the x/y transforms, pencils
+ * per CTA of the f-k temporal stage, the phasor depth sum's persistent
+ * tensor-core, one-CTA-per-tile tensor-core and FP32-FMA forms) time the
+ * whole reconstruction with each variant on a
  * scratch input (coordinate descent, CUDA events on `stream`) and keep the
  * fastest. Results are cached per plan shape for the process and, when the
  * environment variable NLOS_AUTOTUNE_CACHE names a file, in that JSON file
  * (read on first use, rewritten after tuning). Synchronous; allocates a
- * scratch transient and volume for the duration of the call. Numerics do not
- * depend on the variant. Errors: INVALID_ARG (NULL plan, tracing enabled),
+ * scratch transient and volume for the duration of the call. Variants
+ * differ in numerics only by rounding (every one within the storage type's
+ * tolerance of the float64 method). Errors: INVALID_ARG (NULL plan, tracing enabled),
  * OUT_OF_MEMORY, CUDA.
  */
 nlos_status_t nlos_plan_autotune(nlos_plan_t plan, void* stream);
