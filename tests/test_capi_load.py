@@ -57,6 +57,9 @@ def _create(lib, **kw):
     (dict(pad_factor=1, nx=8), 4), (dict(pad_factor=1, nx=24), 4), (dict(nt=8192), 4), (dict(nx=2048), 4),
     (dict(nx=4, ny=4), 4), (dict(method=1, n_depths=0), 1),
     (dict(method=1, n_depths=8, depth_min_m=1.0, depth_max_m=0.5), 1), (dict(output=2), 1), (dict(output=-1), 1),
+    (dict(method=2, storage=1, n_depths=8, depth_min_m=0.5, depth_max_m=1.0), 4),
+    (dict(method=1, n_depths=8, depth_min_m=0.5, depth_max_m=1.0, sigma_s=0, sigma_t=1), 1),
+    (dict(method=1, n_depths=8, depth_min_m=0.5, depth_max_m=1.0, wavelength_m=-0.01), 1),
 ])
 def test_invalid_descriptions_rejected_before_device_work(lib, kw, status):
     st, msg = _create(lib, **kw)
