@@ -83,3 +83,20 @@ def test_null_arguments(lib):
     assert lib.nlos_reconstruct_batch(None, None, None, None, -1, None) == 1
     assert lib.nlos_reconstruct_batch(None, None, None, None, 0, None) == 0
     assert lib.nlos_ffma_rate_launch(None, None, 1, 1, None, None) == 1
+
+
+def test_binding_rejects_host_tensors_before_device_work(lib):
+    """The Python binding only marshals: tensors that are not contiguous CUDA
+    tensors of the right type are refused before any library call, and there
+    is no host fallback to take them instead."""
+    torch = pytest.importorskip("torch")
+    v = torch.zeros((4, 4, 8), dtype=torch.float32)
+    with pytest.raises(ValueError, match="CUDA"):
+        nlos.max_image(v)
+    with pytest.raises(ValueError, match="CUDA"):
+        nlos.moe_mix(v[0], v[1])
+    with pytest.raises(ValueError, match="CUDA"):
+        nlos.dda([v, v])
+    px = torch.zeros(16, dtype=torch.int32)
+    with pytest.raises(ValueError, match="uint32"):
+        nlos.bin_transient(px, px, 4, 4, 8, 0, 1)
