@@ -769,6 +769,14 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   bp.ld_scale = 1.0f;
   bp.ld_dev_scale = s_in;
   bp.st_scale = gn;
+  // the float32 tensor-core depth sum scales the phasors by a bound taken from
+  // their largest component: the band transform records it as it stores them
+  unsigned* amax = reinterpret_cast<unsigned*>(ws + p->off_scal + kAmaxOffset);
+  const bool f16x3 = p->Bu && p->kind_u == kUmmaF16x3;
+  if (f16x3 && !P_in) {
+    NLOS_CU(cudaMemsetAsync(amax, 0, sizeof(unsigned), s), "phasor bound clear");
+    bp.amax = amax;
+  }
   if (!P_in) NLOS_CU(launch_pf_band(bp, st, s), "pf band transform");
   NLOS_MARK(p, s, sid++);
   // PF2: top-left padding and 2D forward transform (y then x) of every band slice
@@ -813,10 +821,12 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
       up.scale = p->kind_u == kUmmaF16 ? c3 : (float)(c3_data / p->bu_scale);
       if (p->kind_u == kUmmaF16x3) {
         // bound on |Phat|: the 2D transforms sum a x b phasors of modulus
-        // <= sqrt(2) max|component| (times the passes' scales)
-        unsigned* amax = reinterpret_cast<unsigned*>(ws + p->off_scal + kAmaxOffset);
-        NLOS_CU(cudaMemsetAsync(amax, 0, sizeof(unsigned), s), "phasor bound clear");
-        NLOS_CU(launch_absmax(static_cast<const float*>(P), 2 * a * b * F, amax, s), "phasor bound");
+        // <= sqrt(2) max|component| (times the passes' scales); phasors the
+        // caller supplied get their maximum here
+        if (P_in) {
+          NLOS_CU(cudaMemsetAsync(amax, 0, sizeof(unsigned), s), "phasor bound clear");
+          NLOS_CU(launch_absmax(static_cast<const float*>(P), 2 * a * b * F, amax, s), "phasor bound");
+        }
         int e2 = 0;
         frexp(1.5 * (double)a * b * g2a * g2b, &e2);
         up.amax = amax;

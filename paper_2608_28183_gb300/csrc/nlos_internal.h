@@ -104,6 +104,7 @@ struct PfBandParams {
   const float* ld_dev_scale;
   float st_scale;
   int accumulate;              // add to P instead of overwriting it
+  unsigned* amax;              // when set: atomicMax of max |Re|, |Im| of the stored P (float bits)
 };
 cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s);
 

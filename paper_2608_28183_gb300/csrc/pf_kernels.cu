@@ -25,6 +25,7 @@ struct PfBandCtx {
   float ldmul, stmul;
   int accumulate;
   int n_in;                    // samples of the pencil; the DFT runs over L >= n_in
+  mutable float m = 0.f;       // max |component| of what this thread stored
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
     x[0] = (valid && l < n_in) ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f) : make_float2(0.f, 0.f);
   }
@@ -35,6 +36,7 @@ struct PfBandCtx {
     float2 v = cscale(x[0], __ldg(w + f) * stmul);
     if (accumulate) v = cadd(v, Cpx<TS>::get(P + f));
     Cpx<TS>::put(P + f, v);
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
   }
 };
 
@@ -60,6 +62,13 @@ pf_band_kernel(const PfBandParams p) {
                            pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale, p.accumulate,
                            p.n};
   fftn_run<L, 1, false, false>(ctx, j0);
+  if (p.amax) {
+    // the bound the float32 depth sum scales its phasors by (see PfBandParams)
+    float m = ctx.m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(p.amax, __float_as_uint(m));
+  }
 }
 
 template <int L, class TR, class TS>
