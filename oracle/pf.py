@@ -14,8 +14,9 @@ taper) and Alg. 4, with these readings where the paper is silent:
     sigma_t = cycles / (6 f0), sigma_f = 1 / (2 pi sigma_t). The band keeps
     bins k0 - K_h .. k0 + K_h with K_h = round(5 sigma_f / df), clipped to
     [1, n/2 - 1]; w(f) = exp(-(f_k - f0)^2 / (2 sigma_f^2)).
-  * Phasors: P(x, y, f) = sum_t H(x, y, t) exp(-2 pi i k_f t / n)
-    (forward DFT sign e^{-i}); w(f) is applied inside the depth sum (Alg. 4).
+  * Phasors: P(x, y, f) = sum_t H(x, y, t) exp(-2 pi i k_f t / Lt), Lt the
+    temporal transform length above (forward DFT sign e^{-i}); w(f) is
+    applied inside the depth sum (Alg. 4).
   * Spectral coordinates: the top-left padded grid is Nu x Nv = 2a x 2b
     (the next powers of two >= 2a, 2b for other sizes)
     with physical sides Nu dx and Nv dy; DFT index (kx, ky) has signed indices
@@ -35,8 +36,10 @@ Parity: pinned (tests/test_oracle_pf.py): the supplementary worked example
 J0 against its integral definition and tabulated zeros, the ring basis
 against angular quadrature of a unit ring's 2D Fourier transform, the
 radial quadrature against the closed-form Hankel transform of a Gaussian,
-taper endpoints, the cos/sin linearity identity, single-point focusing, and
-peak agreement with the direct spatial RSD summation.
+taper endpoints, the cos/sin linearity identity, single-point focusing,
+peak agreement with the direct spatial RSD summation, and the complex field
+of propagate against the direct sum with the fixed dx dy area factor (this
+pins w(f) and the absolute and per-frequency amplitude of K_r).
 """
 from __future__ import annotations
 

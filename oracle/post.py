@@ -23,7 +23,8 @@ Parity: pinned (tests/test_oracle_post.py): coherence bounds 0 <= C < 1,
 C = 0 for frames that cancel and C -> 1 for identical frames, the merge of
 identical frames equals |f| C; beta = 1 gives the plain product of the
 normalised images and beta = 0 the f-k image; DDA with N_w = 1 is the
-identity and a constant sequence is a fixed point.
+identity, a constant sequence is a fixed point, and a 3-frame x 4-depth case
+matches values worked out by hand from the reading above (N = 1, 1, 2, 3).
 """
 from __future__ import annotations
 

@@ -41,3 +41,19 @@ def test_max_image():
     v[1, 2, 3] = 7.0
     img = post.max_image(v)
     assert img.shape == (2, 3) and img[1, 2] == 7.0 and img.sum() == 7.0
+
+
+def test_dda_hand_computed_case():
+    """Three frames (newest first) of four depth planes. With N_w = 3 and
+    n_z = 4 the reading N(z) = min(N_w, 1 + floor(N_w z / n_z)) gives
+    N = 1, 1, 2, 3, so plane 0 and 1 keep the newest frame, plane 2 averages
+    the newest two and plane 3 all three (values worked out by hand)."""
+    frames = np.array([[1.0, 2.0, 3.0, 4.0],
+                       [10.0, 20.0, 30.0, 40.0],
+                       [100.0, 200.0, 300.0, 400.0]])
+    np.testing.assert_array_equal(post.dda_counts(4, 3), [1, 1, 2, 3])
+    np.testing.assert_allclose(post.dda(frames), [1.0, 2.0, 16.5, 148.0], rtol=1e-15)
+    # a lateral axis between frames and depth: every pixel follows the same counts
+    stacked = np.stack([frames, 2 * frames], axis=1)          # [N_w][2][n_z]
+    np.testing.assert_allclose(post.dda(stacked), [[1.0, 2.0, 16.5, 148.0], [2.0, 4.0, 33.0, 296.0]],
+                               rtol=1e-15)
