@@ -190,14 +190,18 @@ nlos_status_t nlos_reconstruct_batch(const nlos_plan_t* plans, const void* const
  * from a fixed 32 MiB array in device memory that the library holds on every
  * GPU it is loaded on, instead of the plan's workspace. (The paper has no
  * counterpart; this serves callers that cannot call cudaMalloc at
- * reconstruction time, e.g. inside a global-mode stream capture, in real-time
- * loops, or under an externally managed memory pool.) The plan must already
- * exist. The first call on each device looks the array's address up with
- * cudaGetSymbolAddress and should come before any stream capture.
- * Errors: INVALID_ARG if the plan's workspace_bytes exceed 32 MiB, if an
- * argument is NULL, or if stage tracing is enabled on the plan; CUDA if the
- * lookup fails. All calls share the array: calls that overlap on the GPU race
- * and must be serialised by the caller. Asynchronous on stream.
+ * reconstruction time: real-time loops, where an allocation may synchronise
+ * the device and stall a frame, and applications that give this library a
+ * fixed share of device memory and manage the rest in their own pool.) The
+ * plan must already exist. The first call on each device looks the array's
+ * address up with cudaGetSymbolAddress and should come before any stream
+ * capture. Errors: INVALID_ARG if the plan's workspace_bytes exceed 32 MiB,
+ * if an argument is NULL, or if stage tracing is enabled on the plan; CUDA if
+ * the lookup fails. All calls share the array, which keeps the previous
+ * call's contents: calls that overlap on the GPU race and must be serialised
+ * by the caller. A bounded wait that gives up inside the call is not
+ * observable here (its error word lives in the array, which
+ * nlos_workspace_check does not read). Asynchronous on stream.
  */
 nlos_status_t nlos_reconstruct_noalloc(nlos_plan_t plan, const void* transient, void* volume, void* stream);
 

@@ -1089,6 +1089,13 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   for (size_t i = 0; i < p->tiles.size(); ++i)
     if (p->stage_kind[i] == 1 || p->stage_kind[i] == 3) p->tiles[i] = axis_ic_count(p->stage_len[i]);
   st = desc->method == NLOS_FK ? build_fk(p) : build_pf(p);
+  // every stage buffer lies inside [0, ws_bytes): the regions are laid out in
+  // order and the scalar area and partials close the workspace. Callers that
+  // supply scratch (nlos_reconstruct_ws, the fixed array of
+  // nlos_reconstruct_noalloc) size it by ws_bytes alone.
+  if (st == NLOS_OK && !(p->off[0] <= p->off[1] && p->off[1] <= p->off[2] && p->off[2] <= p->off_scal &&
+                         p->off_scal + 256 <= p->off_part && p->off_part < p->ws_bytes))
+    st = fail(NLOS_ERR_UNSUPPORTED, "internal: workspace layout out of order");
   const bool own_ws = !(flags & NLOS_PLAN_NO_WORKSPACE);
   if (st == NLOS_OK && own_ws) st = dalloc(p, &p->ws, p->ws_bytes, "workspace");
   if (st == NLOS_OK && own_ws) {

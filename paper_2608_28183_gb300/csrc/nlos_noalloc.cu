@@ -1,12 +1,14 @@
 // nlos_reconstruct_noalloc: a reconstruction that allocates nothing.
 //
-// Some callers cannot call cudaMalloc when they reconstruct: code running
-// while a stream capture in global mode is active (where allocation calls are
-// illegal), real-time loops that must not block on the allocator, and
-// processes whose device memory is handed out by a fixed pool set up
-// elsewhere. For them this entry point runs a plan's stage sequence with its
-// scratch taken from a fixed array in device memory instead of the plan's
-// workspace. The plan itself (and its tables) must have been created earlier.
+// Some callers cannot call cudaMalloc when they reconstruct: real-time
+// capture loops, where an allocation may synchronise the device and stall a
+// frame for an unbounded time; host applications that hand this library a
+// fixed share of device memory and own the rest through their own pool, so
+// that any further allocation fails or competes with them; and code that is
+// not allowed to allocate at that point of its control flow. For them this
+// entry point runs a plan's stage sequence with its scratch taken from a
+// fixed array in device memory instead of the plan's workspace. The plan
+// itself (and its tables) must have been created earlier.
 //
 // The scratch is a file-scope __device__ array of kNoAllocScratchBytes
 // (32 MiB). Every GPU that loads this library holds its own copy until the
@@ -20,6 +22,9 @@
 // only accumulator (the phasor-field depth sum) is cleared by the sequence
 // itself on every call. Calls that overlap on the GPU (for example, calls on
 // different streams) race on the array and must be serialised by the caller.
+// The device error word of the bounded waits lives inside the array, which
+// nlos_workspace_check does not read: a wait that gives up on this path is
+// not reported (the call still returns its launch status).
 #include <stdio.h>
 
 #include <mutex>

@@ -64,10 +64,15 @@ pf_band_kernel(const PfBandParams p) {
   fftn_run<L, 1, false, false>(ctx, j0);
   if (p.amax) {
     // the bound the float32 depth sum scales its phasors by (see PfBandParams)
+    // (blocks of short transforms have fewer than 32 threads: reduce over
+    // the lanes that exist)
+    constexpr int TH = PfBandTile<L>::THREADS;
+    constexpr int WID = TH < 32 ? TH : 32;
+    constexpr unsigned MASK = TH < 32 ? ((1u << TH) - 1u) : 0xffffffffu;
     float m = ctx.m;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(p.amax, __float_as_uint(m));
+    for (int o = WID / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(MASK, m, o, WID));
+    if ((threadIdx.x % WID) == 0) atomicMax(p.amax, __float_as_uint(m));
   }
 }
 

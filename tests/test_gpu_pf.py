@@ -61,6 +61,22 @@ def test_pf_parity_small(geom, depths, zr):
     assert same_peak(got, ref)
 
 
+@pytest.mark.parametrize("nt,dt", [(16, 200e-12), (32, 100e-12)])
+def test_pf_short_transients_f32(nt, dt):
+    """Float32 plans whose band transform has fewer than 32 threads per block
+    (L = 16: 8 threads, L = 32: 16): the phasor bound that scales the
+    tensor-core depth sum's operands is reduced over those lanes only."""
+    geom = synth.Geometry(8, 8, nt, dt, 0.64, 0.64)
+    plan, oplan = _pair(geom, (6, 0.15, 0.45))
+    assert len(oplan.band.bins) == 6
+    cap = _capture(geom, seed=nt, zr=(0.2, 0.4))
+    got = _gpu(plan, cap.counts)
+    ref = pf.pf_reconstruct(exact_input(cap.counts, torch.float32), oplan)
+    err = rel_l2(got, ref)
+    assert err <= 1e-5, err
+    assert same_peak(got, ref)
+
+
 def test_pf_non_confocal_modality():
     geom, depths, zr = CASES[2]
     plan, oplan = _pair(geom, depths, sigma_s=1, sigma_t=1, delta_m=0.05)

@@ -1,9 +1,10 @@
 """nlos_reconstruct_noalloc: the reconstruction entry point that allocates nothing.
 
-It is for callers that cannot call cudaMalloc while they reconstruct (inside a
-global-mode stream capture, real-time loops, externally managed memory pools):
-it runs an existing plan with its scratch in a fixed 32 MiB device array held
-by the library. Its output must match nlos_reconstruct's (the entry point that
+It is for callers that cannot call cudaMalloc while they reconstruct
+(real-time loops, where an allocation may stall a frame; applications that
+give the library a fixed share of device memory and pool the rest
+themselves): it runs an existing plan with its scratch in a fixed 32 MiB
+device array held by the library. Its output must match nlos_reconstruct's (the entry point that
 uses the plan's own workspace) within the parity tolerance, on two calls in a
 row (the array keeps the previous call's contents, so the second call checks
 that nothing stale leaks in). This file is collected last on purpose.
