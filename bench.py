@@ -33,9 +33,10 @@ METRIC = "recon volumes/s + p50/p99 ms at 256x256x512 f-k; HBM GB/s vs peak"
 UNIT = "volumes/s"
 PAPER_SECONDS_PER_VOLUME = 0.143   # offline f-k 256x256x512, padded, FP32, RTX 4080 SUPER (incl. alloc/free)
 FALLBACK_HBM_GBS = 6800.0
-# sources of the dominant kernel (the f-k temporal-frequency stage); a change
-# to them invalidates the committed DRAM-traffic figure
-KERNEL_SOURCES = ["paper_2608_28183_gb300/csrc/nlos_fft.cuh", "paper_2608_28183_gb300/csrc/fk_zstage.cuh"]
+# sources of the f-k kernels (temporal-frequency stage, fused lateral pairs);
+# a change to them invalidates the committed DRAM-traffic figures
+KERNEL_SOURCES = ["paper_2608_28183_gb300/csrc/nlos_fft.cuh", "paper_2608_28183_gb300/csrc/fk_zstage.cuh",
+                  "paper_2608_28183_gb300/csrc/fk_chain.cuh", "paper_2608_28183_gb300/csrc/axis_fft.cuh"]
 
 
 def parse_args():
@@ -99,6 +100,9 @@ def stage_bytes(a, b, n, storage):
         "fk_stolt_z": 2 * half * cb + 4 * V * cb,
         "fk_y_inverse": 4 * V * cb + 2 * V * cb,
         "fk_x_inverse": 2 * V * cb + V * 4,
+        # fused pairs: the intermediate stays on chip / in L2
+        "fk_xy_forward": V * rb + 2 * half * cb,
+        "fk_yx_inverse": 4 * V * cb + V * 4,
     }
     if storage != "f32":
         out["volume_scale"] = V * rb
@@ -860,6 +864,35 @@ def main():
             R16 = ofk.fk_reconstruct(H16d, g.bin_width_s, g.wall_w_m, g.wall_h_m, workers=os.cpu_count())
             variants["f16_storage"]["rel_l2_vs_oracle"] = rel_l2(v16.cpu().numpy(), R16)
 
+    def compact_pf(pf):
+        if not pf or "error" in pf:
+            return pf
+        out = {"workload": pf.get("workload")}
+        for st in ("f32", "f16"):
+            r = pf.get(st) or {}
+            ds = r.get("depth_sum_roofline") or {}
+            out[st] = {"volumes_per_s": r.get("volumes_per_s"), "p50_ms": r.get("p50_ms"), "p99_ms": r.get("p99_ms"),
+                       "rel_l2": r.get("rel_l2_vs_oracle", r.get("rel_l2_vs_f32")),
+                       "depth_sum_ms": (r.get("stages_ms") or {}).get("pf_depth_sum"),
+                       "depth_sum_frac": ds.get("frac"), "depth_sum_form": ds.get("form")}
+        return out
+
+    def compact_batch(b):
+        if not b or "error" in b:
+            return b
+        return {k: b.get(k) for k in ("graph_fp16_volumes_per_s", "sequential_fp32_volumes_per_s",
+                                      "max_rel_l2_fp16_vs_fp32")}
+
+    def compact_serving(sv):
+        if not sv or "error" in sv:
+            return sv
+        return [{"rps": r["rate_rps"], "fp16_served": [round(r["served_fp16"]["volumes_per_s"], 1),
+                                                       round(r["served_fp16"]["p50_ms"], 3),
+                                                       round(r["served_fp16"]["p99_ms"], 3)],
+                 "fp32_serial": [round(r["serial_fp32"]["volumes_per_s"], 1), round(r["serial_fp32"]["p50_ms"], 3),
+                                 round(r["serial_fp32"]["p99_ms"], 3)]} for r in sv.get("sweep", [])]
+
+    # the most read figures go last (a truncated tail of the line keeps them)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": max(3, args.warmup),
         "ms_per_step": step_mean_ms, "higher_is_better": True, "scaling": "weak",
@@ -872,34 +905,38 @@ def main():
                    "storage": args.storage, "scene": "10 points + 3 oriented patches, Poisson, peak log-uniform 1e2-1e4",
                    "l2": "no flush: each step moves >= 3.5 GB through a 2.2 GB workspace, far above the 129 MB L2",
                    "parallelism": f"replicas x{world}"},
-        "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "min": step_ms[0], "max": step_ms[-1]},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": sb[dom],
-                     "launch_ms": per_launch_ms[dom], "peak_source": peak_src},
-        "roofline_pipeline": {"bytes_model": "104 V (fused x/y) per volume" if args.storage == "f32" else "54 V",
-                              "bytes": pipe_bytes, "achieved": pipe_achieved, "peak": peak, "unit": "GB/s",
-                              "frac": pipe_achieved / peak},
-        "stages_ms_per_launch": per_launch_ms,
-        "autotuned_tiles": tiles,
-        "stage_bytes": sb,
-        "cpu_baseline": cpu,
-        "parity": parity,
-        "variants": variants,
-        "batch": extras.get("batch"),
-        "serving": extras.get("serving"),
-        "phasor_field": extras.get("phasor_field"),
+        # detail blocks
         "binning": extras.get("binning"),
         "post": extras.get("post"),
         "moe": extras.get("moe"),
         "cufft_reference": extras.get("cufft_reference"),
         "fk_small": extras.get("fk_small"),
+        "phasor_field_detail": extras.get("phasor_field"),
+        "batch_detail": extras.get("batch"),
+        "stage_bytes": sb,
+        "autotuned_tiles": tiles,
+        "cpu_baseline": cpu,
+        "parity": parity,
+        "variants": variants,
         "roofline_alu": stolt_alu,
+        "gpu_launches": K * len(per_launch_ms),
+        "clocks": clocks,
+        # headline figures
+        "latency_ms": {"p50": pct(0.50), "p99": pct(0.99), "min": step_ms[0], "max": step_ms[-1]},
+        "stages_ms_per_launch": per_launch_ms,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "algorithmic_bytes": sb[dom],
+                     "launch_ms": per_launch_ms[dom], "peak_source": peak_src},
+        "roofline_pipeline": {"bytes_model": "104 V per volume" if args.storage == "f32" else "54 V",
+                              "bytes": pipe_bytes, "achieved": pipe_achieved, "peak": peak, "unit": "GB/s",
+                              "frac": pipe_achieved / peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "steps": Ke,
                 "h2d_bytes_per_step": plan.input_bytes, "d2h_bytes_per_step": plan.output_bytes,
                 "path": "nlos_reconstruct_host_many (copies in/out overlap reconstruction), pinned host buffers",
                 "single_call_volumes_per_s": e2e_single},
-        "gpu_launches": K * (5 if args.storage == "f32" else 7),
-        "clocks": clocks,
+        "batch": compact_batch(extras.get("batch")),
+        "phasor_field": compact_pf(extras.get("phasor_field")),
+        "serving_vol_s_p50_p99": compact_serving(extras.get("serving")),
     }
     print(json.dumps(line), flush=True)
     if dist:

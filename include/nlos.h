@@ -123,6 +123,12 @@ nlos_status_t nlos_plan_create(const nlos_plan_desc_t* desc, nlos_plan_t* out);
  * default workspace (the plan is then used only through nlos_reconstruct_ws,
  * batches or a server, which provide their own). */
 #define NLOS_PLAN_NO_WORKSPACE 1
+/* NLOS_PLAN_SEPARATE_AXES: run the f-k lateral transforms as four separate
+ * passes (x forward, y forward, y inverse, x inverse) even where the fused
+ * pairs apply (zero-padded f-k with Lx = Ly <= 1024 and nt a multiple of 16:
+ * x then y forward in one launch, y then x inverse in another, each pair's
+ * intermediate kept in L2). Same arithmetic; for comparison and testing. */
+#define NLOS_PLAN_SEPARATE_AXES 2
 nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_plan_t* out);
 
 /*

@@ -29,11 +29,6 @@ inline cudaError_t axis_report(const char* path, int L, int ic, int threads, siz
   return e;
 }
 
-template <class TS> struct RealOf;
-template <> struct RealOf<float2> { using T = float; };
-template <> struct RealOf<__half2> { using T = __half; };
-template <> struct RealOf<__nv_bfloat162> { using T = __nv_bfloat16; };
-
 template <int L, int IC_> struct AxisTile {
   static constexpr int IC = IC_;
   static constexpr int THREADS = IC * (L / 16);

@@ -47,6 +47,19 @@ cudaError_t launch_axis_fft(const AxisLaunch& l, cudaStream_t s) {
   return fn[l.storage][l.L <= 64 ? 0 : l.L <= 256 ? 1 : 2](l, s);
 }
 
+cudaError_t launch_fk_chain_f32(const FkChainLaunch& l, cudaStream_t s);
+cudaError_t launch_fk_chain_f16(const FkChainLaunch& l, cudaStream_t s);
+cudaError_t launch_fk_chain_bf16(const FkChainLaunch& l, cudaStream_t s);
+
+cudaError_t launch_fk_chain(const FkChainLaunch& l, int storage, cudaStream_t s) {
+  switch (storage) {
+    case kF32: return launch_fk_chain_f32(l, s);
+    case kF16: return launch_fk_chain_f16(l, s);
+    case kBF16: return launch_fk_chain_bf16(l, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s) {
   static cudaError_t (*const fn[3][3])(const FkZParams&, int, cudaStream_t) = {
       {launch_fk_zstage_f32_r0, launch_fk_zstage_f32_r1, launch_fk_zstage_f32_r2},
@@ -131,6 +144,7 @@ struct nlos_plan_s {
   int storage = kF32;
   int nz = 0;
   std::map<int, float2*> tw;            // twiddle table per FFT length
+  std::map<int, float2*> tw32;          // twiddles of the radix-32 schedule (32 values per thread)
   // f-k Stolt constants
   float2* ax = nullptr;
   float2* ay = nullptr;
@@ -158,6 +172,8 @@ struct nlos_plan_s {
   // workspace layout: up to three complex buffers + scale scalars + partials
   size_t off[3] = {0, 0, 0};
   size_t off_scal = 0, off_part = 0;
+  size_t off_sync = 0;                  // chunk counters of the fused lateral f-k stages
+  bool fused = false;                   // f-k lateral transforms fused in pairs (fk_chain.cuh)
   size_t ws_bytes = 0;
   void* ws = nullptr;
   // host-call staging
@@ -215,13 +231,14 @@ nlos_status_t upload(nlos_plan_s* p, T** dst, const std::vector<T>& src, const c
 // Stockham pass twiddle tables of an L-point transform (same schedule as
 // FftShape<L>): for pass p with span Ns and radix R, T_p[r Ns + k] =
 // exp(-2 pi i k r / (Ns R)), float64 then rounded to float.
-std::vector<float2> make_twiddles(int L) {
-  const int LOG = ilog2i(L), NFULL = LOG / 4, REM = LOG % 4;
+std::vector<float2> make_twiddles(int L, int E = 16) {
+  const int LE = E == 32 ? 5 : 4;
+  const int LOG = ilog2i(L), NFULL = LOG / LE, REM = LOG % LE;
   const int npass = NFULL + (REM ? 1 : 0);
   std::vector<float2> t;
   int span = 1;
   for (int pss = 0; pss < npass; ++pss) {
-    const int R = pss < NFULL ? 16 : (1 << REM);
+    const int R = pss < NFULL ? E : (1 << REM);
     for (int r = 0; r < R; ++r)
       for (int k = 0; k < span; ++k) {
         const long long m = (long long)k * r;           // exponent over span*R
@@ -235,10 +252,17 @@ std::vector<float2> make_twiddles(int L) {
 
 nlos_status_t ensure_twiddles(nlos_plan_s* p, int L) {
   if (p->tw.count(L)) return NLOS_OK;
+  const std::vector<float2> t = make_twiddles(L);
   float2* d = nullptr;
-  nlos_status_t st = upload(p, &d, make_twiddles(L), "twiddle upload");
+  nlos_status_t st = upload(p, &d, t, "twiddle upload");
   if (st != NLOS_OK) return st;
   p->tw[L] = d;
+  // radix-32 schedule (32 values per thread)
+  if (L >= 32) {
+    float2* d32 = nullptr;
+    if ((st = upload(p, &d32, make_twiddles(L, 32), "twiddle upload")) != NLOS_OK) return st;
+    p->tw32[L] = d32;
+  }
   return NLOS_OK;
 }
 
@@ -287,7 +311,8 @@ nlos_status_t build_fk(nlos_plan_s* p) {
   p->off[2] = p->off[1] + align256(b1);
   p->off_scal = p->off[2] + align256(b2);
   p->off_part = p->off_scal + 256;
-  p->ws_bytes = p->off_part + align256(sizeof(float) * kScalePartials);
+  p->off_sync = p->off_part + align256(sizeof(float) * kScalePartials);
+  p->ws_bytes = p->off_sync + align256(sizeof(int) * (2 + n / 16));
   p->nz = p->n;
   return NLOS_OK;
 }
@@ -536,7 +561,8 @@ nlos_status_t pf_finish(nlos_plan_s* p, const std::vector<float>& w) {
   p->off[2] = p->off[1] + align256(b1);
   p->off_scal = p->off[2] + align256(b2);
   p->off_part = p->off_scal + 256;
-  p->ws_bytes = p->off_part + align256(sizeof(float) * kScalePartials);
+  p->off_sync = p->off_part + align256(sizeof(float) * kScalePartials);
+  p->ws_bytes = p->off_sync + 256;
   p->nz = p->D;
   return NLOS_OK;
 }
@@ -619,6 +645,26 @@ void attach_tmap(AxisLaunch& l) {
     l.has_tmap = 1;
 }
 
+// 3D tiled map over `base` with dims (d0 contiguous, d1, d2), byte strides
+// s1, s2 of dims 1 and 2, box (b0, b1, 1) of `elem`-byte elements.
+bool encode_3d(CUtensorMap* m, const void* base, size_t elem, unsigned long long d0, unsigned long long d1,
+               unsigned long long d2, unsigned long long s1, unsigned long long s2, unsigned b0, unsigned b1,
+               bool promote) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  if (s1 % 16 || s2 % 16 || (b0 * elem) % 16 || reinterpret_cast<uintptr_t>(base) % 16) return false;
+  const CUtensorMapDataType dt = elem == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                               : elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                           : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+  const cuuint64_t dims[3] = {d0, d1, d2};
+  const cuuint64_t strides[2] = {s1, s2};
+  const cuuint32_t box[3] = {b0, b1, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(m, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, promote ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 AxisLaunch axis(int storage, int L, long long n_outer, const void* in, void* out, long long inner,
                 long long in_outer, long long in_axis, long long out_outer, long long out_axis, int L_in,
                 int L_out, int inverse, float scale, const float2* tw, int tile) {
@@ -668,8 +714,52 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   }
   const long long pf = p->d.pad_factor, Lx = p->Lx, Ly = p->Ly, Lt = p->Lt, hx = Lx / 2 + 1;
   const float g2a = pass_scale(st, (int)Lx), g2b = pass_scale(st, (int)Ly), g2n = pass_scale(st, (int)Lt);
+  // inverse normalisation: pass scales applied before the last transform (it applies none of its own)
+  const double N = (double)Lx * Ly * Lt;
+  const double gprod = (double)g2a * g2b * g2n * g2n * g2b;
+  const bool cpx = p->d.output == NLOS_OUT_COMPLEX;
+  const float fscale = (float)(cpx ? 1.0 / (N * gprod) : 1.0 / (N * N * gprod * gprod));
+  FkChainParams ch{};
+  int* sync = reinterpret_cast<int*>(ws + p->off_sync);
+  const size_t sync_bytes = sizeof(int) * (size_t)(1 + n / 16);
+  const size_t cb = complex_bytes(st), rb = real_bytes(st);
+  if (p->fused) {
+    ch.tw = p->tw32[(int)Lx];   // radix-32 schedule
+    ch.a = (int)a;
+    ch.b = (int)b;
+    ch.n = (int)n;
+    ch.L = (int)Lx;
+    ch.nchunks = (int)(n / 16);
+    ch.sync = sync;
+    ch.err = err;
+    ch.discard = 0;   // per stage below (variant 0 on float32 storage)
+  }
+  AxisLaunch l{};
+  if (p->fused) {
+    // FK1 fused: x forward (real input, t/(n-1), zero-padded, kx in [0, Lx/2]) then y forward
+    FkChainLaunch c{};
+    c.p = ch;
+    c.p.in = H;
+    c.p.mid = b0;
+    c.p.out = b1;
+    c.p.t_scale = 1.0f / (float)(n - 1);
+    c.p.s1 = g2a;
+    c.p.s2 = g2b;
+    c.p.ld_dev_scale = s_in;
+    c.p.discard = st == kF32 && p->tiles[sid] < 2;
+    c.nslot = p->tiles[sid] % 2 == 0 ? 3 : 2;
+    c.fwd = 1;
+    // x items: 16 real t columns of one wall row, a rows; y items: 8 complex columns of one kx, b rows
+    if (!encode_3d(&c.map1, H, rb, (unsigned long long)(b * n), a, 1, b * n * rb, a * b * n * rb, 16,
+                   (unsigned)std::min<long long>(a, 256), true) ||
+        !encode_3d(&c.map2, b0, cb, n, b, hx, n * cb, b * n * cb, 8, (unsigned)std::min<long long>(b, 256), false))
+      return fail(NLOS_ERR_CUDA, "fk xy-forward: tensor map encoding failed");
+    NLOS_CU(cudaMemsetAsync(sync, 0, sync_bytes, s), "fk chain counters");
+    NLOS_CU(launch_fk_chain(c, st, s), "fk xy-forward");
+    NLOS_MARK(p, s, sid++);
+  } else {
   // FK1: x forward (real input, scaled by t/(n-1), zero-padded to Lx, kx in [0, Lx/2])
-  AxisLaunch l = axis(st, (int)Lx, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)hx, 0, g2a, p->tw[(int)Lx], p->tiles[sid]);
+  l = axis(st, (int)Lx, 1, H, b0, b * n, 0, b * n, 0, b * n, (int)a, (int)hx, 0, g2a, p->tw[(int)Lx], p->tiles[sid]);
   // tiles [0, n): direct loads, two real columns per complex transform;
   // [n, 2n): TMA staging, one real column per transform; [2n, 3n): TMA
   // staging of column pairs (n column widths)
@@ -688,11 +778,13 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   attach_tmap(l);
   NLOS_CU(launch_axis_fft(l, s), "fk y-forward");
   NLOS_MARK(p, s, sid++);
+  }
   // FK3: t forward + Stolt + inverse along z for both Hermitian partners
   FkZParams z{};
   z.G = b1;
   z.psi = b2;
   z.tw = p->tw[(int)Lt];
+  z.tw32 = p->tw32.count((int)Lt) ? p->tw32[(int)Lt] : nullptr;
   z.ax = p->ax;
   z.ay = p->ay;
   z.a_pad = (int)Lx;
@@ -705,6 +797,30 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   z.st_scale = g2n;
   NLOS_CU(launch_fk_zstage(z, st, p->tiles[sid], s), "fk stolt stage");
   NLOS_MARK(p, s, sid++);
+  if (p->fused) {
+    // FK4 fused: y inverse (keep y < b) then x inverse (keep x < a) with |psi|^2
+    FkChainLaunch c{};
+    c.p = ch;
+    c.p.in = b2;
+    c.p.mid = b0;
+    c.p.out = vol;
+    c.p.s1 = g2b;
+    c.p.s2 = fscale;
+    c.p.st_dev_scale = cpx ? inv_s : inv_s2;
+    c.p.discard = st == kF32 && p->tiles[sid] < 2;
+    c.nslot = p->tiles[sid] % 2 == 0 ? 3 : 2;
+    c.fwd = 0;
+    c.store_mode = cpx ? kStoreCpx32 : kStoreAbs2;
+    // y items: 8 complex columns of one kx, Ly rows; x items: 8 complex columns of one wall row y, Lx rows
+    const unsigned box = (unsigned)std::min<long long>(Lx, 256);
+    if (!encode_3d(&c.map1, b2, cb, n, Ly, Lx, n * cb, Ly * n * cb, 8, box, true) ||
+        !encode_3d(&c.map2, b0, cb, n, Lx, b, b * n * cb, n * cb, 8, box, false))
+      return fail(NLOS_ERR_CUDA, "fk yx-inverse: tensor map encoding failed");
+    NLOS_CU(cudaMemsetAsync(sync, 0, sync_bytes, s), "fk chain counters");
+    NLOS_CU(launch_fk_chain(c, st, s), "fk yx-inverse");
+    NLOS_MARK(p, s, sid++);
+    return NLOS_OK;
+  }
   // FK4: y inverse (keep y < b)
   l = axis(st, (int)Ly, Lx, b2, b0, n, Ly * n, n, b * n, n, (int)Ly, (int)b, 1, g2b, p->tw[(int)Ly], p->tiles[sid]);
   l.err = err;
@@ -712,11 +828,6 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_CU(launch_axis_fft(l, s), "fk y-inverse");
   NLOS_MARK(p, s, sid++);
   // FK4: x inverse (keep x < a), |psi|^2 with the 1/(Lx Ly Lt) normalisation
-  const double N = (double)Lx * Ly * Lt;
-  // pass scales applied to the data before this last pass (it applies none of its own)
-  const double gprod = (double)g2a * g2b * g2n * g2n * g2b;
-  const bool cpx = p->d.output == NLOS_OUT_COMPLEX;
-  const float fscale = (float)(cpx ? 1.0 / (N * gprod) : 1.0 / (N * N * gprod * gprod));
   l = axis(st, (int)Lx, 1, b0, vol, b * n, 0, b * n, 0, b * n, (int)Lx, (int)a, 1, fscale, p->tw[(int)Lx], p->tiles[sid]);
   l.store_mode = cpx ? kStoreCpx32 : kStoreAbs2;
   l.p.st_dev_scale = cpx ? inv_s : inv_s2;
@@ -1069,32 +1180,40 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
     p->Lt = fk ? (pad == 1 ? p->n : pow2_at_least(2 * p->n)) : pow2_at_least(p->n);
   }
   p->storage = desc->storage;
+  p->fused = desc->method == NLOS_FK && !(flags & NLOS_PLAN_SEPARATE_AXES) &&
+             fk_chain_eligible(p->a, p->b, p->n, p->Lx, p->Ly, desc->pad_factor);
   if (p->storage != kF32) p->stage_names.push_back("volume_scale");
   const char* fk_names[] = {"fk_x_forward", "fk_y_forward", "fk_stolt_z", "fk_y_inverse", "fk_x_inverse"};
+  const char* fk_fused_names[] = {"fk_xy_forward", "fk_stolt_z", "fk_yx_inverse"};
   const char* pf_names[] = {"pf_band", "pf_y_forward", "pf_x_forward", "pf_depth_sum", "pf_y_inverse",
                             "pf_x_inverse"};
-  if (desc->method == NLOS_FK) for (const char* nm : fk_names) p->stage_names.push_back(nm);
+  if (desc->method == NLOS_FK && p->fused) for (const char* nm : fk_fused_names) p->stage_names.push_back(nm);
+  else if (desc->method == NLOS_FK) for (const char* nm : fk_names) p->stage_names.push_back(nm);
   else for (const char* nm : pf_names) p->stage_names.push_back(nm);
   for (const std::string& nm : p->stage_names) {
     const bool xs = nm.find("_x_") != std::string::npos, ys = nm.find("_y_") != std::string::npos;
     const bool umma = nm == "pf_depth_sum" && desc->method == NLOS_PHASOR_RSD &&
                       (desc->storage == NLOS_F16 || desc->storage == NLOS_F32);
-    p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : nm == "fk_stolt_z" ? 2 : umma ? 4 : 0);
+    const bool chain = nm == "fk_xy_forward" || nm == "fk_yx_inverse";
+    p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : nm == "fk_stolt_z" ? 2 : umma ? 4 : chain ? 5 : 0);
     p->stage_len.push_back(xs ? p->Lx : ys ? p->Ly : nm == "fk_stolt_z" ? p->Lt : 0);
   }
   // default launch shapes: TMA-staged axis transforms (each falls back to
   // direct loads where the layout does not allow TMA); the autotuner may
   // choose others
   p->tiles.assign(p->stage_names.size(), 0);
-  for (size_t i = 0; i < p->tiles.size(); ++i)
+  for (size_t i = 0; i < p->tiles.size(); ++i) {
     if (p->stage_kind[i] == 1 || p->stage_kind[i] == 3) p->tiles[i] = axis_ic_count(p->stage_len[i]);
+    if (p->stage_kind[i] == 2) p->tiles[i] = fk_tile_default(p->stage_len[i]);
+    if (p->stage_kind[i] == 5) p->tiles[i] = 1;   // fused lateral pair: two slots, intermediate dropped from L2
+  }
   st = desc->method == NLOS_FK ? build_fk(p) : build_pf(p);
   // every stage buffer lies inside [0, ws_bytes): the regions are laid out in
   // order and the scalar area and partials close the workspace. Callers that
   // supply scratch (nlos_reconstruct_ws, the fixed array of
   // nlos_reconstruct_noalloc) size it by ws_bytes alone.
   if (st == NLOS_OK && !(p->off[0] <= p->off[1] && p->off[1] <= p->off[2] && p->off[2] <= p->off_scal &&
-                         p->off_scal + 256 <= p->off_part && p->off_part < p->ws_bytes))
+                         p->off_scal + 256 <= p->off_part && p->off_part < p->off_sync && p->off_sync < p->ws_bytes))
     st = fail(NLOS_ERR_UNSUPPORTED, "internal: workspace layout out of order");
   const bool own_ws = !(flags & NLOS_PLAN_NO_WORKSPACE);
   if (st == NLOS_OK && own_ws) st = dalloc(p, &p->ws, p->ws_bytes, "workspace");
@@ -1390,6 +1509,8 @@ int stage_variants(const nlos_plan_s* p, size_t i) {
   if (p->stage_kind[i] == 2) return fk_tile_count(p->stage_len[i]);
   if (p->stage_kind[i] == 3) return 3 * axis_ic_count(p->stage_len[i]);
   if (p->stage_kind[i] == 4) return 3;   // tensor cores (persistent), FFMA, tensor cores (CTA per tile)
+  // fused lateral pair: {3, 2} slots per CTA x {intermediate dropped from L2 after use, kept}
+  if (p->stage_kind[i] == 5) return 4;
   return 1;
 }
 }  // namespace

@@ -1,8 +1,8 @@
 // Device-side FFT building blocks for the NLOS kernels (sm_103a).
 //
 // Every transform here is a power-of-two Stockham FFT (self-sorting, natural
-// order in and out) executed by TPC = L/16 threads, each holding 16 complex
-// values in registers. A pass of radix R (16, or 8/4/2 for the remainder)
+// order in and out) executed by TPC = L/E threads, each holding E = 16 or 32
+// complex values in registers. A pass of radix R (E, or a smaller power of two for the remainder)
 // gathers R values per butterfly at stride L/R, multiplies by the pass
 // twiddles W_{Ns R}^{k r}, runs an in-register radix-R DFT and scatters to
 // (j/Ns) Ns R + j%Ns + r Ns. Between passes data goes through shared memory
@@ -132,16 +132,20 @@ template <int R> struct Dft {
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
 
-template <int L> struct FftShape {
-  static_assert(L >= 16 && (L & (L - 1)) == 0, "power-of-two length >= 16");
-  static constexpr int E = 16;            // complex values held per thread
+// E complex values per thread (16: radix-16 passes, 32: radix-32 passes; a
+// radix-2^(log2 L mod log2 E) remainder pass closes the schedule)
+template <int L, int E_ = 16> struct FftShape {
+  static_assert(L >= E_ && (L & (L - 1)) == 0, "power-of-two length >= E");
+  static_assert(E_ == 16 || E_ == 32, "16 or 32 values per thread");
+  static constexpr int E = E_;            // complex values held per thread
+  static constexpr int LE = ilog2c(E_);
   static constexpr int TPC = L / E;       // threads per transform
   static constexpr int LOG = ilog2c(L);
-  static constexpr int NFULL = LOG / 4;
-  static constexpr int REM = LOG % 4;
+  static constexpr int NFULL = LOG / LE;
+  static constexpr int REM = LOG % LE;
   static constexpr int NPASS = NFULL + (REM ? 1 : 0);
-  static constexpr int SMEM = L + L / 16;  // padded shared-memory elements per transform
-  __host__ __device__ static constexpr int radix(int p) { return p < NFULL ? 16 : (1 << REM); }
+  static constexpr int SMEM = L + L / E;  // padded shared-memory elements per transform
+  __host__ __device__ static constexpr int radix(int p) { return p < NFULL ? E : (1 << REM); }
   __host__ __device__ static constexpr int span(int p) { return p == 0 ? 1 : span(p - 1) * radix(p - 1); }
   __host__ __device__ static constexpr int twoff(int p) {
     return p == 0 ? 0 : twoff(p - 1) + span(p - 1) * radix(p - 1);
@@ -149,9 +153,31 @@ template <int L> struct FftShape {
   static constexpr int TWSIZE = twoff(NPASS);
 };
 
-// One padding element per 16 keeps the radix-16 scatter of the first pass
-// (stride 16) and the contiguous gathers free of bank conflicts.
+// Barrier between the passes of a transform: the whole CTA, or - for a
+// context that declares kBarThreads - the warp (kBarThreads = 32: every
+// transform of the context lies within one warp) or named barrier 1 over the
+// first kBarThreads threads (warp-specialised kernels whose other warps do
+// not take part in the transforms).
+template <class C, class = void> struct CtxBar {
+  static constexpr int threads = 0;
+};
+template <class C> struct CtxBar<C, decltype((void)C::kBarThreads)> {
+  static constexpr int threads = C::kBarThreads;
+};
+template <class Ctx> __device__ __forceinline__ void fft_sync() {
+  if constexpr (CtxBar<Ctx>::threads == 0) {
+    __syncthreads();
+  } else if constexpr (CtxBar<Ctx>::threads == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync 1, %0;" ::"r"(CtxBar<Ctx>::threads) : "memory");
+  }
+}
+
+// One padding element per 16 (per E) keeps the radix-16 (radix-E) scatter of
+// the first pass (stride E) and the contiguous gathers free of bank conflicts.
 __device__ __forceinline__ int pad16(int l) { return l + (l >> 4); }
+template <int E> __device__ __forceinline__ int padE(int l) { return l + l / E; }
 
 // Radix-16 DFT whose inputs 8..15 are zero (first pass of a transform whose
 // upper half is zero padding): the first radix-4 stage sees (x0, x1, 0, 0).
@@ -179,6 +205,52 @@ __device__ __forceinline__ void dft16_half(float2* v) {
   }
 }
 
+// Radix-8 and radix-32 DFTs whose upper half of inputs is zero (first pass of
+// a radix-32 transform whose upper half is zero padding). Radix 8 = 2 x 4:
+// the radix-4 DFTs see (x0, x1, 0, 0); radix 32 = 4 x 8 with the radix-8
+// DFTs pruned that way.
+__device__ __forceinline__ void dft8_half(float2* v) {
+  float2 y[2][4];
+#pragma unroll
+  for (int n1 = 0; n1 < 2; ++n1) {
+    const float2 x0 = v[n1], x1 = v[n1 + 2];
+    const float2 mi = cmul_mi(x1);
+    y[n1][0] = cadd(x0, x1);
+    y[n1][2] = csub(x0, x1);
+    y[n1][1] = cadd(x0, mi);
+    y[n1][3] = csub(x0, mi);
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) y[n1][k2] = mul_w32(y[n1][k2], 4 * n1 * k2);
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 t[2] = {y[0][k2], y[1][k2]};
+    Dft<2>::run(t);
+    v[k2] = t[0];
+    v[k2 + 4] = t[1];
+  }
+}
+__device__ __forceinline__ void dft32_half(float2* v) {
+  float2 y[4][8];
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) {
+#pragma unroll
+    for (int n2 = 0; n2 < 8; ++n2) y[n1][n2] = v[n1 + 4 * n2];   // n2 >= 4 are the zero inputs
+    dft8_half(y[n1]);
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) y[n1][k2] = mul_w32(y[n1][k2], n1 * k2);
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < 8; ++k2) {
+    float2 t[4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) t[n1] = y[n1][k2];
+    Dft<4>::run(t);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) v[k2 + 8 * k1] = t[k1];
+  }
+}
+
 // Runs passes P..NPASS-1 of NT L-point transforms that share one schedule
 // (same thread mapping and twiddles) for one thread.
 //   kHalfIn:  inputs l >= L/2 are zero (not loaded; pruned first butterfly)
@@ -191,12 +263,12 @@ __device__ __forceinline__ void dft16_half(float2* v) {
 //   static constexpr int SSTRIDE
 //   static constexpr bool kSmemInput         load() reads the shared buffer the passes reuse
 //   const float2* tw                         twiddle table of the plan for length L
-template <int L, int NT, bool kHalfIn, bool kHalfOut, int P, class Ctx>
-__device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[NT][16]) {
-  using S = FftShape<L>;
+template <int L, int NT, bool kHalfIn, bool kHalfOut, int P, class Ctx, int E = 16>
+__device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[NT][E]) {
+  using S = FftShape<L, E>;
   constexpr int R = S::radix(P);
   constexpr int NS = S::span(P);
-  constexpr int BPT = 16 / R;
+  constexpr int BPT = E / R;
   constexpr int Q = L / R;
   constexpr int SS = Ctx::SSTRIDE;
   constexpr bool kFirst = (P == 0);
@@ -217,24 +289,24 @@ __device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[
           for (int t = 0; t < NT; ++t) v[t][i * R + r] = x[t];
         }
       }
-    } else if constexpr (Q % 16 == 0) {
-      const int pj = pad16(j) * SS;
+    } else if constexpr (Q % E == 0) {
+      const int pj = padE<E>(j) * SS;
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         const float2* s = ctx.sm(t) + pj;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[t][i * R + r] = s[r * (Q + Q / 16) * SS];
+        for (int r = 0; r < R; ++r) v[t][i * R + r] = s[r * (Q + Q / E) * SS];
       }
     } else {
 #pragma unroll
       for (int t = 0; t < NT; ++t)
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[t][i * R + r] = ctx.sm(t)[pad16(j + r * Q) * SS];
+        for (int r = 0; r < R; ++r) v[t][i * R + r] = ctx.sm(t)[padE<E>(j + r * Q) * SS];
     }
   }
   // in-place: every read of this pass completes before the first write (a
   // first pass whose input was staged in the same shared buffer needs it too)
-  if constexpr (!kFirst || Ctx::kSmemInput) __syncthreads();
+  if constexpr (!kFirst || Ctx::kSmemInput) fft_sync<Ctx>();
 #pragma unroll
   for (int i = 0; i < BPT; ++i) {
     const int j = j0 + i * S::TPC;
@@ -250,6 +322,7 @@ __device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
       if constexpr (kFirst && kHalfIn && R == 16) dft16_half(&v[t][i * R]);
+      else if constexpr (kFirst && kHalfIn && R == 32) dft32_half(&v[t][i * R]);
       else Dft<R>::run(&v[t][i * R]);
     }
   }
@@ -266,39 +339,39 @@ __device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[
         for (int t = 0; t < NT; ++t) x[t] = v[t][i * R + r];
         ctx.store(base + r * NS, x);
       }
-    } else if constexpr (NS == 1 && R == 16) {
-      const int pb = 17 * j * SS;          // pad16(16 j + r) = 17 j + r
+    } else if constexpr (NS == 1 && R == E) {
+      const int pb = (E + 1) * j * SS;     // padE(E j + r) = (E + 1) j + r
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         float2* s = ctx.sm(t) + pb;
 #pragma unroll
         for (int r = 0; r < R; ++r) s[r * SS] = v[t][i * R + r];
       }
-    } else if constexpr (NS % 16 == 0) {
-      const int pb = pad16(base) * SS;
+    } else if constexpr (NS % E == 0) {
+      const int pb = padE<E>(base) * SS;
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         float2* s = ctx.sm(t) + pb;
 #pragma unroll
-        for (int r = 0; r < R; ++r) s[r * (NS + NS / 16) * SS] = v[t][i * R + r];
+        for (int r = 0; r < R; ++r) s[r * (NS + NS / E) * SS] = v[t][i * R + r];
       }
     } else {
 #pragma unroll
       for (int t = 0; t < NT; ++t)
 #pragma unroll
-        for (int r = 0; r < R; ++r) ctx.sm(t)[pad16(base + r * NS) * SS] = v[t][i * R + r];
+        for (int r = 0; r < R; ++r) ctx.sm(t)[padE<E>(base + r * NS) * SS] = v[t][i * R + r];
     }
   }
   if constexpr (!kLast) {
-    __syncthreads();
-    fftn_passes<L, NT, kHalfIn, kHalfOut, P + 1>(ctx, j0, v);
+    fft_sync<Ctx>();
+    fftn_passes<L, NT, kHalfIn, kHalfOut, P + 1, Ctx, E>(ctx, j0, v);
   }
 }
 
-template <int L, int NT, bool kHalfIn, bool kHalfOut, class Ctx>
+template <int L, int NT, bool kHalfIn, bool kHalfOut, class Ctx, int E = 16>
 __device__ __forceinline__ void fftn_run(Ctx& ctx, const int j0) {
-  float2 v[NT][16];
-  fftn_passes<L, NT, kHalfIn, kHalfOut, 0>(ctx, j0, v);
+  float2 v[NT][E];
+  fftn_passes<L, NT, kHalfIn, kHalfOut, 0, Ctx, E>(ctx, j0, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -317,6 +390,12 @@ template <> struct Cpx<__nv_bfloat162> {
   static __device__ __forceinline__ float2 get(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
   static __device__ __forceinline__ void put(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
 };
+
+// real element type of each complex storage type
+template <class TS> struct RealOf;
+template <> struct RealOf<float2> { using T = float; };
+template <> struct RealOf<__half2> { using T = __half; };
+template <> struct RealOf<__nv_bfloat162> { using T = __nv_bfloat16; };
 
 template <class T> struct Real;
 template <> struct Real<float> {

@@ -66,8 +66,14 @@ __host__ __device__ constexpr int axis_ic_count(int L) { return (L >= 128 && L <
 __host__ __device__ constexpr int axis_tile_count(int L) { return 2 * axis_ic_count(L); }
 // error codes written to the device error word
 constexpr int kDevErrTmaTimeout = 1;
-// number of pencils-per-CTA variants of the f-k temporal stage of length L = 2n
-__host__ __device__ constexpr int fk_tile_count(int L) { return 4; }
+constexpr int kDevErrChainTimeout = 2;    // a fused lateral stage gave up waiting for a chunk
+// launch-shape variants of the f-k temporal stage of length L: 0-3 one pencil
+// and its partner per thread group (two CTA sizes, with or without aliased
+// buffers), 4 one warp per radix-32 transform (the pencils (kx, +-ky) and
+// their partners in one CTA); the default at L = 1024 is 2
+// (variant 4 exists for L = 1024 only: one transform of 32 values per thread is one warp)
+__host__ __device__ constexpr int fk_tile_count(int L) { return L == 1024 ? 5 : 4; }
+__host__ __device__ constexpr int fk_tile_default(int L) { return L == 1024 ? 2 : 0; }
 
 // f-k temporal-frequency stage: forward length-2n FFT of each stored pencil
 // G[kx][ky][0..n) (kx in [0, a], ky in [0, 2b)), Stolt resampling with the
@@ -78,6 +84,7 @@ struct FkZParams {
   const void* G;
   void* psi;
   const float2* tw;            // twiddles for the temporal length L
+  const float2* tw32;          // twiddles of the radix-32 schedule for L (warp-per-transform variant)
   const float2* ax;            // [a_pad] float-float (hi, lo) of (L s_x p~ / a_pad)^2
   const float2* ay;            // [b_pad] float-float of (L s_y q~ / b_pad)^2
   int a_pad, b_pad, n;         // padded lateral lengths, time bins (pencil stride, kept outputs)
@@ -89,6 +96,43 @@ struct FkZParams {
   float st_scale;              // multiplies stored values
 };
 cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s);
+
+// f-k lateral transforms fused in pairs (fk_chain.cuh):
+//   forward: in = H [a][b][n] real, mid = [L/2 + 1][b][n], out = G [L/2 + 1][L][n]
+//   inverse: in = psi [L][L][n], mid = [L][b][n], out = [a][b][n] float
+//            (|.|^2) or float2 (complex)
+struct FkChainParams {
+  const void* in;
+  void* mid;
+  void* out;
+  const float2* tw;            // twiddles for L
+  int a, b, n, L;
+  int nchunks;                 // n / 16
+  int lag;                     // chunks between a chunk's first- and second-transform tickets (set by the launcher)
+  float t_scale;               // forward: ramp factor 1/(n-1) (value * t * t_scale)
+  float s1, s2;                // scales of the values the first / second transform stores
+  const float* ld_dev_scale;   // forward: optional device scalar multiplying the input
+  const float* st_dev_scale;   // inverse: optional device scalar multiplying the output
+  int* sync;                   // [1 + nchunks] ints, zero at launch: ticket, finished first-transform items per chunk
+  int* err;                    // device error word
+  int discard;                 // drop consumed lines of `mid` from L2 (float32 storage)
+};
+struct FkChainLaunch {
+  FkChainParams p;
+  CUtensorMap map1, map2;      // TMA maps of the first / second transform's input
+  int fwd;                     // 1 forward, 0 inverse
+  int store_mode;              // inverse: kStoreAbs2 or kStoreCpx32
+  int nslot;                   // shared-memory slots per CTA (2 or 3; 2 at L = 1024)
+};
+cudaError_t launch_fk_chain(const FkChainLaunch& l, int storage, cudaStream_t s);
+// zero-padded f-k with Lx = Ly = L in [128, 1024] (at least one warp of
+// transforming threads per CTA), n a multiple of 16, and every TMA box row
+// count (a, b, L) at most 256 or a multiple of it
+inline bool fk_chain_eligible(int a, int b, int n, int Lx, int Ly, int pad) {
+  auto rows_ok = [](int r) { return r <= 256 || r % 256 == 0; };
+  return pad == 2 && Lx == Ly && Lx >= 128 && Lx <= 1024 && 2 * a <= Lx && 2 * b <= Ly && n % 16 == 0 && n >= 16 &&
+         rows_ok(a) && rows_ok(b);
+}
 
 // Phasor-field temporal band transform: per wall pencil H[x][y][0..n) (real),
 // length-n DFT, keep bins k_lo..k_lo+F-1, multiply by w(f): P[x][y][f].

@@ -20,6 +20,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CUDA", 4: "UNSUPPOR
 METHODS = {"fk": NLOS_FK, "pf": NLOS_PHASOR_RSD, "phasor": NLOS_PHASOR_RSD, "pf_dense": NLOS_PHASOR_DENSE}
 STORAGES = {"f32": NLOS_F32, "f16": NLOS_F16, "bf16": NLOS_BF16}
 OUTPUTS = {"magnitude": 0, "complex": 1}
+PLAN_NO_WORKSPACE, PLAN_SEPARATE_AXES = 1, 2
 
 EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nlos_reconstruct",
             "nlos_reconstruct_ws", "nlos_reconstruct_host", "nlos_reconstruct_batch",
@@ -188,14 +189,16 @@ class Plan:
     """A reconstruction plan (owns device tables and a default workspace)."""
 
     def __init__(self, nx: int, ny: int, nt: int, bin_width_s: float, wall_w_m: float, wall_h_m: float,
-                 method: str = "fk", storage: str = "f32", pad_factor: int = 2, **kw):
+                 method: str = "fk", storage: str = "f32", pad_factor: int = 2, separate_axes: bool = False,
+                 **kw):
         lib = load_library()
         d = make_desc(nx, ny, nt, bin_width_s, wall_w_m, wall_h_m, method, storage, pad_factor, **kw)
         self.desc = d
         self.method = method
         self.storage = storage
         h = ctypes.c_void_p()
-        _check(lib.nlos_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        flags = PLAN_SEPARATE_AXES if separate_axes else 0
+        _check(lib.nlos_plan_create_ex(ctypes.byref(d), flags, ctypes.byref(h)))
         self._h = h
         shape = (ctypes.c_size_t * 3)()
         ws, ib, ob = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_size_t()

@@ -98,11 +98,12 @@ def test_autotune_picks_valid_shapes_and_caches():
     g = synth.Geometry(64, 64, 256, 32e-12, 1.0, 1.0)
     plan = nlos.plan_for_capture(g, "fk", "f32")
     tiles = plan.autotune()
-    assert len(tiles) == 5 and all(t >= 0 for t in tiles)
+    # fused lateral pairs (3 stages) where they apply, else the 5 separate passes
+    assert len(tiles) == len(plan.tiles) in (3, 5) and all(t >= 0 for t in tiles)
     cap = synth.make_capture("fk_32x32x256", 0, geom=g)
     x = to_device(cap.counts, torch.float32)
     tuned = plan.reconstruct(x).clone()
-    plan.tiles = [0] * 5
+    plan.tiles = [0] * len(tiles)
     other = plan.reconstruct(x)
     assert float(torch.linalg.vector_norm((other - tuned).double()) / torch.linalg.vector_norm(tuned.double())) <= 1e-6
     plan2 = nlos.plan_for_capture(g, "fk", "f32")

@@ -209,3 +209,44 @@ def test_fk_any_size_fp16():
     got = _gpu(plan, cap.counts)
     ref = _oracle(geom, exact_input(cap.counts, torch.float16))
     assert rel_l2(got, ref) <= 2e-3
+
+
+FUSED = [
+    (synth.Geometry(48, 64, 256, 32e-12, 1.0, 1.2), "f32", "magnitude"),     # L = 128, a not a power of two
+    (synth.Geometry(64, 48, 160, 24e-12, 1.2, 0.9), "f32", "magnitude"),     # Lx = Ly = 128, b not a power of two
+    (synth.Geometry(128, 128, 512, 16e-12, 2.0, 2.0), "f32", "magnitude"),   # L = 256
+    (synth.Geometry(200, 256, 64, 32e-12, 1.6, 2.0), "f32", "magnitude"),    # L = 512, a not a power of two
+    (synth.Geometry(64, 64, 256, 32e-12, 1.0, 1.0), "f32", "complex"),
+    (synth.Geometry(128, 128, 256, 16e-12, 2.0, 2.0), "f16", "magnitude"),
+]
+
+
+@pytest.mark.parametrize("geom,storage,output", FUSED,
+                         ids=lambda v: f"{v.nx}x{v.ny}x{v.nt}" if hasattr(v, "nx") else str(v))
+def test_fk_fused_lateral_matches_separate(geom, storage, output):
+    """The fused x/y forward and y/x inverse stages (one launch each, the
+    intermediate kept in L2) give the volume of the four separate axis passes
+    (same arithmetic; float32 to rounding), and their chunk waits never run
+    out (device error word 0)."""
+    import ctypes
+    from paper_2608_28183_gb300 import nlos
+    cap = _noise_capture(geom, seed=geom.nx + geom.nt)
+    fused = nlos.plan_for_capture(geom, "fk", storage, output=output)
+    sep = nlos.plan_for_capture(geom, "fk", storage, output=output, separate_axes=True)
+    lib = nlos.load_library()
+    names = [lib.nlos_plan_stage_name(fused.handle, i).decode() for i in range(len(fused.tiles))]
+    assert "fk_xy_forward" in names and "fk_yx_inverse" in names
+    x = to_device(cap.counts, fused.input_dtype())
+    for _ in range(2):          # the second call reuses the counters cleared by the first
+        a = fused.reconstruct(x)
+    b = sep.reconstruct(x)
+    torch.cuda.synchronize()
+    code = ctypes.c_int(-1)
+    assert lib.nlos_workspace_check(fused.handle, None, ctypes.byref(code)) == 0 and code.value == 0
+    an, bn = a.cpu().numpy(), b.cpu().numpy()
+    err = rel_l2(an, bn)
+    assert err <= (1e-6 if storage == "f32" else 2e-3), err
+    if storage == "f32" and output == "magnitude":
+        ref = _oracle(geom, exact_input(cap.counts, torch.float32))
+        assert rel_l2(an.astype(np.float64), ref) <= 1e-5
+        assert same_peak(an, ref)
