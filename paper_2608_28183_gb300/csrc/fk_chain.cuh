@@ -96,6 +96,21 @@ struct ChainTmaPairCtx : AxisTmaPairCtx<L, IC, TS> {
     this->smem[padE<kChainE>(l) * IC + this->c] = x[0];
   }
 };
+// y inverse of the inverse chain: stores the intermediate with an L2
+// evict-last policy (it is read back within microseconds, then dropped)
+template <int L, int IC, class TS>
+struct ChainMidCtx : AxisTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> {
+  static constexpr int kBarThreads = ChainTile<L>::CONSUMERS;
+  uint64_t keep;
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
+    if (l >= this->L_out) return;
+    const float2 v = make_float2(x[0].x * this->stmul, -x[0].y * this->stmul);   // inverse: conjugate
+    TS* o = static_cast<TS*>(this->out) + this->out_base + l * this->out_axis;
+    if constexpr (sizeof(TS) == 8) st_global_hint(reinterpret_cast<float2*>(o), v, keep);
+    else Cpx<TS>::put(o, v);
+  }
+};
+
 template <int L> __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(ChainTile<L>::CONSUMERS) : "memory");
 }
@@ -167,6 +182,8 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
   if (threadIdx.x >= T::CONSUMERS) {
     // ------------------------------ producer ------------------------------
     if (threadIdx.x != T::CONSUMERS) return;
+    // the inverse's input spectrum is read once: keep L2 for the intermediate
+    const uint64_t once = l2_policy_evict_first();
     int t = -1, sub = 0;
     for (int k = 0;; ++k) {
       const int slot = k % NSLOT;
@@ -216,13 +233,16 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         unsigned char* dst = reinterpret_cast<unsigned char*>(buf(slot)) + (size_t)r0 * row_bytes;
         if (xreal)
           tma_load_3d(dst, &map1, &full[slot], it.idx * p.n + it.chunk * kChainCols, r0, 0);
+        else if (it.second)
+          tma_load_3d(dst, &map2, &full[slot], it.chunk * kChainCols + sub * IC, r0, it.idx);
         else
-          tma_load_3d(dst, it.second ? &map2 : &map1, &full[slot], it.chunk * kChainCols + sub * IC, r0, it.idx);
+          tma_load_3d_hint(dst, &map1, &full[slot], it.chunk * kChainCols + sub * IC, r0, it.idx, once);
       }
     }
   }
 
   // ------------------------------ consumers ------------------------------
+  const uint64_t keep = l2_policy_evict_last();
   const int c = threadIdx.x % IC;
   const int j0 = threadIdx.x / IC;
   const float ldm = p.ld_dev_scale ? *p.ld_dev_scale : 1.0f;
@@ -286,15 +306,16 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         fftn_run<L, 1, true, false, ChainTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS>, E>(ctx, j0);
       } else if (!it.second) {
         // y inverse of kx = idx: keep y < b
-        ChainTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> ctx;
+        ChainMidCtx<L, IC, TS> ctx;
         chain_ctx(ctx, buf(slot), p.tw, c, 1);
+        ctx.keep = keep;
         ctx.out = p.mid;
         ctx.out_base = (long long)it.idx * bn + col0 + c;
         ctx.out_axis = p.n;
         ctx.L_in = L;
         ctx.L_out = p.b;
         ctx.stmul = p.s1;
-        fftn_run<L, 1, false, true, ChainTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS>, E>(ctx, j0);
+        fftn_run<L, 1, false, true, ChainMidCtx<L, IC, TS>, E>(ctx, j0);
       } else {
         // x inverse of wall row y = idx: keep x < a, |.|^2 (or complex)
         ChainTmaCtx<L, IC, kLoadCpx, ST, TS> ctx;

@@ -750,8 +750,10 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     c.nslot = p->tiles[sid] % 2 == 0 ? 3 : 2;
     c.fwd = 1;
     // x items: 16 real t columns of one wall row, a rows; y items: 8 complex columns of one kx, b rows
+    // no L2 promotion: a wider fetch would pull in the next chunks' columns, whose
+    // items come hundreds of tickets later (evicted by then, read twice)
     if (!encode_3d(&c.map1, H, rb, (unsigned long long)(b * n), a, 1, b * n * rb, a * b * n * rb, 16,
-                   (unsigned)std::min<long long>(a, 256), true) ||
+                   (unsigned)std::min<long long>(a, 256), false) ||
         !encode_3d(&c.map2, b0, cb, n, b, hx, n * cb, b * n * cb, 8, (unsigned)std::min<long long>(b, 256), false))
       return fail(NLOS_ERR_CUDA, "fk xy-forward: tensor map encoding failed");
     NLOS_CU(cudaMemsetAsync(sync, 0, sync_bytes, s), "fk chain counters");
@@ -813,7 +815,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     c.store_mode = cpx ? kStoreCpx32 : kStoreAbs2;
     // y items: 8 complex columns of one kx, Ly rows; x items: 8 complex columns of one wall row y, Lx rows
     const unsigned box = (unsigned)std::min<long long>(Lx, 256);
-    if (!encode_3d(&c.map1, b2, cb, n, Ly, Lx, n * cb, Ly * n * cb, 8, box, true) ||
+    if (!encode_3d(&c.map1, b2, cb, n, Ly, Lx, n * cb, Ly * n * cb, 8, box, false) ||
         !encode_3d(&c.map2, b0, cb, n, Lx, b, b * n * cb, n * cb, 8, box, false))
       return fail(NLOS_ERR_CUDA, "fk yx-inverse: tensor map encoding failed");
     NLOS_CU(cudaMemsetAsync(sync, 0, sync_bytes, s), "fk chain counters");
