@@ -288,11 +288,14 @@ def batch_bench(torch, nlos, synth, reps=20):
             "max_rel_l2_fp16_vs_fp32": rel, "autotuned": True}
 
 
-def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000), seconds=2.0, budget_gb=120):
+def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000, 0), seconds=2.0, budget_gb=120, saturating_n=1000):
     """Poisson arrivals at each rate; each request a capture of side 32..256
     and 256/512/1024 bins, f-k or phasor at 50/50, FP16, through the
-    continuous-batching server (budget 120 GB, 8 slots); against the plain FP32
-    one-at-a-time path fed by the same arrivals."""
+    continuous-batching server (budget 120 GB for plans and workspaces, 8
+    slots); against the plain FP32 one-at-a-time path fed by the same
+    arrivals. Rate 0 is the saturating point: saturating_n requests offered at
+    once (more than either arm serves per second), so volumes/s measures
+    capacity."""
     import threading
     import numpy as np
     rng = np.random.Generator(np.random.PCG64(4000))
@@ -318,8 +321,12 @@ def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000), seconds=2.0, b
     torch.cuda.synchronize()
     results = []
     for rate in rates:
-        n = max(5, int(rate * seconds))
-        arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        if rate > 0:
+            n = max(5, int(rate * seconds))
+            arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        else:
+            n = saturating_n
+            arr = np.zeros(n)
         pick = rng.integers(0, len(pool), n)
         # continuous-batching server
         tickets = [None] * n
@@ -354,12 +361,14 @@ def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000), seconds=2.0, b
             lat.append((time.perf_counter() - t0 - arr[i]) * 1e3)
         span32 = time.perf_counter() - t0
         lat.sort()
-        results.append({"rate_rps": rate, "requests": n,
+        results.append({"rate_rps": rate if rate > 0 else "saturating", "requests": n,
                         "served_fp16": {"p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "volumes_per_s": n / span},
                         "serial_fp32": {"p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(n - 1, int(0.99 * (n - 1) + 0.5))],
                                         "volumes_per_s": n / span32}})
+    mem = server.memory()
     server.close()
-    return {"budget_gb": budget_gb, "slots": 8, "shapes": len(specs), "sweep": results}
+    return {"budget_gb": budget_gb, "slots": 8, "shapes": len(specs), "resident_plan_gb": mem["plan_bytes"] / 2**30,
+            "evictions": mem["evictions"], "sweep": results}
 
 
 _FFMA = []

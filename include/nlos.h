@@ -259,12 +259,17 @@ nlos_status_t nlos_batch_destroy(nlos_batch_t batch);
  * Continuous-batching server (Sec. 4.1's producer-consumer front end, served
  * from many clients). Requests of any description are queued by any thread
  * and served by one scheduler thread: plans are created once per distinct
- * description and stay resident; a request is admitted in arrival order as
- * soon as one of n_slots streams is free and its workspace (the padded
- * volume's footprint) fits in memory_budget_bytes next to the requests
- * already running; admitted requests overlap on the device. Workspaces come
- * from the stream-ordered allocator. Each result equals that of a standalone
- * nlos_reconstruct with the same description.
+ * description and stay resident; memory_budget_bytes covers the resident
+ * plans (tables, radial kernels, tensor-core operand stores, dense kernels)
+ * and the workspaces of running requests, and idle plans (no request queued
+ * or running) are evicted least recently used first when a new plan or an
+ * admission needs the room; a request is admitted in arrival order as soon
+ * as one of n_slots streams is free and its workspace (the padded volume's
+ * footprint) fits; admitted requests are launched outside the queue's lock
+ * and overlap on the device, and each signals its completion through a host
+ * function on its stream. Workspaces come from the stream-ordered
+ * allocator. Each result equals that of a standalone nlos_reconstruct with
+ * the same description.
  * Errors: INVALID_ARG (budget 0, slots outside [1, 64]), CUDA.
  */
 nlos_status_t nlos_server_create(size_t memory_budget_bytes, int n_slots, nlos_server_t* out);
@@ -276,8 +281,9 @@ nlos_status_t nlos_server_preload(nlos_server_t server, const nlos_plan_desc_t* 
  * Queue one request: transient/volume are caller-owned device buffers (input
  * ready when this is called, output valid once nlos_server_wait returns).
  * Creates the plan if the description is new (synchronous, stalls the
- * device). *ticket identifies the request. Errors: INVALID_ARG (NULL
- * arguments, invalid description), OUT_OF_MEMORY (workspace larger than the
+ * device; may wait for running requests to release plans it can evict).
+ * *ticket identifies the request. Errors: INVALID_ARG (NULL arguments,
+ * invalid description), OUT_OF_MEMORY (the plan and its workspace exceed the
  * whole budget), UNSUPPORTED, CUDA.
  */
 nlos_status_t nlos_server_submit(nlos_server_t server, const nlos_plan_desc_t* desc, const void* transient,
@@ -293,6 +299,15 @@ nlos_status_t nlos_server_wait(nlos_server_t server, uint64_t ticket, double tim
 /* Latency percentiles and throughput of the completed requests (optionally reset). */
 nlos_status_t nlos_server_stats(nlos_server_t server, double* p50_ms, double* p99_ms, double* volumes_per_s,
                                 unsigned long long* completed, int reset);
+
+/*
+ * Device memory the server accounts against its budget: the resident plans'
+ * tables and kernels (*plan_bytes), the workspaces of the requests on the
+ * device (*workspace_bytes), and how many idle plans it has evicted to make
+ * room (*evictions). Any pointer may be NULL. Errors: INVALID_ARG.
+ */
+nlos_status_t nlos_server_memory(nlos_server_t server, size_t* plan_bytes, size_t* workspace_bytes,
+                                 unsigned long long* evictions);
 
 /* Finish queued work, stop the scheduler, release plans and streams. */
 nlos_status_t nlos_server_destroy(nlos_server_t server);
@@ -456,6 +471,14 @@ nlos_status_t nlos_ffma_rate_launch(const float* params, float* sink, int blocks
  * NLOS_ERR_OUT_OF_MEMORY after releasing what it had allocated; k = 0
  * disables. Process-wide; not for production use. */
 void nlos_debug_fail_allocation(int k);
+
+/*
+ * Device memory the plan holds (its tables, twiddles, radial or dense kernel,
+ * tensor-core operand stores and, unless created with
+ * NLOS_PLAN_NO_WORKSPACE, its workspace; host-call staging once used).
+ * Errors: INVALID_ARG.
+ */
+nlos_status_t nlos_plan_memory(nlos_plan_t plan, size_t* resident_bytes);
 
 /* Release the plan's tables, workspace and staging buffers (synchronises the device). */
 nlos_status_t nlos_plan_destroy(nlos_plan_t plan);

@@ -181,6 +181,7 @@ struct nlos_plan_s {
   void* d_out = nullptr;
   struct HostPipe* pipe = nullptr;      // pipelined host calls (created on first use)
   std::vector<void*> allocs;
+  size_t resident = 0;                  // bytes of device memory the plan holds (tables, kernels, workspace)
   // per-stage tile variant (autotuner) and the transform length it applies to
   std::vector<int> tiles;
   std::vector<int> stage_len;     // 0: stage has no variants
@@ -215,6 +216,7 @@ nlos_status_t dalloc(nlos_plan_s* p, void** ptr, size_t bytes, const char* what)
     return cuda_fail(e, what);
   }
   p->allocs.push_back(*ptr);
+  p->resident += bytes ? bytes : 16;
   return NLOS_OK;
 }
 
@@ -1781,6 +1783,12 @@ const char* nlos_plan_stage_name(nlos_plan_t p, int i) {
   return p->stage_names[i].c_str();
 }
 
+nlos_status_t nlos_plan_memory(nlos_plan_t p, size_t* resident_bytes) {
+  if (!p || !resident_bytes) return fail(NLOS_ERR_INVALID_ARG, "plan and resident_bytes must be non-NULL");
+  *resident_bytes = p->resident;
+  return NLOS_OK;
+}
+
 nlos_status_t nlos_plan_destroy(nlos_plan_t p) {
   if (!p) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
   cudaDeviceSynchronize();
@@ -1802,6 +1810,7 @@ const char* nlos_version(void) { return "nlos-gb300 0.1 (sm_103a)"; }
 // Narrow accessors for entry points compiled in other files of the library.
 namespace nlos {
 size_t plan_workspace_bytes(const nlos_plan_s* p) { return p->ws_bytes; }
+size_t plan_resident_bytes(const nlos_plan_s* p) { return p->resident; }
 bool plan_profiling(const nlos_plan_s* p) { return p->prof_on; }
 nlos_status_t plan_run(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaStream_t s) {
   return run_plan(p, H, vol, ws, s);

@@ -2,18 +2,24 @@
 //
 // Requests (a capture description plus caller-owned device input and output
 // buffers) are queued by any thread and served by one scheduler thread:
-//   - plans are created once per distinct description and stay resident on
-//     the device (tables, twiddles, radial kernels) for the server's life;
+//   - plans are created once per distinct description (outside the queue's
+//     lock, so running work is not held up) and stay resident on the device;
+//   - the memory budget covers both the resident plans (tables, twiddles,
+//     radial kernels, tensor-core operand stores, dense kernels) and the
+//     workspaces of the requests on the device; a new plan that does not fit
+//     evicts idle plans (no request queued or running) in least-recently-used
+//     order;
 //   - a request is admitted, in arrival order, as soon as a slot (a stream)
-//     is free and its workspace (the padded volume's footprint) fits in the
-//     memory budget next to the requests already on the device;
-//   - admitted requests run on their slot's stream, so work that arrives while
-//     others are running overlaps with them on the GPU;
+//     is free and its workspace (the padded volume's footprint) fits in what
+//     the budget leaves next to the resident plans and running requests;
+//   - the scheduler launches outside the lock, on the slot's stream, so work
+//     that arrives while others run overlaps with them on the GPU;
 //   - workspaces come from the stream-ordered allocator (cudaMallocAsync /
 //     cudaFreeAsync on the slot's stream), so admissions never force a
 //     device-wide synchronisation;
-//   - completion is detected with events; a request's latency is the host time
-//     from submission to the scheduler observing its completion event.
+//   - completion is signalled by a host function enqueued behind each
+//     request on its stream (no polling); a request's latency is the host
+//     time from submission to that signal.
 // Each request's arithmetic is exactly that of a standalone reconstruction
 // with the same plan, so results are the same alone and in the mix.
 #include <algorithm>
@@ -35,6 +41,7 @@
 
 namespace nlos {
 size_t plan_workspace_bytes(const nlos_plan_s* p);
+size_t plan_resident_bytes(const nlos_plan_s* p);
 nlos_status_t plan_run(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaStream_t s);
 nlos_status_t set_error(nlos_status_t st, const char* msg);
 }  // namespace nlos
@@ -43,9 +50,16 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+struct PlanEntry {
+  nlos_plan_t plan = nullptr;
+  size_t bytes = 0;        // resident device memory of the plan
+  uint64_t last_use = 0;   // LRU stamp
+  int users = 0;           // requests queued or running with this plan
+};
+
 struct Request {
   uint64_t id = 0;
-  nlos_plan_t plan = nullptr;
+  PlanEntry* entry = nullptr;
   const void* in = nullptr;
   void* out = nullptr;
   size_t need = 0;
@@ -55,11 +69,16 @@ struct Request {
   int status = NLOS_OK;
 };
 
+struct Slot;
+struct Done {
+  nlos_server_s* sv = nullptr;
+  Slot* slot = nullptr;
+};
+
 struct Slot {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done = nullptr;
   Request* req = nullptr;
-  void* ws = nullptr;
+  Done done;
 };
 
 std::string desc_key(const nlos_plan_desc_t& d) {
@@ -74,9 +93,12 @@ std::string desc_key(const nlos_plan_desc_t& d) {
 
 struct nlos_server_s {
   size_t budget = 0;
-  size_t in_use = 0;
+  size_t in_use = 0;       // workspaces of running requests
+  size_t resident = 0;     // resident plans
+  uint64_t evictions = 0;
+  uint64_t lru = 0;
   std::vector<Slot> slots;
-  std::map<std::string, nlos_plan_t> plans;
+  std::map<std::string, PlanEntry*> plans;
   std::deque<Request*> queue;
   std::unordered_map<uint64_t, Request*> reqs;
   std::vector<double> latencies;
@@ -86,92 +108,111 @@ struct nlos_server_s {
   bool have_first = false;
   bool stop = false;
   int device = 0;
-  std::mutex mu;
+  std::mutex mu;           // queue, slots, accounting, plan entries
+  std::mutex plan_mu;      // serialises plan creation and eviction (device work, outside mu)
   std::condition_variable cv_work, cv_done;
   std::thread th;
 };
 
 namespace {
 
-// plan lookup/creation; called with the server lock held
-nlos_status_t get_plan(nlos_server_s* sv, const nlos_plan_desc_t& d, nlos_plan_t* out) {
-  const std::string key = desc_key(d);
-  auto it = sv->plans.find(key);
-  if (it != sv->plans.end()) {
-    *out = it->second;
-    return NLOS_OK;
-  }
-  nlos_plan_t p = nullptr;
-  nlos_status_t st = nlos_plan_create_ex(&d, NLOS_PLAN_NO_WORKSPACE, &p);
-  if (st != NLOS_OK) return st;
-  sv->plans[key] = p;
-  *out = p;
-  return NLOS_OK;
-}
-
+// Completion of a request; called with sv->mu held.
 void finish(nlos_server_s* sv, Slot& sl, bool ok) {
   Request* r = sl.req;
   const auto now = Clock::now();
   r->latency_ms = std::chrono::duration<double, std::milli>(now - r->t_submit).count();
   r->state = ok ? 2 : 3;
   sv->in_use -= r->need;
+  --r->entry->users;
   sv->latencies.push_back(r->latency_ms);
   ++sv->completed;
   sv->t_last = now;
   sl.req = nullptr;
-  sl.ws = nullptr;
+}
+
+// Host function behind each request on its slot's stream (a CUDA runtime
+// thread runs it; it makes no CUDA calls).
+void CUDART_CB on_done(void* arg) {
+  Done* d = static_cast<Done*>(arg);
+  nlos_server_s* sv = d->sv;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (d->slot->req) finish(sv, *d->slot, d->slot->req->status == NLOS_OK);
+  }
+  sv->cv_done.notify_all();
+  sv->cv_work.notify_one();
+}
+
+// Evict idle plans (least recently used first) until `extra` more bytes fit
+// in the budget; the evicted plans are appended to `victims` for the caller
+// to destroy outside the lock. Called with sv->mu held.
+void evict_idle(nlos_server_s* sv, size_t extra, std::vector<nlos_plan_t>& victims) {
+  while (sv->resident + sv->in_use + extra > sv->budget) {
+    auto victim = sv->plans.end();
+    for (auto it = sv->plans.begin(); it != sv->plans.end(); ++it)
+      if (it->second->users == 0 && (victim == sv->plans.end() || it->second->last_use < victim->second->last_use))
+        victim = it;
+    if (victim == sv->plans.end()) return;
+    victims.push_back(victim->second->plan);
+    sv->resident -= victim->second->bytes;
+    ++sv->evictions;
+    delete victim->second;
+    sv->plans.erase(victim);
+  }
 }
 
 void scheduler(nlos_server_s* sv) {
   cudaSetDevice(sv->device);
   std::unique_lock<std::mutex> lk(sv->mu);
+  std::vector<nlos_plan_t> victims;
   while (true) {
-    bool changed = false;
-    // completions
-    for (Slot& sl : sv->slots) {
-      if (!sl.req) continue;
-      const cudaError_t q = cudaEventQuery(sl.done);
-      if (q == cudaErrorNotReady) continue;
-      if (q != cudaSuccess) sl.req->status = NLOS_ERR_CUDA;
-      finish(sv, sl, q == cudaSuccess);
-      changed = true;
-    }
-    // admissions, in arrival order
-    while (!sv->queue.empty()) {
-      Request* r = sv->queue.front();
-      Slot* free_slot = nullptr;
+    // admit the head of the queue when a slot is free and its workspace fits
+    // (idle resident plans give way to it)
+    Request* r = nullptr;
+    Slot* slot = nullptr;
+    if (!sv->queue.empty()) {
+      Request* head = sv->queue.front();
       for (Slot& sl : sv->slots)
         if (!sl.req) {
-          free_slot = &sl;
+          slot = &sl;
           break;
         }
-      if (!free_slot || sv->in_use + r->need > sv->budget) break;
-      sv->queue.pop_front();
-      Slot& sl = *free_slot;
-      void* ws = nullptr;
-      cudaError_t e = cudaMallocAsync(&ws, r->need, sl.stream);
-      nlos_status_t st = e == cudaSuccess ? NLOS_OK : NLOS_ERR_OUT_OF_MEMORY;
-      if (st == NLOS_OK) st = nlos::plan_run(r->plan, r->in, r->out, ws, sl.stream);
-      if (ws) cudaFreeAsync(ws, sl.stream);
-      if (st == NLOS_OK && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) st = NLOS_ERR_CUDA;
-      r->state = 1;
-      sl.req = r;
-      sl.ws = ws;
-      sv->in_use += r->need;
-      if (st != NLOS_OK) {
-        r->status = st;
-        finish(sv, sl, false);
+      if (slot) evict_idle(sv, head->need, victims);
+      if (slot && sv->resident + sv->in_use + head->need <= sv->budget) {
+        r = head;
+        sv->queue.pop_front();
+        r->state = 1;
+        slot->req = r;
+        sv->in_use += r->need;
       }
-      changed = true;
     }
-    if (changed) sv->cv_done.notify_all();
+    if (r || !victims.empty()) {
+      // device work outside the lock: submitters and completions proceed meanwhile
+      lk.unlock();
+      for (nlos_plan_t v : victims) nlos_plan_destroy(v);
+      victims.clear();
+      if (!r) {
+        lk.lock();
+        continue;
+      }
+      void* ws = nullptr;
+      nlos_status_t st = cudaMallocAsync(&ws, r->need, slot->stream) == cudaSuccess ? NLOS_OK : NLOS_ERR_OUT_OF_MEMORY;
+      if (st == NLOS_OK) st = nlos::plan_run(r->entry->plan, r->in, r->out, ws, slot->stream);
+      if (ws) cudaFreeAsync(ws, slot->stream);
+      r->status = st;
+      if (st == NLOS_OK && cudaLaunchHostFunc(slot->stream, on_done, &slot->done) != cudaSuccess)
+        r->status = st = NLOS_ERR_CUDA;
+      lk.lock();
+      if (st != NLOS_OK) {
+        finish(sv, *slot, false);
+        sv->cv_done.notify_all();
+      }
+      continue;
+    }
     bool busy = false;
     for (Slot& sl : sv->slots) busy = busy || sl.req;
     if (sv->stop && !busy && sv->queue.empty()) break;
-    if (!busy && sv->queue.empty())
-      sv->cv_work.wait(lk);
-    else
-      sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+    sv->cv_work.wait(lk);   // woken by a submission, a completion or shutdown
   }
 }
 
@@ -180,6 +221,60 @@ double percentile(std::vector<double> v, double q) {
   std::sort(v.begin(), v.end());
   const size_t i = (size_t)std::min<double>(v.size() - 1, q * (v.size() - 1) + 0.5);
   return v[i];
+}
+
+// The entry of desc's plan with one more user, creating the plan (and
+// evicting idle plans in LRU order to make room for it and a workspace of
+// `ws_floor` bytes) if it is not resident. Called with sv->plan_mu held and
+// sv->mu not held.
+nlos_status_t acquire_plan(nlos_server_s* sv, const nlos_plan_desc_t& d, PlanEntry** out) {
+  const std::string key = desc_key(d);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->plans.find(key);
+    if (it != sv->plans.end()) {
+      ++it->second->users;
+      it->second->last_use = ++sv->lru;
+      *out = it->second;
+      return NLOS_OK;
+    }
+  }
+  nlos_plan_t p = nullptr;
+  nlos_status_t st = nlos_plan_create_ex(&d, NLOS_PLAN_NO_WORKSPACE, &p);
+  if (st != NLOS_OK) return st;
+  const size_t bytes = nlos::plan_resident_bytes(p), need = nlos::plan_workspace_bytes(p);
+  if (bytes + need > sv->budget) {
+    nlos_plan_destroy(p);
+    char msg[200];
+    snprintf(msg, sizeof msg, "plan (%zu bytes) and workspace (%zu bytes) exceed the budget of %zu bytes", bytes,
+             need, sv->budget);
+    return nlos::set_error(NLOS_ERR_OUT_OF_MEMORY, msg);
+  }
+  std::vector<nlos_plan_t> victims;
+  {
+    std::unique_lock<std::mutex> lk(sv->mu);
+    while (true) {
+      // evict idle plans, least recently used first, until the new plan and
+      // one request's workspace fit next to what is resident and running
+      evict_idle(sv, bytes + need, victims);
+      if (sv->resident + sv->in_use + bytes + need <= sv->budget) break;
+      // every resident plan is in use: wait for requests to finish
+      bool busy = !sv->queue.empty();
+      for (Slot& sl : sv->slots) busy = busy || sl.req;
+      if (!busy) break;   // nothing will free memory: admit over what fits (it runs alone)
+      sv->cv_done.wait_for(lk, std::chrono::milliseconds(50));
+    }
+    PlanEntry* e = new PlanEntry();
+    e->plan = p;
+    e->bytes = bytes;
+    e->users = 1;
+    e->last_use = ++sv->lru;
+    sv->plans[key] = e;
+    sv->resident += bytes;
+    *out = e;
+  }
+  for (nlos_plan_t v : victims) nlos_plan_destroy(v);
+  return NLOS_OK;
 }
 
 }  // namespace
@@ -203,12 +298,11 @@ nlos_status_t nlos_server_create(size_t memory_budget_bytes, int n_slots, nlos_s
   }
   sv->slots.resize(n_slots);
   for (Slot& sl : sv->slots) {
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
-      for (Slot& t : sv->slots) {
+    sl.done.sv = sv;
+    sl.done.slot = &sl;
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+      for (Slot& t : sv->slots)
         if (t.stream) cudaStreamDestroy(t.stream);
-        if (t.done) cudaEventDestroy(t.done);
-      }
       delete sv;
       return set_error(NLOS_ERR_CUDA, "server streams");
     }
@@ -221,40 +315,46 @@ nlos_status_t nlos_server_create(size_t memory_budget_bytes, int n_slots, nlos_s
 nlos_status_t nlos_server_preload(nlos_server_t sv, const nlos_plan_desc_t* desc) {
   using namespace nlos;
   if (!sv || !desc) return set_error(NLOS_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> pk(sv->plan_mu);
+  PlanEntry* e = nullptr;
+  nlos_status_t st = acquire_plan(sv, *desc, &e);
+  if (st != NLOS_OK) return st;
   std::lock_guard<std::mutex> lk(sv->mu);
-  nlos_plan_t p;
-  return get_plan(sv, *desc, &p);
+  --e->users;
+  return NLOS_OK;
 }
 
 nlos_status_t nlos_server_submit(nlos_server_t sv, const nlos_plan_desc_t* desc, const void* transient,
                                  void* volume, uint64_t* ticket) {
   using namespace nlos;
   if (!sv || !desc || !transient || !volume || !ticket) return set_error(NLOS_ERR_INVALID_ARG, "NULL argument");
-  std::lock_guard<std::mutex> lk(sv->mu);
-  if (sv->stop) return set_error(NLOS_ERR_INVALID_ARG, "server is shutting down");
-  nlos_plan_t p;
-  nlos_status_t st = get_plan(sv, *desc, &p);
-  if (st != NLOS_OK) return st;
-  const size_t need = plan_workspace_bytes(p);
-  if (need > sv->budget) {
-    char msg[160];
-    snprintf(msg, sizeof msg, "request needs %zu bytes of workspace; the budget is %zu", need, sv->budget);
-    return set_error(NLOS_ERR_OUT_OF_MEMORY, msg);
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->stop) return set_error(NLOS_ERR_INVALID_ARG, "server is shutting down");
+  }
+  PlanEntry* e = nullptr;
+  {
+    std::lock_guard<std::mutex> pk(sv->plan_mu);
+    nlos_status_t st = acquire_plan(sv, *desc, &e);
+    if (st != NLOS_OK) return st;
   }
   Request* r = new Request();
-  r->id = sv->next_id++;
-  r->plan = p;
+  r->entry = e;
   r->in = transient;
   r->out = volume;
-  r->need = need;
+  r->need = plan_workspace_bytes(e->plan);
   r->t_submit = Clock::now();
-  if (!sv->have_first) {
-    sv->have_first = true;
-    sv->t_first = r->t_submit;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->id = sv->next_id++;
+    if (!sv->have_first) {
+      sv->have_first = true;
+      sv->t_first = r->t_submit;
+    }
+    sv->reqs[r->id] = r;
+    sv->queue.push_back(r);
+    *ticket = r->id;
   }
-  sv->reqs[r->id] = r;
-  sv->queue.push_back(r);
-  *ticket = r->id;
   sv->cv_work.notify_one();
   return NLOS_OK;
 }
@@ -299,21 +399,34 @@ nlos_status_t nlos_server_stats(nlos_server_t sv, double* p50_ms, double* p99_ms
   return NLOS_OK;
 }
 
+nlos_status_t nlos_server_memory(nlos_server_t sv, size_t* plan_bytes, size_t* workspace_bytes,
+                                 unsigned long long* evictions) {
+  using namespace nlos;
+  if (!sv) return set_error(NLOS_ERR_INVALID_ARG, "server is NULL");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (plan_bytes) *plan_bytes = sv->resident;
+  if (workspace_bytes) *workspace_bytes = sv->in_use;
+  if (evictions) *evictions = sv->evictions;
+  return NLOS_OK;
+}
+
 nlos_status_t nlos_server_destroy(nlos_server_t sv) {
   using namespace nlos;
   if (!sv) return set_error(NLOS_ERR_INVALID_ARG, "server is NULL");
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stop = true;
-    sv->cv_work.notify_all();
   }
+  sv->cv_work.notify_all();
   sv->th.join();
   for (Slot& sl : sv->slots) {
     cudaStreamSynchronize(sl.stream);
     cudaStreamDestroy(sl.stream);
-    cudaEventDestroy(sl.done);
   }
-  for (auto& kv : sv->plans) nlos_plan_destroy(kv.second);
+  for (auto& kv : sv->plans) {
+    nlos_plan_destroy(kv.second->plan);
+    delete kv.second;
+  }
   for (auto& kv : sv->reqs) delete kv.second;
   delete sv;
   return NLOS_OK;

@@ -33,7 +33,7 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
             "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
             "nlos_reconstruct_host_many", "nlos_debug_fail_allocation", "nlos_selftest_umma",
-            "nlos_ffma_rate_launch"]
+            "nlos_ffma_rate_launch", "nlos_plan_memory", "nlos_server_memory"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -127,6 +127,11 @@ def load_library(path: str = LIB_PATH):
                  "nlos_server_preload", "nlos_server_submit", "nlos_server_wait", "nlos_server_stats",
                  "nlos_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.nlos_plan_memory.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
+    lib.nlos_plan_memory.restype = ctypes.c_int
+    lib.nlos_server_memory.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                       ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.nlos_server_memory.restype = ctypes.c_int
     lib.nlos_plan_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.nlos_plan_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]
@@ -211,6 +216,13 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def resident_bytes(self) -> int:
+        """Device memory the plan holds (tables, kernels, workspace)."""
+        v = ctypes.c_size_t()
+        _check(_lib.nlos_plan_memory(self._h, ctypes.byref(v)))
+        return v.value
 
     def input_dtype(self):
         import torch
@@ -427,6 +439,11 @@ class Server:
         lat = ctypes.c_double()
         _check(_lib.nlos_server_wait(self._h, ctypes.c_uint64(ticket), timeout_s, ctypes.byref(lat)))
         return lat.value
+
+    def memory(self) -> dict:
+        pb, wb, ev = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_ulonglong()
+        _check(_lib.nlos_server_memory(self._h, ctypes.byref(pb), ctypes.byref(wb), ctypes.byref(ev)))
+        return {"plan_bytes": pb.value, "workspace_bytes": wb.value, "evictions": ev.value}
 
     def stats(self, reset: bool = False) -> dict:
         p50, p99, vps = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

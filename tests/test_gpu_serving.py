@@ -1,7 +1,7 @@
 """Continuous-batching server: requests of mixed sizes, methods and storage
 types submitted back to back overlap on the device, and every result equals
 the standalone reconstruction of the same capture bit for bit (same alone and
-in the mix). Admission is by workspace footprint under the memory budget."""
+in the mix). The memory budget covers resident plans and running workspaces."""
 import numpy as np
 import pytest
 
@@ -82,3 +82,43 @@ def test_budget_admission_serialises_and_rejects():
     assert e.value.status == 2
     server.close()
     small.close()
+
+
+def test_plan_memory_counts_and_idle_plans_give_way():
+    """The budget covers resident plans (radial kernels and tensor-core operand
+    stores of phasor-field plans are tens of MB) as well as workspaces: with a
+    budget that holds about two plans and a workspace, a mix over four plans
+    evicts idle plans (least recently used first), never holds more than the
+    budget, and every result still equals its standalone reconstruction."""
+    from paper_2608_28183_gb300 import nlos
+    shapes = []
+    for k, nt in enumerate((256, 512, 384, 448)):
+        g = synth.Geometry(32, 32, nt, 16e-12, 1.0, 1.0)
+        kw = dict(n_depths=48, depth_min_m=0.4, depth_max_m=nt * g.bin_depth_m)
+        shapes.append((g, kw))
+    plans = [nlos.plan_for_capture(g, "pf", "f32", **kw) for g, kw in shapes]
+    # what a plan holds besides its own default workspace (the server's plans have none)
+    sizes = [p.resident_bytes - p.workspace_bytes for p in plans]
+    assert min(sizes) > 1 << 20                       # tables and kernels, not just the workspace
+    budget = 2 * max(sizes) + 2 * max(p.workspace_bytes for p in plans) + (1 << 20)
+    server = nlos.Server(memory_budget_bytes=budget, n_slots=2)
+    rng = np.random.default_rng(7)
+    order = [0, 1, 2, 3, 0, 2, 1, 3, 3, 0]
+    outs, refs, tickets = [], [], []
+    for i in order:
+        g, kw = shapes[i]
+        cap = synth.point_capture(g, [(rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2), 0.6, 1.0)], peak=200.0)
+        x = to_device(cap.counts, torch.float32)
+        refs.append(plans[i].reconstruct(x).clone())
+        o = torch.full(plans[i].out_shape, float("nan"), device="cuda")
+        outs.append(o)
+        tickets.append(server.submit(nlos.desc_for_capture(g, "pf", "f32", **kw), x, o))
+        m = server.memory()
+        assert m["plan_bytes"] + m["workspace_bytes"] <= budget
+    for t in tickets:
+        server.wait(t)
+    for o, r in zip(outs, refs):
+        assert torch.equal(o, r)
+    m = server.memory()
+    assert m["evictions"] >= 2 and m["plan_bytes"] <= budget
+    server.close()
