@@ -316,10 +316,24 @@ nlos_status_t nlos_server_destroy(nlos_server_t server);
  * Read and clear the device error word of a workspace (NULL: the plan's
  * default one). Kernels that stage tiles with TMA wait on barriers with an
  * iteration limit; a wait that runs out records a timeout there and the
- * kernel returns instead of hanging. Synchronous.
- * Returns OK (code 0), TIMEOUT (code 1) or CUDA.
+ * kernel returns instead of hanging (code 1; code 2 for the chunk counters
+ * of the fused f-k stages). In the bounds-checked build (compiled with
+ * NLOS_BOUNDS_CHECK; nlos_version says so) every global access of the
+ * transform, Stolt, band, depth-sum and binning kernels checks its index
+ * against its buffer's extent, and one outside records code 3 and is
+ * skipped. Synchronous.
+ * Returns OK (code 0), TIMEOUT (codes 1, 2) or CUDA (code 3 or a failed read).
  */
 nlos_status_t nlos_workspace_check(nlos_plan_t plan, const void* workspace, int* code);
+
+/*
+ * Self-test of the bounds checks: one thread checks an index one past the end
+ * of a small buffer (without accessing it) and one inside. *code is 3 in the
+ * bounds-checked build (the check recorded the index) and 0 in the normal
+ * build (checks compile away). Synchronous. Errors: INVALID_ARG,
+ * OUT_OF_MEMORY, CUDA.
+ */
+nlos_status_t nlos_selftest_bounds(int* code);
 
 /*
  * Self-test of that bounded wait: one CTA waits at most `limit` polls on a

@@ -50,9 +50,22 @@ def _run(cmd, verbose):
     return r
 
 
+def bounds_checked() -> bool:
+    """NLOS_BOUNDS_CHECK=1 in the environment selects the bounds-checked debug
+    build (every checked global access outside its buffer is recorded in the
+    workspace's error word and skipped)."""
+    return os.environ.get("NLOS_BOUNDS_CHECK", "0") not in ("", "0")
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     """Compile csrc/*.cu for sm_103a and link libnlos_gb300.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
+    extra_flags = list(extra_flags or []) + (["-DNLOS_BOUNDS_CHECK"] if bounds_checked() else [])
+    # objects built with other flags are rebuilt
+    stamp = os.path.join(BUILD, "flags.txt")
+    sig = " ".join(CFLAGS + extra_flags)
+    if not os.path.exists(stamp) or open(stamp).read() != sig:
+        force = True
     srcs = _sources()
     keep = {os.path.basename(x)[:-3] + ".o" for x in srcs}
     for stale in glob.glob(os.path.join(BUILD, "*.o")):
@@ -73,6 +86,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if force or jobs or not os.path.exists(LIB) or os.path.getmtime(LIB) < _newest(objs):
         _run([NVCC] + ARCH + ["-shared", "-o", LIB] + objs
              + ["-cudart", "shared", "-Xlinker", "-rpath," + os.path.join(CUDA_HOME, "lib64")], verbose)
+    with open(stamp, "w") as f:
+        f.write(sig)
     return LIB
 
 

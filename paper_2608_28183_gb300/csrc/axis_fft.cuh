@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include "nlos_bounds.cuh"
 #include "nlos_fft.cuh"
 #include "nlos_internal.h"
 #include "nlos_tma.cuh"
@@ -50,10 +51,13 @@ struct AxisCtx {
   int L_in, L_out, c, t_len, inverse;
   bool valid;
   float ldmul, stmul, tmul;
+  long long in_n = 0, out_n = 0;   // extents (bounds-checked build)
+  int* err = nullptr;
 
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
     x[0] = make_float2(0.f, 0.f);
     if (!valid || l >= L_in) return;
+    if (!bchk(in_base + l * in_axis, in_n, err)) return;
     if constexpr (LD == kLoadReal) {
       float v = Real<TR>::get(static_cast<const TR*>(in) + in_base + l * in_axis) * ldmul;
       x[0] = make_float2(v * tmul, 0.f);
@@ -67,6 +71,7 @@ struct AxisCtx {
     float2 v = x[0];
     if (!valid || l >= L_out) return;
     const long long o = out_base + l * out_axis;
+    if (!bchk(o, out_n, err)) return;
     if constexpr (ST == kStoreCpx) {
       if (inverse) v = cconj(v);
       Cpx<TS>::put(static_cast<TS*>(out) + o, cscale(v, stmul));
@@ -100,11 +105,13 @@ struct AxisPairCtx {
   int L_in, c;
   bool v0, v1;
   float m0, m1;
+  long long in_n = 0;
+  int* err = nullptr;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
     x[0] = make_float2(0.f, 0.f);
     if (l >= L_in) return;
-    if (v0) x[0].x = Real<TR>::get(in + base0 + l * in_axis) * m0;
-    if (v1) x[0].y = Real<TR>::get(in + base1 + l * in_axis) * m1;
+    if (v0 && bchk(base0 + l * in_axis, in_n, err)) x[0].x = Real<TR>::get(in + base0 + l * in_axis) * m0;
+    if (v1 && bchk(base1 + l * in_axis, in_n, err)) x[0].y = Real<TR>::get(in + base1 + l * in_axis) * m1;
   }
   __device__ __forceinline__ float2* sm(int) const { return smem + c; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { smem[pad16(l) * IC + c] = x[0]; }
@@ -134,6 +141,8 @@ axis_fft_realpair_kernel(const AxisParams p) {
   ctx.v1 = ii1 < p.inner;
   ctx.m0 = ldmul * (p.t_len > 0 ? (float)(int)(ii0 % p.t_len) * p.t_scale : 1.0f);
   ctx.m1 = ldmul * (p.t_len > 0 ? (float)(int)(ii1 % p.t_len) * p.t_scale : 1.0f);
+  ctx.in_n = p.in_n;
+  ctx.err = p.err;
   fftn_run<L, 1, kHalfIn, false>(ctx, j0);
   __syncthreads();
   const float h = 0.5f * p.scale * (p.st_dev_scale ? *p.st_dev_scale : 1.0f);
@@ -141,10 +150,9 @@ axis_fft_realpair_kernel(const AxisParams p) {
   for (int k = j0; k < p.L_out; k += TPC) {
     const float2 zk = pair_sm[pad16(k) * IC + c];
     const float2 zm = pair_sm[pad16((L - k) & (L - 1)) * IC + c];
-    if (ctx.v0)
-      Cpx<TS>::put(out + outer * p.out_outer + ii0 + k * p.out_axis, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
-    if (ctx.v1)
-      Cpx<TS>::put(out + outer * p.out_outer + ii1 + k * p.out_axis, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
+    const long long o0 = outer * p.out_outer + ii0 + k * p.out_axis, o1 = outer * p.out_outer + ii1 + k * p.out_axis;
+    if (ctx.v0 && bchk(o0, p.out_n, p.err)) Cpx<TS>::put(out + o0, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
+    if (ctx.v1 && bchk(o1, p.out_n, p.err)) Cpx<TS>::put(out + o1, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
   }
 }
 
@@ -188,6 +196,9 @@ axis_fft_kernel(const AxisParams p) {
   ctx.ldmul = p.ld_dev_scale ? *p.ld_dev_scale : 1.0f;
   ctx.stmul = p.scale * (p.st_dev_scale ? *p.st_dev_scale : 1.0f);
   ctx.tmul = p.t_len > 0 ? (float)(int)(ii % p.t_len) * p.t_scale : 1.0f;
+  ctx.in_n = p.in_n;
+  ctx.out_n = p.out_n;
+  ctx.err = p.err;
   fftn_run<L, 1, kHalfIn, kHalfOut>(ctx, j0);
 }
 
@@ -291,6 +302,8 @@ axis_fft_tma_kernel(const __grid_constant__ CUtensorMap tmap, const AxisParams p
     ctx.ldmul = ldmul;
     ctx.stmul = stmul;
     ctx.tmul = p.t_len > 0 ? (float)(int)(ii % p.t_len) * p.t_scale : 1.0f;
+    ctx.out_n = p.out_n;
+    ctx.err = p.err;
     fftn_run<L, 1, kHalfIn, kHalfOut>(ctx, j0);
     __syncthreads();   // the buffer is free before the next issue into it
   }
@@ -410,8 +423,9 @@ axis_fft_tma_pair_kernel(const __grid_constant__ CUtensorMap tmap, const AxisPar
     for (int q = j0; q < p.L_out; q += TPC) {
       const float2 zk = z[pad16(q) * IC + c];
       const float2 zm = z[pad16((L - q) & (L - 1)) * IC + c];
-      if (v0) Cpx<TS>::put(out + outer * p.out_outer + ii0 + q * p.out_axis, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
-      if (v1) Cpx<TS>::put(out + outer * p.out_outer + ii1 + q * p.out_axis, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
+      const long long o0 = outer * p.out_outer + ii0 + q * p.out_axis, o1 = outer * p.out_outer + ii1 + q * p.out_axis;
+      if (v0 && bchk(o0, p.out_n, p.err)) Cpx<TS>::put(out + o0, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
+      if (v1 && bchk(o1, p.out_n, p.err)) Cpx<TS>::put(out + o1, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
     }
     __syncthreads();   // the buffer is free before the next issue into it
   }

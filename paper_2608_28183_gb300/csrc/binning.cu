@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "nlos.h"
+#include "nlos_bounds.cuh"
 #include "nlos_internal.h"
 
 namespace nlos {
@@ -79,7 +80,8 @@ bin_phasor_kernel(const PhasorBinParams q) {
         const uint32_t pj = __shfl_sync(0xffffffffu, p, j);
         const uint32_t bj = __shfl_sync(0xffffffffu, b, j);
         if (pj != cur) {                       // warp-uniform: a new run of one wall point
-          if (cur < npix && f < q.F) atomicAdd(P + (size_t)cur * q.F + f, make_float2(acc.x * w, acc.y * w));
+          if (cur < npix && f < q.F && bchk((long long)cur * q.F + f, (long long)npix * q.F, q.err))
+            atomicAdd(P + (size_t)cur * q.F + f, make_float2(acc.x * w, acc.y * w));
           acc = make_float2(0.f, 0.f);
           cur = pj;
         }
@@ -89,7 +91,8 @@ bin_phasor_kernel(const PhasorBinParams q) {
           acc.y += e.y;
         }
       }
-      if (cur < npix && f < q.F) atomicAdd(P + (size_t)cur * q.F + f, make_float2(acc.x * w, acc.y * w));
+      if (cur < npix && f < q.F && bchk((long long)cur * q.F + f, (long long)npix * q.F, q.err))
+        atomicAdd(P + (size_t)cur * q.F + f, make_float2(acc.x * w, acc.y * w));
     }
   }
 }

@@ -23,6 +23,7 @@
 // where a chunk row is one 128-byte line), so it never reaches DRAM.
 #pragma once
 #include "axis_fft.cuh"
+#include "nlos_bounds.cuh"
 #include "nlos_internal.h"
 #include "nlos_tma.cuh"
 
@@ -104,6 +105,7 @@ struct ChainMidCtx : AxisTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> {
   uint64_t keep;
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     if (l >= this->L_out) return;
+    if (!bchk(this->out_base + l * this->out_axis, this->out_n, this->err)) return;
     const float2 v = make_float2(x[0].x * this->stmul, -x[0].y * this->stmul);   // inverse: conjugate
     TS* o = static_cast<TS*>(this->out) + this->out_base + l * this->out_axis;
     if constexpr (sizeof(TS) == 8) st_global_hint(reinterpret_cast<float2*>(o), v, keep);
@@ -130,6 +132,7 @@ __device__ __forceinline__ void chain_ctx(Ctx& ctx, float2* slot, const float2* 
   ctx.t_len = 0;
   ctx.ldmul = 1.0f;
   ctx.tmul = 1.0f;
+  ctx.in_n = 0;   // the staged tile is read from shared memory
 }
 
 // Forward (kFwd) and inverse chains. Per chunk: forward n1 = b x items (one
@@ -264,9 +267,11 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
       if (p.discard && it.second && d.sub == nsubs - 1) {
         const int nl = kFwd ? p.b : L;
         const float2* base = static_cast<const float2*>(p.mid) + (long long)it.chunk * kChainCols;
-        for (int r = threadIdx.x; r < nl; r += T::CONSUMERS)
-          l2_discard(kFwd ? base + (long long)it.idx * bn + (long long)r * p.n
-                          : base + (long long)r * bn + (long long)it.idx * p.n);
+        for (int r = threadIdx.x; r < nl; r += T::CONSUMERS) {
+          const long long o = (long long)it.chunk * kChainCols +
+                              (kFwd ? (long long)it.idx * bn + (long long)r * p.n : (long long)r * bn + (long long)it.idx * p.n);
+          if (bchk(o + kChainCols - 1, p.mid_n, p.err)) l2_discard(base + (o - (long long)it.chunk * kChainCols));
+        }
       }
       if (kFwd && !it.second) {
         // x forward of wall row y = idx: 16 real columns t0 + c, t0 + c + 8
@@ -285,19 +290,24 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         // X_{c+8}[k] = (Z[k] - conj Z[L-k]) / (2i), k in [0, L/2]
         const float h = 0.5f * p.s1;
         const float2* z = buf(slot);
-        TS* o0 = static_cast<TS*>(p.mid) + (long long)it.idx * p.n + t0 + c;
+        const long long oo = (long long)it.idx * p.n + t0 + c;
+        TS* o0 = static_cast<TS*>(p.mid) + oo;
         for (int q = j0; q < hx; q += TPC) {
           const float2 zk = z[padE<E>(q) * IC + c];
           const float2 zm = z[padE<E>((L - q) & (L - 1)) * IC + c];
           TS* o = o0 + q * bn;
-          Cpx<TS>::put(o, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
-          Cpx<TS>::put(o + IC, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
+          if (bchk(oo + q * bn + IC, p.mid_n, p.err)) {
+            Cpx<TS>::put(o, make_float2((zk.x + zm.x) * h, (zk.y - zm.y) * h));
+            Cpx<TS>::put(o + IC, make_float2((zk.y + zm.y) * h, (zm.x - zk.x) * h));
+          }
         }
       } else if (kFwd) {
         // y forward of kx = idx: rows y < b, all L outputs
         ChainTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> ctx;
         chain_ctx(ctx, buf(slot), p.tw, c, 0);
         ctx.out = p.out;
+        ctx.out_n = p.out_n;
+        ctx.err = p.err;
         ctx.out_base = (long long)it.idx * L * p.n + col0 + c;
         ctx.out_axis = p.n;
         ctx.L_in = p.b;
@@ -310,6 +320,8 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         chain_ctx(ctx, buf(slot), p.tw, c, 1);
         ctx.keep = keep;
         ctx.out = p.mid;
+        ctx.out_n = p.mid_n;
+        ctx.err = p.err;
         ctx.out_base = (long long)it.idx * bn + col0 + c;
         ctx.out_axis = p.n;
         ctx.L_in = L;
@@ -321,6 +333,8 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         ChainTmaCtx<L, IC, kLoadCpx, ST, TS> ctx;
         chain_ctx(ctx, buf(slot), p.tw, c, 1);
         ctx.out = p.out;
+        ctx.out_n = p.out_n;
+        ctx.err = p.err;
         ctx.out_base = (long long)it.idx * p.n + col0 + c;
         ctx.out_axis = bn;
         ctx.L_in = L;

@@ -21,6 +21,7 @@
 #pragma once
 #include "fk_stolt.cuh"
 #include "fk_zwarp.cuh"
+#include "nlos_bounds.cuh"
 #include "nlos_fft.cuh"
 #include "nlos_internal.h"
 
@@ -39,8 +40,11 @@ struct FkFwdCtx {
   bool valid;
   float ldmul;
   int n_in;                  // stored samples of the pencil (the rest is zero padding)
+  long long g_off, g_n;      // offset of g in its buffer, the buffer's extent (bounds-checked build)
+  int* err;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = (valid && (!kGuard || l < n_in)) ? cscale(Cpx<TS>::get(g + l), ldmul) : make_float2(0.f, 0.f);
+    x[0] = (valid && (!kGuard || l < n_in) && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), ldmul)
+                                                                         : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[pad16(l)] = x[0]; }
@@ -65,6 +69,8 @@ struct FkInvCtx {
   bool st0, st1;
   float stmul;
   int n_out;                 // kept outputs z < n_out
+  long long off0, off1, psi_n;   // offsets of out0 / out1 in their buffer, its extent (bounds-checked build)
+  int* err;
   __device__ __forceinline__ void load(int m, float2 (&x)[2]) const {
     x[0] = x[1] = make_float2(0.f, 0.f);
     if (m < 1) return;                                // m < L/2 (upper half is pruned)
@@ -82,8 +88,8 @@ struct FkInvCtx {
   __device__ __forceinline__ float2* sm(int t) const { return t == 0 ? W0 : W1; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[2]) const {   // every l the schedule keeps
     if (kGuard && l >= n_out) return;
-    if (st0) Cpx<TS>::put(out0 + l, cscale(cconj(x[0]), stmul));
-    if (st1) Cpx<TS>::put(out1 + l, cscale(cconj(x[1]), stmul));
+    if (st0 && bchk(off0 + l, psi_n, err)) Cpx<TS>::put(out0 + l, cscale(cconj(x[0]), stmul));
+    if (st1 && bchk(off1 + l, psi_n, err)) Cpx<TS>::put(out1 + l, cscale(cconj(x[1]), stmul));
   }
 };
 
@@ -131,7 +137,8 @@ fk_zstage_kernel(const FkZParams p) {
   float2* W1 = fk_sm + ((kAlias ? 1 : 2) * PPC + w) * S::SMEM;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
-    FkFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul, p.n};
+    FkFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul, p.n,
+                                (valid ? pid : 0) * p.n, p.G_n, p.err};
     fftn_run<L, 1, kPad2, false>(ctx, j0);
   }
   __syncthreads();
@@ -146,7 +153,7 @@ fk_zstage_kernel(const FkZParams p) {
   const long long o_mirror = ((long long)mkx * twob + mky) * p.n;
   // the partner is stored only where it is not itself a stored pencil
   FkInvCtx<L, TS, kAlias, kGuard> ctx{U, W0, W1, p.tw, psi + o_direct, psi + o_mirror, L / 2, A.x, A.y,
-                      valid, valid && kx > 0 && 2 * kx < p.a_pad, p.st_scale, p.n};
+                      valid, valid && kx > 0 && 2 * kx < p.a_pad, p.st_scale, p.n, o_direct, o_mirror, p.psi_n, p.err};
   fftn_run<L, 2, true, kPad2>(ctx, j0);
 }
 

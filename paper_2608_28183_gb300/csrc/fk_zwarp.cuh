@@ -23,6 +23,7 @@
 // it as a float.
 #pragma once
 #include "fk_stolt.cuh"
+#include "nlos_bounds.cuh"
 #include "nlos_fft.cuh"
 #include "nlos_internal.h"
 
@@ -49,8 +50,11 @@ struct FkWarpFwdCtx {
   const float2* tw;
   float ldmul;
   int n_in;
+  long long g_off, g_n;      // offset of g in its buffer, the buffer's extent (bounds-checked build)
+  int* err;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = (!kGuard || l < n_in) ? cscale(Cpx<TS>::get(g + l), ldmul) : make_float2(0.f, 0.f);
+    x[0] = ((!kGuard || l < n_in) && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), ldmul)
+                                                                : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return U; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[padE<32>(l)] = x[0]; }
@@ -72,6 +76,8 @@ struct FkWarpInvCtx {
   bool st;
   float stmul;
   int n_out;
+  long long out_off, psi_n;  // offset of out in its buffer, the buffer's extent (bounds-checked build)
+  int* err;
   __device__ __forceinline__ void load(int m, float2 (&x)[1]) const {
     x[0] = make_float2(0.f, 0.f);
     const unsigned e = coord[m];                  // m < L/2: the upper half is pruned
@@ -96,7 +102,7 @@ struct FkWarpInvCtx {
   __device__ __forceinline__ float2* sm(int) const { return buf; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     if (kGuard && l >= n_out) return;
-    if (st) Cpx<TS>::put(out + l, make_float2(x[0].x * stmul, -x[0].y * stmul));
+    if (st && bchk(out_off + l, psi_n, err)) Cpx<TS>::put(out + l, make_float2(x[0].x * stmul, -x[0].y * stmul));
   }
 };
 
@@ -119,7 +125,8 @@ __global__ void __launch_bounds__(64) fk_zwarp_kernel(const FkZParams p) {
   const long long pid = (long long)kx * p.b_pad + ky;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
-    FkWarpFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + pid * p.n, U, p.tw32, ldmul, p.n};
+    FkWarpFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + pid * p.n, U, p.tw32, ldmul, p.n, pid * p.n, p.G_n,
+                                    p.err};
     fftn_run<L, 1, kPad2, false, FkWarpFwdCtx<L, TS, kGuard>, 32>(ctx, lane);
   }
   {
@@ -147,7 +154,8 @@ __global__ void __launch_bounds__(64) fk_zwarp_kernel(const FkZParams p) {
   TS* psi = static_cast<TS*>(p.psi);
   const bool own = w == 0 || !single;
   {
-    FkWarpInvCtx<L, TS, kGuard, false> ctx{U, W, coord, jac, p.tw32, psi + pid * p.n, own, p.st_scale, p.n};
+    FkWarpInvCtx<L, TS, kGuard, false> ctx{U, W, coord, jac, p.tw32, psi + pid * p.n, own, p.st_scale, p.n, pid * p.n,
+                                           p.psi_n, p.err};
     fftn_run<L, 1, true, kPad2, FkWarpInvCtx<L, TS, kGuard, false>, 32>(ctx, lane);
   }
   {
@@ -155,8 +163,8 @@ __global__ void __launch_bounds__(64) fk_zwarp_kernel(const FkZParams p) {
     const int mkx = (kx == 0) ? 0 : p.a_pad - kx;
     const int mky = (p.b_pad - ky) & (p.b_pad - 1);
     const bool st = own && kx > 0 && 2 * kx < p.a_pad;
-    FkWarpInvCtx<L, TS, kGuard, true> ctx{U, U, coord, jac, p.tw32, psi + ((long long)mkx * p.b_pad + mky) * p.n, st,
-                                          p.st_scale, p.n};
+    const long long mo = ((long long)mkx * p.b_pad + mky) * p.n;
+    FkWarpInvCtx<L, TS, kGuard, true> ctx{U, U, coord, jac, p.tw32, psi + mo, st, p.st_scale, p.n, mo, p.psi_n, p.err};
     fftn_run<L, 1, true, kPad2, FkWarpInvCtx<L, TS, kGuard, true>, 32>(ctx, lane);
   }
 }

@@ -692,6 +692,17 @@ AxisLaunch axis(int storage, int L, long long n_outer, const void* in, void* out
   return l;
 }
 
+// element extents of the workspace's three complex buffers (bounds-checked build)
+long long ws_extent(const nlos_plan_s* p, int k) {
+  const size_t end = k == 0 ? p->off[1] : k == 1 ? p->off[2] : p->off_scal;
+  return (long long)((end - p->off[k]) / complex_bytes(p->storage));
+}
+void set_extents(AxisLaunch& l, long long in_n, long long out_n) {
+  l.p.in_n = in_n;
+  l.p.out_n = out_n;
+  l.p.err = l.err;
+}
+
 nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStream_t s) {
   const int st = p->storage;
   const long long a = p->a, b = p->b, n = p->n;
@@ -748,6 +759,9 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     c.p.s1 = g2a;
     c.p.s2 = g2b;
     c.p.ld_dev_scale = s_in;
+    c.p.in_n = a * b * n;
+    c.p.mid_n = ws_extent(p, 0);
+    c.p.out_n = ws_extent(p, 1);
     c.p.discard = st == kF32 && p->tiles[sid] < 2;
     c.nslot = p->tiles[sid] % 2 == 0 ? 3 : 2;
     c.fwd = 1;
@@ -774,12 +788,14 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   l.p.ld_dev_scale = s_in;
   l.err = err;
   attach_tmap(l);
+  set_extents(l, a * b * n, ws_extent(p, 0));
   NLOS_CU(launch_axis_fft(l, s), "fk x-forward");
   NLOS_MARK(p, s, sid++);
   // FK1: y forward (zero-padded to Ly)
   l = axis(st, (int)Ly, hx, b0, b1, n, b * n, n, Ly * n, n, (int)b, (int)Ly, 0, g2b, p->tw[(int)Ly], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
+  set_extents(l, ws_extent(p, 0), ws_extent(p, 1));
   NLOS_CU(launch_axis_fft(l, s), "fk y-forward");
   NLOS_MARK(p, s, sid++);
   }
@@ -799,6 +815,9 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   z.npencils = hx * Ly;
   z.ld_scale = g2n;
   z.st_scale = g2n;
+  z.G_n = ws_extent(p, 1);
+  z.psi_n = ws_extent(p, 2);
+  z.err = err;
   NLOS_CU(launch_fk_zstage(z, st, p->tiles[sid], s), "fk stolt stage");
   NLOS_MARK(p, s, sid++);
   if (p->fused) {
@@ -811,6 +830,9 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     c.p.s1 = g2b;
     c.p.s2 = fscale;
     c.p.st_dev_scale = cpx ? inv_s : inv_s2;
+    c.p.in_n = ws_extent(p, 2);
+    c.p.mid_n = ws_extent(p, 0);
+    c.p.out_n = a * b * n;
     c.p.discard = st == kF32 && p->tiles[sid] < 2;
     c.nslot = p->tiles[sid] % 2 == 0 ? 3 : 2;
     c.fwd = 0;
@@ -829,6 +851,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   l = axis(st, (int)Ly, Lx, b2, b0, n, Ly * n, n, b * n, n, (int)Ly, (int)b, 1, g2b, p->tw[(int)Ly], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
+  set_extents(l, ws_extent(p, 2), ws_extent(p, 0));
   NLOS_CU(launch_axis_fft(l, s), "fk y-inverse");
   NLOS_MARK(p, s, sid++);
   // FK4: x inverse (keep x < a), |psi|^2 with the 1/(Lx Ly Lt) normalisation
@@ -837,6 +860,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   l.p.st_dev_scale = cpx ? inv_s : inv_s2;
   l.err = err;
   attach_tmap(l);
+  set_extents(l, ws_extent(p, 0), a * b * n);
   NLOS_CU(launch_axis_fft(l, s), "fk x-inverse");
   NLOS_MARK(p, s, sid++);
   return NLOS_OK;
@@ -884,6 +908,9 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   bp.ld_scale = 1.0f;
   bp.ld_dev_scale = s_in;
   bp.st_scale = gn;
+  bp.H_n = a * b * n;
+  bp.P_n = ws_extent(p, 0);
+  bp.err = err;
   // the float32 tensor-core depth sum scales the phasors by a bound taken from
   // their largest component: the band transform records it as it stores them
   unsigned* amax = reinterpret_cast<unsigned*>(ws + p->off_scal + kAmaxOffset);
@@ -899,11 +926,13 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   AxisLaunch l = axis(st, (int)Nv, a, P, b1, F, b * F, F, Nv * F, F, (int)b, (int)Nv, 0, g2b, p->tw[(int)Nv], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
+  set_extents(l, P_in ? a * b * F : ws_extent(p, 0), ws_extent(p, 1));
   NLOS_CU(launch_axis_fft(l, s), "pf y-forward");
   NLOS_MARK(p, s, sid++);
   l = axis(st, (int)Nu, 1, b1, b2, Nv * F, 0, Nv * F, 0, Nv * F, (int)a, (int)Nu, 0, g2a, p->tw[(int)Nu], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
+  set_extents(l, ws_extent(p, 1), ws_extent(p, 2));
   NLOS_CU(launch_axis_fft(l, s), "pf x-forward");
   NLOS_MARK(p, s, sid++);
   if (p->d.method == NLOS_PHASOR_DENSE) {
@@ -948,6 +977,8 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
         up.abound_exp = e2;
       }
       up.err = err;
+      up.Phat_n = ws_extent(p, 2);
+      up.C_n = ws_extent(p, 1);
       // launch shape 0: persistent warp-specialised schedule; 2: one CTA per tile
       const bool ws_sched = p->tiles[sid] != 2;
       const int t0 = ws_sched ? pf_umma_first_split_tile(up) : up.ntiles;
@@ -977,6 +1008,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   l = axis(st, (int)Nv, Nu, b1, b0, D, Nv * D, D, b * D, D, (int)Nv, (int)b, 1, g2b, p->tw[(int)Nv], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
+  set_extents(l, ws_extent(p, 1), ws_extent(p, 0));
   NLOS_CU(launch_axis_fft(l, s), "pf y-inverse");
   NLOS_MARK(p, s, sid++);
   // scales the data carries into this last pass (it applies none of its own)
@@ -987,6 +1019,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   l.p.st_dev_scale = inv_s;
   l.err = err;
   attach_tmap(l);
+  set_extents(l, ws_extent(p, 0), a * b * D);
   NLOS_CU(launch_axis_fft(l, s), "pf x-inverse");
   NLOS_MARK(p, s, sid++);
   return NLOS_OK;
@@ -1331,6 +1364,7 @@ nlos_status_t nlos_bin_phasors(nlos_plan_t p, const uint32_t* pixel, const uint3
   q.k_lo = p->k_lo;
   q.F = p->F;
   q.P = static_cast<float2*>(phasors);
+  q.err = p->ws ? reinterpret_cast<int*>(static_cast<char*>(p->ws) + p->off_scal + kErrOffset) : nullptr;
   NLOS_CU(launch_bin_phasors(q, s), "phasor binning");
   return NLOS_OK;
 }
@@ -1744,6 +1778,8 @@ nlos_status_t nlos_workspace_check(nlos_plan_t p, const void* workspace, int* co
   if (v != 0) NLOS_CU(cudaMemset(const_cast<char*>(ws) + p->off_scal + kErrOffset, 0, sizeof v), "error word reset");
   if (code) *code = v;
   if (v == kDevErrTmaTimeout) return fail(NLOS_ERR_TIMEOUT, "a staged-load wait ran out of its iteration limit");
+  if (v == kDevErrChainTimeout) return fail(NLOS_ERR_TIMEOUT, "a fused stage's chunk wait ran out of its iteration limit");
+  if (v == kDevErrBounds) return fail(NLOS_ERR_CUDA, "bounds-checked build: an index fell outside its buffer");
   if (v != 0) return fail(NLOS_ERR_CUDA, "device error word %d", v);
   return NLOS_OK;
 }
@@ -1803,7 +1839,11 @@ void nlos_debug_fail_allocation(int k) { g_fail_alloc.store(k > 0 ? k : 0); }
 
 const char* nlos_last_error(void) { return g_err.c_str(); }
 
-const char* nlos_version(void) { return "nlos-gb300 0.1 (sm_103a)"; }
+#ifdef NLOS_BOUNDS_CHECK
+const char* nlos_version(void) { return "nlos-gb300 0.2 (sm_103a, bounds-checked)"; }
+#else
+const char* nlos_version(void) { return "nlos-gb300 0.2 (sm_103a)"; }
+#endif
 
 }  // extern "C"
 

@@ -34,6 +34,8 @@ struct AxisParams {
   const float* st_dev_scale;   // optional device scalar multiplying stores
   int t_len;                   // real loads: multiply by (inner index % t_len) * t_scale
   float t_scale;
+  long long in_n, out_n;       // element extents of in / out (bounds-checked build; 0: unchecked)
+  int* err;                    // device error word (bounds-checked build), may be null
 };
 
 struct AxisLaunch {
@@ -67,6 +69,7 @@ __host__ __device__ constexpr int axis_tile_count(int L) { return 2 * axis_ic_co
 // error codes written to the device error word
 constexpr int kDevErrTmaTimeout = 1;
 constexpr int kDevErrChainTimeout = 2;    // a fused lateral stage gave up waiting for a chunk
+constexpr int kDevErrBounds = 3;          // bounds-checked build: an index outside its buffer (access skipped)
 // launch-shape variants of the f-k temporal stage of length L: 0-3 one pencil
 // and its partner per thread group (two CTA sizes, with or without aliased
 // buffers), 4 one warp per radix-32 transform (the pencils (kx, +-ky) and
@@ -94,6 +97,8 @@ struct FkZParams {
   float ld_scale;              // multiplies forward loads
   const float* ld_dev_scale;   // optional device scalar multiplying forward loads
   float st_scale;              // multiplies stored values
+  long long G_n, psi_n;        // element extents (bounds-checked build; 0: unchecked)
+  int* err;                    // device error word (bounds-checked build), may be null
 };
 cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s);
 
@@ -116,6 +121,7 @@ struct FkChainParams {
   int* sync;                   // [1 + nchunks] ints, zero at launch: ticket, finished first-transform items per chunk
   int* err;                    // device error word
   int discard;                 // drop consumed lines of `mid` from L2 (float32 storage)
+  long long in_n, mid_n, out_n;  // element extents (bounds-checked build; 0: unchecked)
 };
 struct FkChainLaunch {
   FkChainParams p;
@@ -149,6 +155,8 @@ struct PfBandParams {
   float st_scale;
   int accumulate;              // add to P instead of overwriting it
   unsigned* amax;              // when set: atomicMax of max |Re|, |Im| of the stored P (float bits)
+  long long H_n, P_n;          // element extents (bounds-checked build; 0: unchecked)
+  int* err;                    // device error word (bounds-checked build), may be null
 };
 cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s);
 
@@ -165,6 +173,7 @@ struct PhasorBinParams {
   const float* w;              // [F]
   int k_lo, F;
   float2* P;
+  int* err;                    // device error word (bounds-checked build), may be null
 };
 cudaError_t launch_bin_phasors(const PhasorBinParams& q, cudaStream_t s);
 // photon records -> float32 histogram H[pixel][bin] (+= 1 per kept record)
@@ -242,6 +251,7 @@ struct PfUmmaParams {
   int abound_exp;
   float scale;
   int* err;                    // device error word (bounded waits)
+  long long Phat_n, C_n;       // element extents (bounds-checked build; 0: unchecked)
 };
 // pipelined: persistent warp-specialised CTAs (one per SM) instead of one CTA per tile
 cudaError_t launch_pf_umma(const PfUmmaParams& p, bool pipelined, cudaStream_t s);

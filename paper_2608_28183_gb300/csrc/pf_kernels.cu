@@ -1,6 +1,7 @@
 // Phasor-field (radial RSD) kernels: temporal band transform, depth sum over
 // the radial kernel, plan-time float64 construction of the radial kernel, and
 // the per-volume scale used by reduced-precision storage.
+#include "nlos_bounds.cuh"
 #include "nlos_fft.cuh"
 #include "nlos_internal.h"
 
@@ -25,14 +26,18 @@ struct PfBandCtx {
   float ldmul, stmul;
   int accumulate;
   int n_in;                    // samples of the pencil; the DFT runs over L >= n_in
+  long long h_off, H_n, p_off, P_n;   // offsets of h / P in their buffers, the extents (bounds-checked build)
+  int* err;
   mutable float m = 0.f;       // max |component| of what this thread stored
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = (valid && l < n_in) ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f) : make_float2(0.f, 0.f);
+    x[0] = (valid && l < n_in && bchk(h_off + l, H_n, err)) ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f)
+                                                           : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     const int f = l - k_lo;
     if (!valid || f < 0 || f >= F) return;
+    if (!bchk(p_off + f, P_n, err)) return;
     float2 v = cscale(x[0], __ldg(w + f) * stmul);
     if (accumulate) v = cadd(v, Cpx<TS>::get(P + f));
     Cpx<TS>::put(P + f, v);
@@ -60,7 +65,7 @@ pf_band_kernel(const PfBandParams p) {
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   PfBandCtx<L, TR, TS> ctx{static_cast<const TR*>(p.H) + q * p.n, static_cast<TS*>(p.P) + q * p.F,
                            pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale, p.accumulate,
-                           p.n};
+                           p.n, q * p.n, p.H_n, q * p.F, p.P_n, p.err};
   fftn_run<L, 1, false, false>(ctx, j0);
   if (p.amax) {
     // the bound the float32 depth sum scales its phasors by (see PfBandParams)

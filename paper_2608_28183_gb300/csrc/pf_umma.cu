@@ -36,6 +36,7 @@
 //  * pf_umma_kernel: one CTA per tile, one stage.
 #include <cuda_fp16.h>
 
+#include "nlos_bounds.cuh"
 #include "nlos_internal.h"
 #include "nlos_umma.cuh"
 
@@ -402,7 +403,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         break;
       }
       tc_fence_after_sync();
-      const int pix = p.tile_pix[(size_t)sg.tile * kUmmaTile + row];
+      int pix = p.tile_pix[(size_t)sg.tile * kUmmaTile + row];
+      if (pix >= 0 && !bchk((long long)pix * p.D + p.D - 1, p.C_n, p.err)) pix = -1;   // the row must lie in C
       const float ac = p.tile_acut[(size_t)sg.tile * kUmmaTile + row];
       Out* crow = static_cast<Out*>(p.C) + (size_t)(pix >= 0 ? pix : 0) * p.D + (size_t)sg.blk * Db;
       epilogue_cols<Op, Db>(tm + (uint32_t)(a * S::ACC_COLS), warp, pix, p.scale * inv_sa * ac, crow, sg.blk, p.D, 0, Db,
@@ -433,7 +435,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) pf_umma_ws_kernel(const PfUmmaP
         int r, q;
         A::coords(i, t, r, q);
         const int f = kc * Op::kQ + q;
-        h[i] = (rp[i] >= 0 && f < p.F) ? Ph[(size_t)rp[i] * p.F + f] : Op::zero();
+        h[i] = (rp[i] >= 0 && f < p.F && bchk((long long)rp[i] * p.F + f, p.Phat_n, p.err))
+                   ? Ph[(size_t)rp[i] * p.F + f] : Op::zero();
       }
     };
     In hc[A::kIters], hn[A::kIters];
@@ -501,7 +504,8 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
   const int row = tid & (kUmmaTile - 1), half = tid >> 7;
   const int tile = blockIdx.x;
   const int2 i01 = p.tile_i01[tile];
-  const int pix = p.tile_pix[(size_t)tile * kUmmaTile + row];
+  int pix = p.tile_pix[(size_t)tile * kUmmaTile + row];
+  if (pix >= 0 && !bchk((long long)pix * p.D + p.D - 1, p.C_n, p.err)) pix = -1;   // the row must lie in C
   const float ac = p.tile_acut[(size_t)tile * kUmmaTile + row];
   if (tid < kUmmaTile) {
     spix[tid] = p.tile_pix[(size_t)tile * kUmmaTile + tid];
@@ -524,7 +528,8 @@ __global__ void __launch_bounds__(kThreads) pf_umma_kernel(const PfUmmaParams p)
       A::coords(i, tid, r, q);
       const int f = kc * Op::kQ + q;
       const int px = spix[r];
-      h[i] = (px >= 0 && f < p.F) ? Ph[(size_t)px * p.F + f] : Op::zero();
+      h[i] = (px >= 0 && f < p.F && bchk((long long)px * p.F + f, p.Phat_n, p.err)) ? Ph[(size_t)px * p.F + f]
+                                                                                      : Op::zero();
     }
   };
   In hcur[A::kIters], hnext[A::kIters];

@@ -169,3 +169,40 @@ extern "C" nlos_status_t nlos_ffma_rate_launch(const float* params, float* sink,
   *flops = 2.0 * 8 * 16 * (double)iters * blocks * 256;
   return NLOS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Bounds-check self-test: one thread checks an index one past the end of a
+// 4-element buffer and the last valid one. The check never performs the
+// access, so nothing is read or written out of bounds; the bounds-checked
+// build records kDevErrBounds for the first, the normal build records nothing.
+// ---------------------------------------------------------------------------
+#include "nlos_bounds.cuh"
+
+namespace {
+__global__ void bounds_probe_kernel(float* buf, int* err) {
+  if (nlos::bchk(4, 4, err)) buf[0] = 1.0f;      // index 4 of 4 elements: outside, skipped
+  if (nlos::bchk(3, 4, err)) buf[3] = 2.0f;      // inside
+}
+}  // namespace
+
+extern "C" nlos_status_t nlos_selftest_bounds(int* code) {
+  using namespace nlos;
+  if (!code) return set_error(NLOS_ERR_INVALID_ARG, "code is NULL");
+  int* d = nullptr;
+  float* buf = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return set_error(NLOS_ERR_OUT_OF_MEMORY, "self-test word");
+  if (cudaMalloc(&buf, 4 * sizeof(float)) != cudaSuccess) {
+    cudaFree(d);
+    return set_error(NLOS_ERR_OUT_OF_MEMORY, "self-test buffer");
+  }
+  cudaMemset(d, 0, sizeof(int));
+  bounds_probe_kernel<<<1, 1>>>(buf, d);
+  cudaError_t e = cudaDeviceSynchronize();
+  int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, d, sizeof v, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  cudaFree(buf);
+  if (e != cudaSuccess) return set_error(NLOS_ERR_CUDA, cudaGetErrorString(e));
+  *code = v;
+  return NLOS_OK;
+}

@@ -21,6 +21,10 @@ METHODS = {"fk": NLOS_FK, "pf": NLOS_PHASOR_RSD, "phasor": NLOS_PHASOR_RSD, "pf_
 STORAGES = {"f32": NLOS_F32, "f16": NLOS_F16, "bf16": NLOS_BF16}
 OUTPUTS = {"magnitude": 0, "complex": 1}
 PLAN_NO_WORKSPACE, PLAN_SEPARATE_AXES = 1, 2
+# bounds-checked debug build (NLOS_BOUNDS_CHECK=1): plans read their device
+# error word when closed and record nonzero codes here
+BOUNDS_CHECKED = os.environ.get("NLOS_BOUNDS_CHECK", "0") not in ("", "0")
+WORKSPACE_ERRORS = []
 
 EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nlos_reconstruct",
             "nlos_reconstruct_ws", "nlos_reconstruct_host", "nlos_reconstruct_batch",
@@ -33,7 +37,7 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
             "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
             "nlos_reconstruct_host_many", "nlos_debug_fail_allocation", "nlos_selftest_umma",
-            "nlos_ffma_rate_launch", "nlos_plan_memory", "nlos_server_memory"]
+            "nlos_ffma_rate_launch", "nlos_plan_memory", "nlos_server_memory", "nlos_selftest_bounds"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -127,6 +131,8 @@ def load_library(path: str = LIB_PATH):
                  "nlos_server_preload", "nlos_server_submit", "nlos_server_wait", "nlos_server_stats",
                  "nlos_server_destroy"):
         getattr(lib, name).restype = ctypes.c_int
+    lib.nlos_selftest_bounds.argtypes = [ctypes.POINTER(ctypes.c_int)]
+    lib.nlos_selftest_bounds.restype = ctypes.c_int
     lib.nlos_plan_memory.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t)]
     lib.nlos_plan_memory.restype = ctypes.c_int
     lib.nlos_server_memory.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
@@ -203,6 +209,7 @@ class Plan:
         self.storage = storage
         h = ctypes.c_void_p()
         flags = PLAN_SEPARATE_AXES if separate_axes else 0
+        self._own_ws = True
         _check(lib.nlos_plan_create_ex(ctypes.byref(d), flags, ctypes.byref(h)))
         self._h = h
         shape = (ctypes.c_size_t * 3)()
@@ -358,8 +365,20 @@ class Plan:
         arr = (ctypes.c_int * len(values))(*values)
         _check(_lib.nlos_plan_set_tiles(self._h, arr, len(values)))
 
+    def check_workspace(self) -> int:
+        """Read and clear the default workspace's device error word (0: clean;
+        1, 2: a bounded wait ran out; 3: bounds-checked build, an index fell
+        outside its buffer)."""
+        code = ctypes.c_int(0)
+        _lib.nlos_workspace_check(self._h, None, ctypes.byref(code))
+        return code.value
+
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
+            if BOUNDS_CHECKED and self.workspace_bytes and self._own_ws:
+                code = self.check_workspace()
+                if code:
+                    WORKSPACE_ERRORS.append((self.method, self.desc.nx, self.desc.ny, self.desc.nt, code))
             _check(_lib.nlos_plan_destroy(self._h))
             self._h = ctypes.c_void_p()
 

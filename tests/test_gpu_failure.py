@@ -104,3 +104,16 @@ def test_server_wait_times_out_then_completes(lib):
     assert server.wait(t, timeout_s=60.0) > 0
     torch.cuda.synchronize()
     assert float(out.abs().sum()) == 0.0
+
+
+def test_bounds_check_records_without_access():
+    """The bounds checks record an index outside its buffer (code 3) in the
+    bounds-checked build and compile away in the normal one; the probe never
+    touches memory outside the buffer either way."""
+    import ctypes
+    from paper_2608_28183_gb300 import build, nlos
+    lib = nlos.load_library()
+    code = ctypes.c_int(-1)
+    assert lib.nlos_selftest_bounds(ctypes.byref(code)) == 0
+    assert code.value == (3 if build.bounds_checked() else 0)
+    assert (b"bounds-checked" in lib.nlos_version()) == build.bounds_checked()
