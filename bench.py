@@ -621,8 +621,33 @@ def moe_bench(torch, nlos, synth, reps=20):
         cur.wait_stream(s1)
         cur.wait_stream(s2)
         nlos.moe_mix(i_f, i_p, out=mix)
-    return {"grid": [g.nx, g.ny, g.nt], "serial_ms": _event_ms(torch, serial, reps),
-            "two_streams_ms": _event_ms(torch, concurrent, reps)}
+
+    def shared(two):
+        # one x/y forward transform feeds both branches (nlos_reconstruct_moe)
+        def run():
+            nlos.reconstruct_moe(fk, pf, x, vf, vp, stream2=s2 if two else None)
+            nlos.max_image(vf, take_sqrt=True, image=i_f)
+            nlos.max_image(vp, image=i_p)
+            nlos.moe_mix(i_f, i_p, out=mix)
+        return run
+    out = {"grid": [g.nx, g.ny, g.nt], "serial_ms": _event_ms(torch, serial, reps),
+           "two_streams_ms": _event_ms(torch, concurrent, reps)}
+    ref = mix.clone()
+    out["shared_spectrum_serial_ms"] = _event_ms(torch, shared(False), reps)
+    out["shared_spectrum_two_streams_ms"] = _event_ms(torch, shared(True), reps)
+    torch.cuda.synchronize()
+    out["shared_vs_separate_mix_rel_l2"] = float(torch.linalg.norm(mix - ref) / torch.linalg.norm(ref))
+    # what the phasor branch's input costs either way: its own band and
+    # lateral transforms, or the band taken from the shared spectrum
+    for name, fn in (("separate", lambda: pf.reconstruct(x, vp)), ("shared", shared(False))):
+        pf.set_profiling(True)
+        for _ in range(10):
+            fn()
+        torch.cuda.synchronize()
+        st, calls = pf.stage_times()
+        pf.set_profiling(False)
+        out[f"pf_input_{name}_ms"] = sum(st.get(k, 0.0) for k in ("pf_band", "pf_y_forward", "pf_x_forward")) / calls
+    return out
 
 
 def small_fk_bench(torch, nlos, synth, steps=400, with_oracle=True):

@@ -420,6 +420,35 @@ nlos_status_t nlos_plan_band(nlos_plan_t plan, int* k_lo, int* n_freqs);
 nlos_status_t nlos_reconstruct_phasors(nlos_plan_t plan, const void* phasors, void* volume, void* stream);
 
 /*
+ * nlos_reconstruct_moe: both experts of the mixture (Sec. 4.4) from one
+ * transient, with the lateral forward transform shared. The x then y forward
+ * transform of the transient is taken once (the f-k forward spectrum, before
+ * f-k's t/(n-1) ramp); the f-k branch applies the ramp as its temporal stage
+ * reads that spectrum (the ramp commutes with the lateral transforms), and
+ * the phasor-field branch takes each stored pencil's temporal DFT, keeps its
+ * band and writes the Hermitian partner (-kx, -ky) from the mirrored bins
+ * (Sec. 3.1 band transform, Eq. 6 propagation input). Results equal those of
+ * nlos_reconstruct on each plan up to rounding.
+ *   fk_plan: NLOS_FK; pf_plan: NLOS_PHASOR_RSD or NLOS_PHASOR_DENSE; both
+ *   float32 storage, created with their own workspace, for the same grid
+ *   (nx, ny, nt) and the same padded lateral lengths (the same pad_factor).
+ *   transient: device float32 [nx][ny][nt]; volume_fk, volume_pf: device,
+ *   each plan's output layout. The spectrum is written into the f-k plan's
+ *   workspace, the phasor branch's intermediates into its own.
+ *   stream: the f-k branch and the shared transform run here. stream2: the
+ *   phasor branch; it waits for the shared spectrum, and stream waits for the
+ *   phasor branch before the call's last work is done, so everything the call
+ *   wrote is complete once `stream` reaches it. stream2 == stream runs the
+ *   two branches one after the other. Two plan events are created on the
+ *   first two-stream call.
+ * Asynchronous. Errors: INVALID_ARG (NULL pointers, wrong methods, no
+ * workspace, grids or paddings that differ), UNSUPPORTED (16-bit storage),
+ * CUDA (launch). The plans' workspaces must not be in use elsewhere meanwhile.
+ */
+nlos_status_t nlos_reconstruct_moe(nlos_plan_t fk_plan, nlos_plan_t pf_plan, const void* transient, void* volume_fk,
+                                   void* volume_pf, void* stream, void* stream2);
+
+/*
  * Post-processing of reconstructed volumes. All pointers are device memory
  * owned by the caller; volumes are [nx][ny][nz] with depth innermost; every
  * call is asynchronous on stream and allocates nothing. Errors: INVALID_ARG

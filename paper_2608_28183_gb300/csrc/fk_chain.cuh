@@ -282,8 +282,8 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         ctx.tw = p.tw;
         ctx.L_in = p.a;
         ctx.c = c;
-        ctx.m0 = ldm * (float)(t0 + c) * p.t_scale;
-        ctx.m1 = ldm * (float)(t0 + c + IC) * p.t_scale;
+        ctx.m0 = p.t_scale != 0.f ? ldm * (float)(t0 + c) * p.t_scale : ldm;
+        ctx.m1 = p.t_scale != 0.f ? ldm * (float)(t0 + c + IC) * p.t_scale : ldm;
         fftn_run<L, 1, true, false, ChainTmaPairCtx<L, IC, TS>, E>(ctx, j0);
         consumer_sync<L>();
         // split the two real columns: X_c[k] = (Z[k] + conj Z[L-k]) / 2,

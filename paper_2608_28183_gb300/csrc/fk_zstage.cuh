@@ -42,8 +42,10 @@ struct FkFwdCtx {
   int n_in;                  // stored samples of the pencil (the rest is zero padding)
   long long g_off, g_n;      // offset of g in its buffer, the buffer's extent (bounds-checked build)
   int* err;
+  float t_ramp;              // non-zero: sample t is also multiplied by t * t_ramp
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = (valid && (!kGuard || l < n_in) && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), ldmul)
+    const float m = t_ramp != 0.f ? ldmul * (float)l * t_ramp : ldmul;
+    x[0] = (valid && (!kGuard || l < n_in) && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), m)
                                                                          : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
@@ -138,7 +140,7 @@ fk_zstage_kernel(const FkZParams p) {
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
     FkFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul, p.n,
-                                (valid ? pid : 0) * p.n, p.G_n, p.err};
+                                (valid ? pid : 0) * p.n, p.G_n, p.err, p.t_ramp};
     fftn_run<L, 1, kPad2, false>(ctx, j0);
   }
   __syncthreads();

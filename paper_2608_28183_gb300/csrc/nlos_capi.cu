@@ -194,6 +194,8 @@ struct nlos_plan_s {
   std::vector<cudaEvent_t> prof_pool;
   std::vector<int> prof_stage;          // stage index of each recorded event (-1: call start)
   size_t prof_used = 0;
+  // shared-spectrum mixture of experts: spectrum ready, phasor branch done (created on first use)
+  cudaEvent_t moe_ev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -703,7 +705,11 @@ void set_extents(AxisLaunch& l, long long in_n, long long out_n) {
   l.p.err = l.err;
 }
 
-nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStream_t s) {
+// part: 0 the whole reconstruction; 1 only the lateral forward transforms,
+// without the t/(n-1) ramp (the spectrum shared with a phasor-field plan,
+// float32 plans only); 2 the rest after part 1, the ramp applied as the
+// temporal stage loads the spectrum (it commutes with the lateral transforms).
+nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStream_t s, int part) {
   const int st = p->storage;
   const long long a = p->a, b = p->b, n = p->n;
   void* b0 = ws + p->off[0];
@@ -715,7 +721,8 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   const float* inv_s = nullptr;
   const float* inv_s2 = nullptr;
   int sid = 0;
-  NLOS_MARK(p, s, -1);
+  if (part != 2) NLOS_MARK(p, s, -1);
+  const float ramp = 1.0f / (float)(n - 1);
   if (st != kF32) {
     NLOS_CU(launch_volume_scale(H, a * b * n, (int)n, 1.0f / (float)(n - 1), st, kVolumeTarget,
                                 reinterpret_cast<float*>(ws + p->off_part), kScalePartials, scal, s),
@@ -748,14 +755,16 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     ch.discard = 0;   // per stage below (variant 0 on float32 storage)
   }
   AxisLaunch l{};
-  if (p->fused) {
+  if (part == 2) {
+    sid = p->fused ? 1 : 2;
+  } else if (p->fused) {
     // FK1 fused: x forward (real input, t/(n-1), zero-padded, kx in [0, Lx/2]) then y forward
     FkChainLaunch c{};
     c.p = ch;
     c.p.in = H;
     c.p.mid = b0;
     c.p.out = b1;
-    c.p.t_scale = 1.0f / (float)(n - 1);
+    c.p.t_scale = part == 1 ? 0.0f : ramp;
     c.p.s1 = g2a;
     c.p.s2 = g2b;
     c.p.ld_dev_scale = s_in;
@@ -783,8 +792,8 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   // staging of column pairs (n column widths)
   const int nicx = axis_ic_count((int)Lx);
   l.load_mode = (l.tile < nicx || l.tile >= 2 * nicx) ? kLoadRealPair : kLoadReal;
-  l.p.t_len = (int)n;
-  l.p.t_scale = 1.0f / (float)(n - 1);
+  l.p.t_len = part == 1 ? 0 : (int)n;
+  l.p.t_scale = ramp;
   l.p.ld_dev_scale = s_in;
   l.err = err;
   attach_tmap(l);
@@ -799,6 +808,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   NLOS_CU(launch_axis_fft(l, s), "fk y-forward");
   NLOS_MARK(p, s, sid++);
   }
+  if (part == 1) return NLOS_OK;
   // FK3: t forward + Stolt + inverse along z for both Hermitian partners
   FkZParams z{};
   z.G = b1;
@@ -815,6 +825,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   z.npencils = hx * Ly;
   z.ld_scale = g2n;
   z.st_scale = g2n;
+  z.t_ramp = part == 2 ? ramp : 0.0f;
   z.G_n = ws_extent(p, 1);
   z.psi_n = ws_extent(p, 2);
   z.err = err;
@@ -867,8 +878,12 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
 }
 
 // H: the transient; or, when P_in is given (float32 plans only), the band
-// transform is skipped and P_in is the compact phasor field [x][y][F].
-nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol, char* ws, cudaStream_t s) {
+// transform is skipped and P_in is the compact phasor field [x][y][F]; or,
+// when G0 is given (float32 plans only), the band and the lateral forward
+// transforms come from the shared spectrum G0 [Lx/2 + 1][Ly][n] (the x then y
+// forward transforms of the transient, taken once for both experts).
+nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol, char* ws, cudaStream_t s,
+                     const void* G0) {
   const int st = p->storage;
   const long long a = p->a, b = p->b, n = p->n, F = p->F, D = p->D;
   void* b0 = ws + p->off[0];
@@ -880,7 +895,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   const float* inv_s = nullptr;
   int sid = 0;
   NLOS_MARK(p, s, -1);
-  if (st != kF32 && !P_in) {
+  if (st != kF32 && !P_in && !G0) {
     NLOS_CU(launch_volume_scale(H, a * b * n, (int)n, 0.0f, st, kVolumeTarget,
                                 reinterpret_cast<float*>(ws + p->off_part), kScalePartials, scal, s),
             "volume scale");
@@ -919,11 +934,34 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
     NLOS_CU(cudaMemsetAsync(amax, 0, sizeof(unsigned), s), "phasor bound clear");
     bp.amax = amax;
   }
+  const void* P = P_in ? P_in : b0;
+  AxisLaunch l{};
+  if (G0) {
+    // PF1 + PF2 from the shared spectrum: its lateral transforms are already
+    // taken (the y and x forward stages record no time of their own)
+    PfSpecParams sp{};
+    sp.G = static_cast<const float2*>(G0);
+    sp.Phat = static_cast<float2*>(b2);
+    sp.tw = p->tw[(int)Lt];
+    sp.w = p->w;
+    sp.n = (int)n;
+    sp.L = (int)Lt;
+    sp.k_lo = p->k_lo;
+    sp.F = (int)F;
+    sp.Lx = (int)Nu;
+    sp.Ly = (int)Nv;
+    sp.amax = bp.amax;
+    sp.G_n = (Nu / 2 + 1) * Nv * n;
+    sp.Phat_n = ws_extent(p, 2);
+    sp.err = err;
+    NLOS_CU(launch_pf_band_spectrum(sp, s), "pf band from shared spectrum");
+    NLOS_MARK(p, s, sid++);
+    sid += 2;
+  } else {
   if (!P_in) NLOS_CU(launch_pf_band(bp, st, s), "pf band transform");
   NLOS_MARK(p, s, sid++);
   // PF2: top-left padding and 2D forward transform (y then x) of every band slice
-  const void* P = P_in ? P_in : b0;
-  AxisLaunch l = axis(st, (int)Nv, a, P, b1, F, b * F, F, Nv * F, F, (int)b, (int)Nv, 0, g2b, p->tw[(int)Nv], p->tiles[sid]);
+  l = axis(st, (int)Nv, a, P, b1, F, b * F, F, Nv * F, F, (int)b, (int)Nv, 0, g2b, p->tw[(int)Nv], p->tiles[sid]);
   l.err = err;
   attach_tmap(l);
   set_extents(l, P_in ? a * b * F : ws_extent(p, 0), ws_extent(p, 1));
@@ -935,6 +973,7 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
   set_extents(l, ws_extent(p, 1), ws_extent(p, 2));
   NLOS_CU(launch_axis_fft(l, s), "pf x-forward");
   NLOS_MARK(p, s, sid++);
+  }
   if (p->d.method == NLOS_PHASOR_DENSE) {
     // PF3, dense kernel: C = sum_f Phat * Khat (Alg. 3), every pixel written
     PfDenseParams dp{static_cast<const float2*>(b2), p->Kd, static_cast<float2*>(b1), Nu * Nv, (int)F, (int)D};
@@ -971,8 +1010,9 @@ nlos_status_t run_pf(nlos_plan_s* p, const void* H, const void* P_in, void* vol,
           NLOS_CU(cudaMemsetAsync(amax, 0, sizeof(unsigned), s), "phasor bound clear");
           NLOS_CU(launch_absmax(static_cast<const float*>(P), 2 * a * b * F, amax, s), "phasor bound");
         }
+        // (phasors taken from the shared spectrum had their own maximum recorded)
         int e2 = 0;
-        frexp(1.5 * (double)a * b * g2a * g2b, &e2);
+        frexp(G0 ? 1.5 : 1.5 * (double)a * b * g2a * g2b, &e2);
         up.amax = amax;
         up.abound_exp = e2;
       }
@@ -1031,7 +1071,7 @@ nlos_status_t run_plan(nlos_plan_s* p, const void* H, void* vol, void* ws, cudaS
   // (the runtime is shared with the host application) must not be reported
   // against this sequence's launches
   cudaGetLastError();
-  return p->d.method == NLOS_FK ? run_fk(p, H, vol, w, s) : run_pf(p, H, nullptr, vol, w, s);
+  return p->d.method == NLOS_FK ? run_fk(p, H, vol, w, s, 0) : run_pf(p, H, nullptr, vol, w, s, nullptr);
 }
 
 // Dense method (Alg. 3): Khat[kx][ky][f][d] = DFT2 of the spatial kernel on
@@ -1376,9 +1416,49 @@ nlos_status_t nlos_reconstruct_phasors(nlos_plan_t p, const void* phasors, void*
   if (!phasors || !volume) return fail(NLOS_ERR_INVALID_ARG, "phasors/volume is NULL");
   if (!p->ws) return fail(NLOS_ERR_INVALID_ARG, "plan was created without a workspace");
   cudaGetLastError();
-  return run_pf(p, nullptr, phasors, volume, static_cast<char*>(p->ws), static_cast<cudaStream_t>(stream));
+  return run_pf(p, nullptr, phasors, volume, static_cast<char*>(p->ws), static_cast<cudaStream_t>(stream), nullptr);
 }
 
+
+nlos_status_t nlos_reconstruct_moe(nlos_plan_t fk, nlos_plan_t pf, const void* transient, void* volume_fk,
+                                   void* volume_pf, void* stream, void* stream2) {
+  if (!fk || !pf) return fail(NLOS_ERR_INVALID_ARG, "plan is NULL");
+  if (!transient || !volume_fk || !volume_pf) return fail(NLOS_ERR_INVALID_ARG, "transient/volume is NULL");
+  if (fk->d.method != NLOS_FK || pf->d.method == NLOS_FK)
+    return fail(NLOS_ERR_INVALID_ARG, "needs an f-k plan and a phasor-field plan");
+  if (!fk->ws || !pf->ws) return fail(NLOS_ERR_INVALID_ARG, "both plans need their own workspace");
+  if (fk->storage != kF32 || pf->storage != kF32)
+    return fail(NLOS_ERR_UNSUPPORTED, "the shared spectrum needs float32 plans");
+  if (fk->a != pf->a || fk->b != pf->b || fk->n != pf->n || fk->Lx != pf->Lx || fk->Ly != pf->Ly)
+    return fail(NLOS_ERR_INVALID_ARG, "plans differ in grid (%dx%dx%d vs %dx%dx%d) or lateral padding", fk->a, fk->b,
+                fk->n, pf->a, pf->b, pf->n);
+  cudaStream_t s = static_cast<cudaStream_t>(stream), s2 = static_cast<cudaStream_t>(stream2);
+  const bool two = s2 != s;
+  if (two)
+    for (cudaEvent_t& e : fk->moe_ev)
+      if (!e) NLOS_CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "mixture-of-experts event");
+  cudaGetLastError();
+  char* wf = static_cast<char*>(fk->ws);
+  // the shared spectrum lives in the f-k plan's second buffer, which the
+  // f-k temporal stage only reads and the phasor branch only reads
+  const void* G0 = wf + fk->off[1];
+  nlos_status_t st = run_fk(fk, transient, volume_fk, wf, s, 1);
+  if (st != NLOS_OK) return st;
+  if (two) {
+    NLOS_CU(cudaEventRecord(fk->moe_ev[0], s), "mixture-of-experts order");
+    NLOS_CU(cudaStreamWaitEvent(s2, fk->moe_ev[0], 0), "mixture-of-experts order");
+  }
+  st = run_pf(pf, nullptr, nullptr, volume_pf, static_cast<char*>(pf->ws), s2, G0);
+  if (st != NLOS_OK) return st;
+  st = run_fk(fk, transient, volume_fk, wf, s, 2);
+  if (st != NLOS_OK) return st;
+  if (two) {
+    // join: the next call's spectrum must not overwrite what the phasor branch still reads
+    NLOS_CU(cudaEventRecord(fk->moe_ev[1], s2), "mixture-of-experts order");
+    NLOS_CU(cudaStreamWaitEvent(s, fk->moe_ev[1], 0), "mixture-of-experts order");
+  }
+  return NLOS_OK;
+}
 
 nlos_status_t nlos_reconstruct_host_many(nlos_plan_t p, const void* const* transients_host, void* const* volumes_host,
                                          int n, void* stream) {
@@ -1830,6 +1910,8 @@ nlos_status_t nlos_plan_destroy(nlos_plan_t p) {
   cudaDeviceSynchronize();
   destroy_pipe(p->pipe);
   for (cudaEvent_t e : p->prof_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->moe_ev)
+    if (e) cudaEventDestroy(e);
   for (void* v : p->allocs) cudaFree(v);
   delete p;
   return NLOS_OK;

@@ -97,6 +97,8 @@ struct FkZParams {
   float ld_scale;              // multiplies forward loads
   const float* ld_dev_scale;   // optional device scalar multiplying forward loads
   float st_scale;              // multiplies stored values
+  float t_ramp;                // non-zero: forward loads also multiplied by t * t_ramp (the
+                               // spectrum was taken without the t/(n-1) ramp)
   long long G_n, psi_n;        // element extents (bounds-checked build; 0: unchecked)
   int* err;                    // device error word (bounds-checked build), may be null
 };
@@ -114,7 +116,7 @@ struct FkChainParams {
   int a, b, n, L;
   int nchunks;                 // n / 16
   int lag;                     // chunks between a chunk's first- and second-transform tickets (set by the launcher)
-  float t_scale;               // forward: ramp factor 1/(n-1) (value * t * t_scale)
+  float t_scale;               // forward: ramp factor 1/(n-1) (value * t * t_scale; 0: no ramp)
   float s1, s2;                // scales of the values the first / second transform stores
   const float* ld_dev_scale;   // forward: optional device scalar multiplying the input
   const float* st_dev_scale;   // inverse: optional device scalar multiplying the output
@@ -159,6 +161,25 @@ struct PfBandParams {
   int* err;                    // device error word (bounds-checked build), may be null
 };
 cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s);
+
+// PF1 + PF2 from a lateral spectrum shared with f-k (mixture of experts,
+// Sec. 4.4): G holds the x then y forward transforms of the transient,
+// kx in [0, Lx/2], ky in [0, Ly), n samples per pencil (the f-k forward
+// spectrum taken without its ramp). The temporal DFT Z of each pencil (length
+// L >= n, zero beyond n) gives Phat(kx, ky, f) = w(f) Z(k_lo + f) and, for
+// 0 < kx < Lx/2, the Hermitian partner of the real transient:
+// Phat(Lx - kx, -ky, f) = w(f) conj(Z(L - k_lo - f)). Float32 only.
+struct PfSpecParams {
+  const float2* G;             // [Lx/2 + 1][Ly][n]
+  float2* Phat;                // [Lx][Ly][F]
+  const float2* tw;            // twiddles for L
+  const float* w;              // [F]
+  int n, L, k_lo, F, Lx, Ly;
+  unsigned* amax;              // when set: atomicMax of max |Re|, |Im| of the stored Phat (float bits)
+  long long G_n, Phat_n;       // element extents (bounds-checked build; 0: unchecked)
+  int* err;                    // device error word (bounds-checked build), may be null
+};
+cudaError_t launch_pf_band_spectrum(const PfSpecParams& p, cudaStream_t s);
 
 // Photon binning into the compact phasor field P[pixel][f] (float32 complex):
 // P += w_f * exp(-2 pi i (k_lo + f) b / n) per kept photon.

@@ -121,6 +121,112 @@ cudaError_t launch_pf_band(const PfBandParams& p, int storage, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
+// PF1 + PF2 from the shared lateral spectrum (Sec. 4.4 mixture of experts):
+// one temporal DFT per stored pencil (kx, ky), kx in [0, Lx/2], writes the
+// band of (kx, ky) and, from the mirrored bins, that of (Lx - kx, -ky); the
+// rows kx = 0 and kx = Lx/2 are their own partners' rows and store once.
+// ---------------------------------------------------------------------------
+template <int L>
+struct PfSpecCtx {
+  static constexpr int SSTRIDE = 1;
+  static constexpr bool kSmemInput = false;
+  const float2* g;
+  float2* P0;                  // band row of (kx, ky)
+  float2* P1;                  // band row of the partner, or null
+  float2* W;
+  const float2* tw;
+  const float* w;
+  int k_lo, F, n_in;
+  bool valid;
+  long long g_off, G_n, off0, off1, P_n;   // offsets and extents (bounds-checked build)
+  int* err;
+  mutable float m = 0.f;       // max |component| of what this thread stored
+  __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
+    x[0] = (valid && l < n_in && bchk(g_off + l, G_n, err)) ? __ldg(g + l) : make_float2(0.f, 0.f);
+  }
+  __device__ __forceinline__ float2* sm(int) const { return W; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
+    if (!valid) return;
+    int f = l - k_lo;
+    float2 v;
+    if (f >= 0 && f < F) {
+      if (!bchk(off0 + f, P_n, err)) return;
+      v = cscale(x[0], __ldg(w + f));
+      P0[f] = v;
+    } else {
+      f = ((L - l) & (L - 1)) - k_lo;
+      if (!P1 || f < 0 || f >= F || !bchk(off1 + f, P_n, err)) return;
+      v = cscale(cconj(x[0]), __ldg(w + f));
+      P1[f] = v;
+    }
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+};
+
+template <int L>
+__global__ void __launch_bounds__(PfBandTile<L>::THREADS)
+pf_band_spectrum_kernel(const PfSpecParams p) {
+  using S = FftShape<L>;
+  constexpr int PPC = PfBandTile<L>::PPC;
+  extern __shared__ float2 pfs_sm[];
+  const int w = threadIdx.x / S::TPC;
+  const int j0 = threadIdx.x % S::TPC;
+  const long long np = (long long)(p.Lx / 2 + 1) * p.Ly;
+  const long long pid = (long long)blockIdx.x * PPC + w;
+  const bool valid = pid < np;
+  const long long q = valid ? pid : 0;
+  const int kx = (int)(q / p.Ly);
+  const int ky = (int)(q % p.Ly);
+  const long long o0 = q * p.F;                     // (kx Ly + ky) F
+  const long long o1 = ((long long)(p.Lx - kx) * p.Ly + ((p.Ly - ky) & (p.Ly - 1))) * p.F;
+  const bool partner = kx > 0 && 2 * kx < p.Lx;
+  PfSpecCtx<L> ctx{p.G + q * p.n, p.Phat + o0, partner ? p.Phat + o1 : nullptr, pfs_sm + w * S::SMEM, p.tw, p.w,
+                   p.k_lo, p.F, p.n, valid, q * p.n, p.G_n, o0, o1, p.Phat_n, p.err};
+  fftn_run<L, 1, false, false>(ctx, j0);
+  if (p.amax) {
+    constexpr int TH = PfBandTile<L>::THREADS;
+    constexpr int WID = TH < 32 ? TH : 32;
+    constexpr unsigned MASK = TH < 32 ? ((1u << TH) - 1u) : 0xffffffffu;
+    float m = ctx.m;
+#pragma unroll
+    for (int o = WID / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(MASK, m, o, WID));
+    if ((threadIdx.x % WID) == 0) atomicMax(p.amax, __float_as_uint(m));
+  }
+}
+
+template <int L>
+static cudaError_t launch_spec_one(const PfSpecParams& p, cudaStream_t s) {
+  using T = PfBandTile<L>;
+  auto k = pf_band_spectrum_kernel<L>;
+  if (T::SMEM > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+    if (e != cudaSuccess) return e;
+  }
+  const long long np = (long long)(p.Lx / 2 + 1) * p.Ly;
+  const long long blocks = (np + T::PPC - 1) / T::PPC;
+  k<<<(unsigned)blocks, T::THREADS, T::SMEM, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pf_band_spectrum(const PfSpecParams& p, cudaStream_t s) {
+  if (p.F <= 0 || p.n <= 0 || p.n > p.L || p.Lx < 2 || p.Ly < 1 || (p.Ly & (p.Ly - 1)) ||
+      p.k_lo < 1 || p.k_lo + p.F > p.L / 2)
+    return cudaErrorInvalidValue;
+  switch (p.L) {
+    case 16: return launch_spec_one<16>(p, s);
+    case 32: return launch_spec_one<32>(p, s);
+    case 64: return launch_spec_one<64>(p, s);
+    case 128: return launch_spec_one<128>(p, s);
+    case 256: return launch_spec_one<256>(p, s);
+    case 512: return launch_spec_one<512>(p, s);
+    case 1024: return launch_spec_one<1024>(p, s);
+    case 2048: return launch_spec_one<2048>(p, s);
+    case 4096: return launch_spec_one<4096>(p, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // PF3: depth sum (Alg. 4 inner loop; Sec. 4.3 propagation sum). One CTA owns a
 // chunk of up to 16 pixels that share the radial index pair (i0, i1) and 128
 // depths; each thread keeps 16 complex accumulators (one per pixel) for its

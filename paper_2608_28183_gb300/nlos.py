@@ -37,7 +37,8 @@ EXPORTED = ["nlos_plan_desc_default", "nlos_plan_create", "nlos_plan_query", "nl
             "nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda",
             "nlos_bin_transient", "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors",
             "nlos_reconstruct_host_many", "nlos_debug_fail_allocation", "nlos_selftest_umma",
-            "nlos_ffma_rate_launch", "nlos_plan_memory", "nlos_server_memory", "nlos_selftest_bounds"]
+            "nlos_ffma_rate_launch", "nlos_plan_memory", "nlos_server_memory", "nlos_selftest_bounds",
+            "nlos_reconstruct_moe"]
 
 
 class PlanDesc(ctypes.Structure):
@@ -116,6 +117,7 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_bin_phasors.argtypes = [vp, vp, vp, ll, u32, u32, ctypes.c_int, vp, vp]
     lib.nlos_plan_band.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.nlos_reconstruct_phasors.argtypes = [vp, vp, vp, vp]
+    lib.nlos_reconstruct_moe.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     lib.nlos_reconstruct_host_many.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, vp]
     lib.nlos_debug_fail_allocation.argtypes = [ctypes.c_int]
     lib.nlos_debug_fail_allocation.restype = None
@@ -124,7 +126,8 @@ def load_library(path: str = LIB_PATH):
     lib.nlos_ffma_rate_launch.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), vp]
     lib.nlos_ffma_rate_launch.restype = ctypes.c_int
     for name in ("nlos_max_image", "nlos_moe_mix", "nlos_coherence_merge", "nlos_dda", "nlos_bin_transient",
-                 "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors", "nlos_reconstruct_host_many"):
+                 "nlos_bin_phasors", "nlos_plan_band", "nlos_reconstruct_phasors", "nlos_reconstruct_host_many",
+                 "nlos_reconstruct_moe"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("nlos_plan_autotune", "nlos_plan_get_tiles", "nlos_plan_set_tiles", "nlos_batch_create",
                  "nlos_batch_launch", "nlos_batch_destroy", "nlos_plan_create_ex", "nlos_server_create",
@@ -522,6 +525,26 @@ def max_image(volume, take_sqrt: bool = False, image=None, stream=None):
     _check(_lib.nlos_max_image(ctypes.c_void_p(volume.data_ptr()), nx, ny, nz, int(bool(take_sqrt)),
                                ctypes.c_void_p(image.data_ptr()), _stream_ptr(stream)))
     return image
+
+
+def reconstruct_moe(fk_plan, pf_plan, transient, volume_fk=None, volume_pf=None, stream=None, stream2=None):
+    """Both experts of the mixture (Sec. 4.4) from one transient with the
+    lateral forward transform shared: f-k on `stream`, the phasor branch on
+    `stream2` (None: after the f-k branch on `stream`); `stream` waits for
+    both. Float32 plans with their own workspaces, same grid and padding.
+    Returns (volume_fk, volume_pf)."""
+    if volume_fk is None:
+        volume_fk = fk_plan.empty_volume()
+    if volume_pf is None:
+        volume_pf = pf_plan.empty_volume()
+    fk_plan._check_io(transient, volume_fk)
+    pf_plan._check_io(transient, volume_pf)
+    s1 = _stream_ptr(stream)
+    s2 = s1 if stream2 is None else _stream_ptr(stream2)
+    _check(_lib.nlos_reconstruct_moe(fk_plan._h, pf_plan._h, ctypes.c_void_p(transient.data_ptr()),
+                                     ctypes.c_void_p(volume_fk.data_ptr()), ctypes.c_void_p(volume_pf.data_ptr()),
+                                     s1, s2))
+    return volume_fk, volume_pf
 
 
 def moe_mix(img_fk, img_rsd, beta: float = 0.3, eps: float = 1e-3, out=None, stream=None):

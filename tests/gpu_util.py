@@ -3,8 +3,10 @@ import numpy as np
 
 
 def rel_l2(got, ref):
-    got = np.asarray(got, dtype=np.float64)
-    ref = np.asarray(ref, dtype=np.float64)
+    """||got - ref|| / ||ref||; complex inputs compare as complex."""
+    cpx = np.iscomplexobj(got) or np.iscomplexobj(ref)
+    got = np.asarray(got, dtype=np.complex128 if cpx else np.float64)
+    ref = np.asarray(ref, dtype=np.complex128 if cpx else np.float64)
     den = np.linalg.norm(ref)
     return float(np.linalg.norm(got - ref) / den) if den > 0 else float(np.linalg.norm(got))
 

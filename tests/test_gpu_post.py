@@ -181,3 +181,81 @@ def test_post_rejects_bad_arguments():
         nlos.dda([r] * 17)
     with pytest.raises(nlos.NlosError, match="INVALID_ARG"):
         nlos.moe_mix(r, r, eps=-1.0)
+
+
+# the mixture's two experts from one shared lateral spectrum (Sec. 4.4):
+# geometry, phasor method, f-k lateral stages separate, two streams, f-k output
+SHARED = [
+    (GEOM, "pf", False, True, "magnitude"),
+    (GEOM, "pf", True, False, "magnitude"),
+    (synth.Geometry(48, 64, 160, 24e-12, 0.8, 1.0), "pf", False, True, "complex"),
+    (synth.Geometry(16, 16, 200, 24e-12, 0.6, 0.6), "pf_dense", False, True, "magnitude"),
+]
+
+
+@pytest.mark.parametrize("geom,method,sep,two,fk_out", SHARED,
+                         ids=["32x32-fused-2streams", "32x32-separate-1stream", "48x64x160-complex",
+                              "16x16x200-dense"])
+def test_moe_shared_spectrum(geom, method, sep, two, fk_out):
+    """Both experts from one x/y forward transform: each volume matches the
+    oracle and the plan's own reconstruction of the same transient."""
+    from oracle import rsd_direct
+    from paper_2608_28183_gb300 import nlos
+    D, dmin, dmax = DEPTHS
+    H = _frames(geom, 1, seed=17, peak=300.0)[0]
+    Hx = exact_input(H, torch.float32)
+    fkp = nlos.plan_for_capture(geom, "fk", separate_axes=sep, output=fk_out)
+    pfp = nlos.plan_for_capture(geom, method, n_depths=D, depth_min_m=dmin, depth_max_m=dmax)
+    x = to_device(H, torch.float32)
+    s2 = torch.cuda.Stream() if two else None
+    for _ in range(2):                  # the second call reuses both workspaces and the events
+        vf, vp = nlos.reconstruct_moe(fkp, pfp, x, stream2=s2)
+    torch.cuda.synchronize()
+    cpx = fk_out == "complex"
+    got_fk = vf.cpu().numpy().astype(np.complex128 if cpx else np.float64)
+    got_pf = vp.cpu().numpy().astype(np.float64)
+    ref_fk = fk.fk_reconstruct(Hx, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m, return_complex=cpx)
+    assert np.linalg.norm(got_fk - ref_fk) / np.linalg.norm(ref_fk) <= 1e-5
+    oplan = pf.make_plan(geom.nx, geom.ny, geom.nt, geom.bin_width_s, geom.wall_w_m, geom.wall_h_m, D, dmin, dmax)
+    if method == "pf":
+        ref_pf = pf.pf_reconstruct(Hx, oplan)
+    else:
+        P = pf.phasor_field(Hx, oplan)
+        ref_pf = np.abs(rsd_direct.rsd_direct(P, oplan.band.freqs, oplan.band.weights, oplan.depths,
+                                              geom.wall_w_m, geom.wall_h_m))
+    assert rel_l2(got_pf, ref_pf) <= 1e-5
+    assert same_peak(got_pf, ref_pf)
+    # against each plan's own path on the same transient
+    own_fk = fkp.reconstruct(x).cpu().numpy()
+    own_pf = pfp.reconstruct(x).cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(got_fk - own_fk) / np.linalg.norm(own_fk) <= 2e-6
+    assert rel_l2(got_pf, own_pf) <= 2e-6
+
+
+def test_moe_shared_spectrum_rejects_mismatched_plans():
+    """The C entry refuses plans it cannot share a spectrum between (status
+    codes, nothing launched); a zero transient gives zero volumes."""
+    import ctypes
+    from paper_2608_28183_gb300 import nlos
+    D, dmin, dmax = DEPTHS
+    fkp = nlos.plan_for_capture(GEOM, "fk")
+    pfp = nlos.plan_for_capture(GEOM, "pf", n_depths=D, depth_min_m=dmin, depth_max_m=dmax)
+    x = torch.zeros((GEOM.nx, GEOM.ny, GEOM.nt), device="cuda")
+    vf, vp = fkp.empty_volume(), pfp.empty_volume()
+    other = nlos.plan_for_capture(synth.Geometry(32, 32, 128, 24e-12, 0.8, 0.8), "pf", n_depths=D,
+                                  depth_min_m=dmin, depth_max_m=dmax)
+    half = nlos.plan_for_capture(GEOM, "pf", "f16", n_depths=D, depth_min_m=dmin, depth_max_m=dmax)
+
+    def call(a, b):
+        return nlos._lib.nlos_reconstruct_moe(a._h, b._h, ctypes.c_void_p(x.data_ptr()),
+                                              ctypes.c_void_p(vf.data_ptr()), ctypes.c_void_p(vp.data_ptr()),
+                                              None, None)
+    invalid, unsupported = 1, 4
+    assert nlos.STATUS[invalid] == "INVALID_ARG" and nlos.STATUS[unsupported] == "UNSUPPORTED"
+    assert call(fkp, other) == invalid        # grids differ
+    assert call(fkp, fkp) == invalid          # two f-k plans
+    assert call(pfp, fkp) == invalid          # plans swapped
+    assert call(fkp, half) == unsupported     # 16-bit storage
+    nlos.reconstruct_moe(fkp, pfp, x, vf, vp)
+    torch.cuda.synchronize()
+    assert float(vf.abs().max()) == 0.0 and float(vp.abs().max()) == 0.0
