@@ -4,6 +4,8 @@
 #include "nlos_bounds.cuh"
 #include "nlos_fft.cuh"
 #include "nlos_internal.h"
+#include "nlos_tma.cuh"
+#include "nlos_umma.cuh"
 
 namespace nlos {
 
@@ -11,86 +13,232 @@ namespace nlos {
 // PF1: P[x][y][f] = w(f) * sum_t H[x][y][t] exp(-2 pi i (k_lo + f) t / n)
 // (Sec. 3.1 phasor field; w(f) is the virtual wave's spectrum, folded here
 // instead of inside the depth sum.)
+// Two real pencils share one complex transform: z = h0 + i h1, Z = DFT(z),
+// then X0[k] = (Z[k] + conj Z[L - k]) / 2 and X1[k] = (Z[k] - conj Z[L - k]) / (2i).
+// The transform keeps the band bins and their mirrors in shared memory; the
+// pair's threads then split them and store both pencils' bands.
 // ---------------------------------------------------------------------------
-template <int L, class TR, class TS>
+template <int L, class TR, bool kStaged>
 struct PfBandCtx {
   static constexpr int SSTRIDE = 1;
-  static constexpr bool kSmemInput = false;
-  const TR* h;
-  TS* P;
+  // staged: the pair's samples sit at the start of the transform's own
+  // buffer, so the first pass reads them all before it writes
+  static constexpr bool kSmemInput = kStaged;
+  const TR* h0;                // global pencil, or (staged) the pair's samples in shared memory
+  bool has1;                   // the pair's second pencil exists
+  float2* O;                   // [2F]: Z[k_lo + f], then Z[L - k_lo - f]
   float2* W;
   const float2* tw;
-  const float* w;
   int k_lo, F;
-  bool valid;
-  float ldmul, stmul;
-  int accumulate;
+  float ldmul;
   int n_in;                    // samples of the pencil; the DFT runs over L >= n_in
-  long long h_off, H_n, p_off, P_n;   // offsets of h / P in their buffers, the extents (bounds-checked build)
+  long long h_off, H_n;        // offset of h0 in H, H's extent (bounds-checked build)
   int* err;
-  mutable float m = 0.f;       // max |component| of what this thread stored
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = (valid && l < n_in && bchk(h_off + l, H_n, err)) ? make_float2(Real<TR>::get(h + l) * ldmul, 0.f)
-                                                           : make_float2(0.f, 0.f);
+    const bool in = l < n_in;
+    float re = 0.f, im = 0.f;
+    if (kStaged) {
+      if (in) re = Real<TR>::get(h0 + l) * ldmul;
+      if (in && has1) im = Real<TR>::get(h0 + n_in + l) * ldmul;
+    } else {
+      if (in && bchk(h_off + l, H_n, err)) re = Real<TR>::get(h0 + l) * ldmul;
+      if (in && has1 && bchk(h_off + n_in + l, H_n, err)) im = Real<TR>::get(h0 + n_in + l) * ldmul;
+    }
+    x[0] = make_float2(re, im);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     const int f = l - k_lo;
-    if (!valid || f < 0 || f >= F) return;
-    if (!bchk(p_off + f, P_n, err)) return;
-    float2 v = cscale(x[0], __ldg(w + f) * stmul);
-    if (accumulate) v = cadd(v, Cpx<TS>::get(P + f));
-    Cpx<TS>::put(P + f, v);
-    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    if (f >= 0 && f < F) O[f] = x[0];
+    const int g = ((L - l) & (L - 1)) - k_lo;
+    if (g >= 0 && g < F) O[F + g] = x[0];
   }
 };
 
 template <int L> struct PfBandTile {
-  static constexpr int PPC = L <= 256 ? 8 : (L <= 1024 ? 4 : 2);
+  // transforms (pencil pairs) per CTA
+  static constexpr int PPC = L <= 256 ? 8 : 2;
   static constexpr int THREADS = PPC * (L / 16);
-  static constexpr size_t SMEM = (L > 16) ? sizeof(float2) * PPC * FftShape<L>::SMEM : 0;
+  static constexpr size_t BUF = sizeof(float2) * PPC * FftShape<L>::SMEM;   // one slot of transform buffers
+  // slots of transform buffers (two when staged), the band bins, two barriers
+  static constexpr size_t smem(int F, bool staged) {
+    return (staged ? 2 : 1) * BUF + sizeof(float2) * PPC * 2 * F + 2 * sizeof(uint64_t);
+  }
 };
 
+constexpr int kBandWaitLimit = 1 << 21;   // polls of a staged-load barrier (~1 s in all)
+
+// split the transform of one pencil pair into both pencils' bands (w(f) and
+// the store scale applied) and store them; returns the largest |component| stored
+template <class TS>
+__device__ __forceinline__ float band_split_store(const PfBandParams& p, const float2* O, long long q, bool has1,
+                                                  int j0, int TPC) {
+  float m = 0.f;
+  TS* P0 = static_cast<TS*>(p.P) + q * p.F;
+  TS* P1 = P0 + p.F;
+  for (int f = j0; f < p.F; f += TPC) {
+    const float2 z = O[f], c = cconj(O[p.F + f]);
+    const float s = 0.5f * __ldg(p.w + f) * p.st_scale;
+    float2 x0 = make_float2(s * (z.x + c.x), s * (z.y + c.y));
+    float2 x1 = make_float2(s * (z.y - c.y), -s * (z.x - c.x));   // (z - c) / (2i)
+    if (bchk(q * p.F + f, p.P_n, p.err)) {
+      if (p.accumulate) x0 = cadd(x0, Cpx<TS>::get(P0 + f));
+      Cpx<TS>::put(P0 + f, x0);
+      m = fmaxf(m, fmaxf(fabsf(x0.x), fabsf(x0.y)));
+    }
+    if (has1 && bchk((q + 1) * p.F + f, p.P_n, p.err)) {
+      if (p.accumulate) x1 = cadd(x1, Cpx<TS>::get(P1 + f));
+      Cpx<TS>::put(P1 + f, x1);
+      m = fmaxf(m, fmaxf(fabsf(x1.x), fabsf(x1.y)));
+    }
+  }
+  return m;
+}
+
+template <int L>
+__device__ __forceinline__ void band_amax(const PfBandParams& p, float m) {
+  if (!p.amax) return;
+  // the bound the float32 depth sum scales its phasors by (see PfBandParams)
+  // (blocks of short transforms have fewer than 32 threads: reduce over
+  // the lanes that exist)
+  constexpr int TH = PfBandTile<L>::THREADS;
+  constexpr int WID = TH < 32 ? TH : 32;
+  constexpr unsigned MASK = TH < 32 ? ((1u << TH) - 1u) : 0xffffffffu;
+#pragma unroll
+  for (int o = WID / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(MASK, m, o, WID));
+  if ((threadIdx.x % WID) == 0) atomicMax(p.amax, __float_as_uint(m));
+}
+
+// one pass over the pairs, samples loaded by each thread from global memory
 template <int L, class TR, class TS>
 __global__ void __launch_bounds__(PfBandTile<L>::THREADS)
 pf_band_kernel(const PfBandParams p) {
   using S = FftShape<L>;
-  constexpr int PPC = PfBandTile<L>::PPC;
-  extern __shared__ float2 pfb_sm[];
+  using T = PfBandTile<L>;
+  extern __shared__ __align__(16) unsigned char pfb_sm[];
   const int w = threadIdx.x / S::TPC;
   const int j0 = threadIdx.x % S::TPC;
-  const long long pid = (long long)blockIdx.x * PPC + w;
-  const bool valid = pid < p.npencils;
-  const long long q = valid ? pid : 0;
+  const long long q0 = 2 * ((long long)blockIdx.x * T::PPC + w);    // the pair's first pencil
+  const bool v0 = q0 < p.npencils, v1 = q0 + 1 < p.npencils;
+  const long long q = v0 ? q0 : 0;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
-  PfBandCtx<L, TR, TS> ctx{static_cast<const TR*>(p.H) + q * p.n, static_cast<TS*>(p.P) + q * p.F,
-                           pfb_sm + w * S::SMEM, p.tw, p.w, p.k_lo, p.F, valid, ldmul, p.st_scale, p.accumulate,
-                           p.n, q * p.n, p.H_n, q * p.F, p.P_n, p.err};
+  float2* W = reinterpret_cast<float2*>(pfb_sm) + w * S::SMEM;
+  float2* O = reinterpret_cast<float2*>(pfb_sm + T::BUF) + (size_t)w * 2 * p.F;
+  PfBandCtx<L, TR, false> ctx{static_cast<const TR*>(p.H) + q * p.n, v1, O, W, p.tw, p.k_lo, p.F, ldmul, p.n,
+                              q * p.n, p.H_n, p.err};
   fftn_run<L, 1, false, false>(ctx, j0);
-  if (p.amax) {
-    // the bound the float32 depth sum scales its phasors by (see PfBandParams)
-    // (blocks of short transforms have fewer than 32 threads: reduce over
-    // the lanes that exist)
-    constexpr int TH = PfBandTile<L>::THREADS;
-    constexpr int WID = TH < 32 ? TH : 32;
-    constexpr unsigned MASK = TH < 32 ? ((1u << TH) - 1u) : 0xffffffffu;
-    float m = ctx.m;
-#pragma unroll
-    for (int o = WID / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(MASK, m, o, WID));
-    if ((threadIdx.x % WID) == 0) atomicMax(p.amax, __float_as_uint(m));
+  __syncthreads();
+  const float m = v0 ? band_split_store<TS>(p, O, q, v1, j0, S::TPC) : 0.f;
+  band_amax<L>(p, m);
+}
+
+// persistent CTAs over sets of PPC pairs (2 PPC consecutive pencils): one
+// thread stages the next set's samples with bulk copies into the other slot
+// of transform buffers while the CTA transforms the current set
+template <int L, class TR, class TS>
+__global__ void __launch_bounds__(PfBandTile<L>::THREADS)
+pf_band_staged_kernel(const PfBandParams p, const long long nsets) {
+  using S = FftShape<L>;
+  using T = PfBandTile<L>;
+  extern __shared__ __align__(128) unsigned char pfb_sm[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(pfb_sm + 2 * T::BUF + sizeof(float2) * T::PPC * 2 * p.F);
+  const int w = threadIdx.x / S::TPC;
+  const int j0 = threadIdx.x % S::TPC;
+  const size_t pbytes = (size_t)p.n * sizeof(TR);                 // one pencil (a multiple of 16)
+  auto slot_buf = [&](int slot, int t) {
+    return reinterpret_cast<float2*>(pfb_sm + slot * T::BUF) + t * S::SMEM;
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
   }
+  __syncthreads();
+  const TR* H = static_cast<const TR*>(p.H);
+  auto issue = [&](long long set, int slot) {
+    const long long first = 2 * T::PPC * set;
+    const long long cnt = p.npencils - first < 2 * T::PPC ? p.npencils - first : 2 * T::PPC;
+    mbar_arrive_expect_tx(&bar[slot], (uint32_t)(cnt * pbytes));
+    for (int t = 0; 2 * t < cnt; ++t) {
+      const long long k = cnt - 2 * t < 2 ? cnt - 2 * t : 2;
+      bulk_load(slot_buf(slot, t), H + (first + 2 * t) * p.n, (uint32_t)(k * pbytes), &bar[slot]);
+    }
+  };
+  long long set = blockIdx.x;
+  if (threadIdx.x == 0 && set < nsets) issue(set, 0);
+  const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
+  float2* O = reinterpret_cast<float2*>(pfb_sm + 2 * T::BUF) + (size_t)w * 2 * p.F;
+  float m = 0.f;
+  for (int k = 0; set < nsets; ++k, set += gridDim.x) {
+    const int slot = k & 1;
+    const long long next = set + gridDim.x;
+    if (threadIdx.x == 0 && next < nsets) issue(next, slot ^ 1);
+    // every thread waits for the slot; a wait that gives up anywhere sends
+    // the whole CTA out (after a last bounded wait for its copies in flight)
+    const bool ok = __syncthreads_and(mbar_wait_bounded(&bar[slot], (k >> 1) & 1, kBandWaitLimit));
+    if (!ok) {
+      if (threadIdx.x == 0) {
+        if (p.err) atomicExch(p.err, kDevErrTmaTimeout);
+        mbar_wait_bounded(&bar[slot], (k >> 1) & 1, kBandWaitLimit);
+        if (next < nsets) mbar_wait_bounded(&bar[slot ^ 1], ((k + 1) >> 1) & 1, kBandWaitLimit);
+      }
+      return;
+    }
+    const long long q0 = 2 * (set * T::PPC + w);
+    const bool v0 = q0 < p.npencils, v1 = q0 + 1 < p.npencils;
+    float2* W = slot_buf(slot, w);
+    PfBandCtx<L, TR, true> ctx{reinterpret_cast<const TR*>(W), v1, O, W, p.tw, p.k_lo, p.F, ldmul, p.n, 0, 0, p.err};
+    fftn_run<L, 1, false, false>(ctx, j0);
+    __syncthreads();
+    if (v0) m = fmaxf(m, band_split_store<TS>(p, O, q0, v1, j0, S::TPC));
+    // the slot and the band bins are rewritten next: order this iteration's
+    // shared-memory accesses before the coming bulk copies and transforms
+    fence_proxy_async_smem();
+    __syncthreads();
+  }
+  band_amax<L>(p, m);
+}
+
+static int band_sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    sms = v > 0 ? v : 1;
+  }
+  return sms;
 }
 
 template <int L, class TR, class TS>
 static cudaError_t launch_band_one(const PfBandParams& p, cudaStream_t s) {
   using T = PfBandTile<L>;
+  const long long pairs = (p.npencils + 1) / 2;
+  const long long nsets = (pairs + T::PPC - 1) / T::PPC;
+  // staged bulk copies need 16-byte aligned pencils; a pair must fit the
+  // transform buffer it is staged in
+  const bool staged = (sizeof(float2) * FftShape<L>::SMEM) % 16 == 0 && (reinterpret_cast<uintptr_t>(p.H) & 15) == 0 &&
+                      ((size_t)p.n * sizeof(TR)) % 16 == 0 &&
+                      2 * (size_t)p.n * sizeof(TR) <= sizeof(float2) * FftShape<L>::SMEM;
+  if (staged) {
+    auto k = pf_band_staged_kernel<L, TR, TS>;
+    const size_t smem = T::smem(p.F, true);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, T::THREADS, smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = std::min<long long>(nsets, (long long)band_sm_count() * std::max(per, 1));
+    k<<<(unsigned)grid, T::THREADS, smem, s>>>(p, nsets);
+    return cudaGetLastError();
+  }
   auto k = pf_band_kernel<L, TR, TS>;
-  if (T::SMEM > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+  const size_t smem = T::smem(p.F, false);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const long long blocks = (p.npencils + T::PPC - 1) / T::PPC;
-  k<<<(unsigned)blocks, T::THREADS, T::SMEM, s>>>(p);
+  k<<<(unsigned)nsets, T::THREADS, smem, s>>>(p);
   return cudaGetLastError();
 }
 
@@ -198,13 +346,14 @@ template <int L>
 static cudaError_t launch_spec_one(const PfSpecParams& p, cudaStream_t s) {
   using T = PfBandTile<L>;
   auto k = pf_band_spectrum_kernel<L>;
-  if (T::SMEM > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
+  const size_t smem = sizeof(float2) * T::PPC * FftShape<L>::SMEM;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   const long long np = (long long)(p.Lx / 2 + 1) * p.Ly;
   const long long blocks = (np + T::PPC - 1) / T::PPC;
-  k<<<(unsigned)blocks, T::THREADS, T::SMEM, s>>>(p);
+  k<<<(unsigned)blocks, T::THREADS, smem, s>>>(p);
   return cudaGetLastError();
 }
 
