@@ -108,3 +108,33 @@ def test_autotune_picks_valid_shapes_and_caches():
     assert float(torch.linalg.vector_norm((other - tuned).double()) / torch.linalg.vector_norm(tuned.double())) <= 1e-6
     plan2 = nlos.plan_for_capture(g, "fk", "f32")
     assert plan2.autotune() == tiles          # served from the process cache
+
+
+def test_fp16_batch_of_full_size_captures_matches_oracle():
+    """Full-size captures of the FP16 batch mix (f-k 256 x 256 x 512 and a
+    phasor field 128 x 128 x 1024 with 128 planes) in one graph batch: each
+    result equals its single call bit for bit and lies within 2e-3 of the
+    FP64 oracle on the same rounded input, with the same peak voxel."""
+    from oracle import fk, pf
+    from paper_2608_28183_gb300 import nlos
+    from tests.gpu_util import exact_input, rel_l2, same_peak
+    caps = [synth.make_capture("fk_256x256x512", 0), synth.make_capture("pf_128x128x1024", 0)]
+    plans = [nlos.plan_for_capture(caps[0].geometry, "fk", "f16"),
+             nlos.plan_for_capture(caps[1].geometry, "pf", "f16", n_depths=128, depth_min_m=0.5, depth_max_m=2.5)]
+    ins = [to_device(c.counts, torch.float16) for c in caps]
+    outs = [p.empty_volume() for p in plans]
+    batch = nlos.Batch(plans, ins, outs, max_streams=2)
+    batch.launch()
+    torch.cuda.synchronize()
+    got = [o.cpu().numpy().astype(np.float64) for o in outs]
+    for p, x, o in zip(plans, ins, outs):
+        assert torch.equal(o, p.reconstruct(x))
+    batch.close()
+    g0, g1 = caps[0].geometry, caps[1].geometry
+    refs = [fk.fk_reconstruct(exact_input(caps[0].counts, torch.float16), g0.bin_width_s, g0.wall_w_m, g0.wall_h_m),
+            pf.pf_reconstruct(exact_input(caps[1].counts, torch.float16),
+                              pf.make_plan(g1.nx, g1.ny, g1.nt, g1.bin_width_s, g1.wall_w_m, g1.wall_h_m, 128, 0.5,
+                                           2.5))]
+    for a, r in zip(got, refs):
+        assert rel_l2(a, r) <= 2e-3
+        assert same_peak(a, r, rtol=2e-3)
