@@ -19,6 +19,7 @@
 // correction from an exact FMA residual. Plain float would put the
 // interpolation weight off by up to 6e-5 near m ~ 1000.
 #pragma once
+#include <type_traits>
 #include "fk_stolt.cuh"
 #include "fk_zwarp.cuh"
 #include "nlos_bounds.cuh"
@@ -28,8 +29,9 @@
 namespace nlos {
 
 // forward transform of the stored pencil; its upper half is zero padding
-// (kGuard: the pencil is shorter than L / 2, loads past it read zero)
-template <int L, class TS, bool kGuard>
+// (kGuard: the pencil is shorter than L / 2, loads past it read zero;
+// kRamp: sample t is also multiplied by t * t_ramp)
+template <int L, class TS, bool kGuard, bool kRamp>
 struct FkFwdCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = false;
@@ -42,9 +44,9 @@ struct FkFwdCtx {
   int n_in;                  // stored samples of the pencil (the rest is zero padding)
   long long g_off, g_n;      // offset of g in its buffer, the buffer's extent (bounds-checked build)
   int* err;
-  float t_ramp;              // non-zero: sample t is also multiplied by t * t_ramp
+  float t_ramp;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    const float m = t_ramp != 0.f ? ldmul * (float)l * t_ramp : ldmul;
+    const float m = kRamp ? ldmul * (float)l * t_ramp : ldmul;
     x[0] = (valid && (!kGuard || l < n_in) && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), m)
                                                                          : make_float2(0.f, 0.f);
   }
@@ -122,7 +124,9 @@ template <int L, int PPC_, bool kAlias = false> struct FkTile {
 // kGuard: L > 2n (a time axis that is not a power of two): loads beyond the
 // pencil and stores beyond z = n are masked; otherwise the pruned passes
 // already stop there.
-template <int L, int PPC, class TS, bool kPad2, bool kAlias, bool kGuard>
+// kRamp: the spectrum was taken without f-k's t/(n-1) ramp, which the
+// forward loads apply (float32 shared-spectrum plans, launch shape 0 only)
+template <int L, int PPC, class TS, bool kPad2, bool kAlias, bool kGuard, bool kRamp = false>
 __global__ void __launch_bounds__(FkTile<L, PPC, kAlias>::THREADS, FkTile<L, PPC, kAlias>::MIN_BLOCKS)
 fk_zstage_kernel(const FkZParams p) {
   using S = FftShape<L>;
@@ -139,8 +143,8 @@ fk_zstage_kernel(const FkZParams p) {
   float2* W1 = fk_sm + ((kAlias ? 1 : 2) * PPC + w) * S::SMEM;
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
-    FkFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid, ldmul, p.n,
-                                (valid ? pid : 0) * p.n, p.G_n, p.err, p.t_ramp};
+    FkFwdCtx<L, TS, kGuard, kRamp> ctx{static_cast<const TS*>(p.G) + (valid ? pid : 0) * p.n, U, W0, p.tw, valid,
+                                       ldmul, p.n, (valid ? pid : 0) * p.n, p.G_n, p.err, p.t_ramp};
     fftn_run<L, 1, kPad2, false>(ctx, j0);
   }
   __syncthreads();
@@ -159,12 +163,12 @@ fk_zstage_kernel(const FkZParams p) {
   fftn_run<L, 2, true, kPad2>(ctx, j0);
 }
 
-template <int L, int PPC, class TS, bool kAlias>
+template <int L, int PPC, class TS, bool kAlias, bool kRamp = false>
 cudaError_t launch_fk_ppc(const FkZParams& p, cudaStream_t s) {
   using T = FkTile<L, PPC, kAlias>;
-  auto k = p.pad != 2 ? fk_zstage_kernel<L, PPC, TS, false, kAlias, false>
-           : p.L == 2 * p.n ? fk_zstage_kernel<L, PPC, TS, true, kAlias, false>
-                            : fk_zstage_kernel<L, PPC, TS, true, kAlias, true>;
+  auto k = p.pad != 2 ? fk_zstage_kernel<L, PPC, TS, false, kAlias, false, kRamp>
+           : p.L == 2 * p.n ? fk_zstage_kernel<L, PPC, TS, true, kAlias, false, kRamp>
+                            : fk_zstage_kernel<L, PPC, TS, true, kAlias, true, kRamp>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -177,6 +181,11 @@ cudaError_t launch_fk_ppc(const FkZParams& p, cudaStream_t s) {
 // tiles 0/1: the two CTA sizes; 2/3: the same with aliased buffers
 template <int L, class TS>
 cudaError_t launch_fk_one(const FkZParams& p, int tile, cudaStream_t s) {
+  if (p.t_ramp != 0.f) {
+    // ramp applied at the loads: float32 storage, launch shape 0
+    if constexpr (std::is_same<TS, float2>::value) return launch_fk_ppc<L, fk_ppc(L, 0), TS, false, true>(p, s);
+    else return cudaErrorInvalidValue;
+  }
   switch (tile) {
     case 4:
       if constexpr (L == 1024) return launch_fk_warp<L, TS>(p, s);

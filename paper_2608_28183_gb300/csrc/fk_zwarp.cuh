@@ -52,10 +52,8 @@ struct FkWarpFwdCtx {
   int n_in;
   long long g_off, g_n;      // offset of g in its buffer, the buffer's extent (bounds-checked build)
   int* err;
-  float t_ramp;              // non-zero: sample t is also multiplied by t * t_ramp
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    const float m = t_ramp != 0.f ? ldmul * (float)l * t_ramp : ldmul;
-    x[0] = ((!kGuard || l < n_in) && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), m)
+    x[0] = ((!kGuard || l < n_in) && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), ldmul)
                                                                 : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return U; }
@@ -128,7 +126,7 @@ __global__ void __launch_bounds__(64) fk_zwarp_kernel(const FkZParams p) {
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
     FkWarpFwdCtx<L, TS, kGuard> ctx{static_cast<const TS*>(p.G) + pid * p.n, U, p.tw32, ldmul, p.n, pid * p.n, p.G_n,
-                                    p.err, p.t_ramp};
+                                    p.err};
     fftn_run<L, 1, kPad2, false, FkWarpFwdCtx<L, TS, kGuard>, 32>(ctx, lane);
   }
   {

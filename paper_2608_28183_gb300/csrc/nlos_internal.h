@@ -98,7 +98,8 @@ struct FkZParams {
   const float* ld_dev_scale;   // optional device scalar multiplying forward loads
   float st_scale;              // multiplies stored values
   float t_ramp;                // non-zero: forward loads also multiplied by t * t_ramp (the
-                               // spectrum was taken without the t/(n-1) ramp)
+                               // spectrum was taken without the t/(n-1) ramp; float32 only,
+                               // launch shape 0 whatever `tile` asks)
   long long G_n, psi_n;        // element extents (bounds-checked build; 0: unchecked)
   int* err;                    // device error word (bounds-checked build), may be null
 };
