@@ -77,7 +77,8 @@ template <int L, int NSLOT = 2> struct ChainTile {
   static constexpr int CONSUMERS = kChainIC * (L / kChainE);   // threads that transform
   static constexpr int THREADS = CONSUMERS + 32;               // + the producer warp
   static constexpr size_t BUF = sizeof(float2) * FftShape<L, kChainE>::SMEM * kChainIC;   // multiple of 128 bytes
-  static constexpr size_t SMEM = NSLOT * BUF + 2 * NSLOT * sizeof(uint64_t) + NSLOT * sizeof(ChainSlot);
+  static constexpr size_t TW = sizeof(float2) * FftShape<L, kChainE>::TWSIZE;   // the twiddle table's copy
+  static constexpr size_t SMEM = NSLOT * BUF + TW + 2 * NSLOT * sizeof(uint64_t) + NSLOT * sizeof(ChainSlot);
   // resident CTAs per SM the register budget is held to (what shared memory allows at L = 512)
   static constexpr int MIN_BLOCKS = L <= 512 ? (NSLOT == 2 ? 3 : 2) : 1;
   // the consumers' named barrier counts whole warps
@@ -86,13 +87,18 @@ template <int L, int NSLOT = 2> struct ChainTile {
 
 // transform contexts of the consumer threads: their barriers are named
 // barrier 1 over the consumers only
+// (the kernel keeps a copy of the twiddle table in shared memory: its data
+// slots take most of the SM's shared memory, leaving little L1 for the
+// table's global reads)
 template <int L, int IC, int LD, int ST, class TS>
 struct ChainTmaCtx : AxisTmaCtx<L, IC, LD, ST, TS> {
   static constexpr int kBarThreads = ChainTile<L>::CONSUMERS;
+  static constexpr bool kTwShared = true;
 };
 template <int L, int IC, class TS>
 struct ChainTmaPairCtx : AxisTmaPairCtx<L, IC, TS> {
   static constexpr int kBarThreads = ChainTile<L>::CONSUMERS;
+  static constexpr bool kTwShared = true;
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     this->smem[padE<kChainE>(l) * IC + this->c] = x[0];
   }
@@ -102,6 +108,7 @@ struct ChainTmaPairCtx : AxisTmaPairCtx<L, IC, TS> {
 template <int L, int IC, class TS>
 struct ChainMidCtx : AxisTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> {
   static constexpr int kBarThreads = ChainTile<L>::CONSUMERS;
+  static constexpr bool kTwShared = true;
   uint64_t keep;
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
     if (l >= this->L_out) return;
@@ -162,9 +169,10 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
   constexpr int TPC = L / E;
   extern __shared__ __align__(128) unsigned char cs[];
   auto buf = [&](int slot) { return reinterpret_cast<float2*>(cs + slot * T::BUF); };
-  uint64_t* full = reinterpret_cast<uint64_t*>(cs + NSLOT * T::BUF);
+  float2* tw = reinterpret_cast<float2*>(cs + NSLOT * T::BUF);
+  uint64_t* full = reinterpret_cast<uint64_t*>(cs + NSLOT * T::BUF + T::TW);
   uint64_t* empty = full + NSLOT;
-  ChainSlot* desc = reinterpret_cast<ChainSlot*>(cs + NSLOT * T::BUF + 2 * NSLOT * sizeof(uint64_t));
+  ChainSlot* desc = reinterpret_cast<ChainSlot*>(cs + NSLOT * T::BUF + T::TW + 2 * NSLOT * sizeof(uint64_t));
   const int hx = L / 2 + 1;
   const int n1 = kFwd ? p.b : L;
   const int n2 = kFwd ? hx : p.b;
@@ -180,6 +188,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
     }
     mbar_fence_init();
   }
+  for (int i = threadIdx.x; i < FftShape<L, kChainE>::TWSIZE; i += T::THREADS) tw[i] = __ldg(p.tw + i);
   __syncthreads();
 
   if (threadIdx.x >= T::CONSUMERS) {
@@ -279,7 +288,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         ChainTmaPairCtx<L, IC, TS> ctx;
         ctx.tile = reinterpret_cast<const TR*>(buf(slot));
         ctx.smem = buf(slot);
-        ctx.tw = p.tw;
+        ctx.tw = tw;
         ctx.L_in = p.a;
         ctx.c = c;
         ctx.m0 = p.t_scale != 0.f ? ldm * (float)(t0 + c) * p.t_scale : ldm;
@@ -304,7 +313,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
       } else if (kFwd) {
         // y forward of kx = idx: rows y < b, all L outputs
         ChainTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> ctx;
-        chain_ctx(ctx, buf(slot), p.tw, c, 0);
+        chain_ctx(ctx, buf(slot), tw, c, 0);
         ctx.out = p.out;
         ctx.out_n = p.out_n;
         ctx.err = p.err;
@@ -317,7 +326,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
       } else if (!it.second) {
         // y inverse of kx = idx: keep y < b
         ChainMidCtx<L, IC, TS> ctx;
-        chain_ctx(ctx, buf(slot), p.tw, c, 1);
+        chain_ctx(ctx, buf(slot), tw, c, 1);
         ctx.keep = keep;
         ctx.out = p.mid;
         ctx.out_n = p.mid_n;
@@ -331,7 +340,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
       } else {
         // x inverse of wall row y = idx: keep x < a, |.|^2 (or complex)
         ChainTmaCtx<L, IC, kLoadCpx, ST, TS> ctx;
-        chain_ctx(ctx, buf(slot), p.tw, c, 1);
+        chain_ctx(ctx, buf(slot), tw, c, 1);
         ctx.out = p.out;
         ctx.out_n = p.out_n;
         ctx.err = p.err;

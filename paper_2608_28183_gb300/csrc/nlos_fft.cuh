@@ -164,6 +164,16 @@ template <class C, class = void> struct CtxBar {
 template <class C> struct CtxBar<C, decltype((void)C::kBarThreads)> {
   static constexpr int threads = C::kBarThreads;
 };
+// Where a context's twiddle table lives: global memory read through the
+// read-only path (default), or - for a context that declares kTwShared - a
+// copy in shared memory.
+template <class C, class = void> struct CtxTwShared {
+  static constexpr bool value = false;
+};
+template <class C> struct CtxTwShared<C, decltype((void)C::kTwShared)> {
+  static constexpr bool value = C::kTwShared;
+};
+
 template <class Ctx> __device__ __forceinline__ void fft_sync() {
   if constexpr (CtxBar<Ctx>::threads == 0) {
     __syncthreads();
@@ -314,7 +324,7 @@ __device__ __forceinline__ void fftn_passes(Ctx& ctx, const int j0, float2 (&v)[
       const float2* tp = ctx.tw + S::twoff(P) + (j & (NS - 1));
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const float2 w = __ldg(tp + r * NS);
+        const float2 w = CtxTwShared<Ctx>::value ? tp[r * NS] : __ldg(tp + r * NS);
 #pragma unroll
         for (int t = 0; t < NT; ++t) v[t][i * R + r] = cmul(v[t][i * R + r], w);
       }
