@@ -75,8 +75,15 @@ struct Done {
   Slot* slot = nullptr;
 };
 
+// Stream priority levels a slot can run at: a request is admitted at the
+// level of how many requests already run (the oldest runs at the highest
+// priority), so later arrivals fill the SMs the older ones leave idle
+// instead of slowing them down.
+constexpr int kPrioLevels = 4;
+
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t prio[kPrioLevels] = {};   // one stream per level, highest first
+  cudaStream_t stream = nullptr;         // the running request's stream
   Request* req = nullptr;
   Done done;
 };
@@ -179,10 +186,13 @@ void scheduler(nlos_server_s* sv) {
         }
       if (slot) evict_idle(sv, head->need, victims);
       if (slot && sv->resident + sv->in_use + head->need <= sv->budget) {
+        int running = 0;
+        for (Slot& sl : sv->slots) running += sl.req ? 1 : 0;
         r = head;
         sv->queue.pop_front();
         r->state = 1;
         slot->req = r;
+        slot->stream = slot->prio[std::min(running, kPrioLevels - 1)];
         sv->in_use += r->need;
       }
     }
@@ -297,12 +307,22 @@ nlos_status_t nlos_server_create(size_t memory_budget_bytes, int n_slots, nlos_s
     cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
   }
   sv->slots.resize(n_slots);
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
   for (Slot& sl : sv->slots) {
     sl.done.sv = sv;
     sl.done.slot = &sl;
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    bool ok = true;
+    for (int k = 0; k < kPrioLevels && ok; ++k) {
+      // greatest is the numerically lowest value; levels past the range repeat the least
+      const int prio = std::min(greatest + k, least);
+      ok = cudaStreamCreateWithPriority(&sl.prio[k], cudaStreamNonBlocking, prio) == cudaSuccess;
+    }
+    sl.stream = sl.prio[0];
+    if (!ok) {
       for (Slot& t : sv->slots)
-        if (t.stream) cudaStreamDestroy(t.stream);
+        for (cudaStream_t st : t.prio)
+          if (st) cudaStreamDestroy(st);
       delete sv;
       return set_error(NLOS_ERR_CUDA, "server streams");
     }
@@ -419,10 +439,11 @@ nlos_status_t nlos_server_destroy(nlos_server_t sv) {
   }
   sv->cv_work.notify_all();
   sv->th.join();
-  for (Slot& sl : sv->slots) {
-    cudaStreamSynchronize(sl.stream);
-    cudaStreamDestroy(sl.stream);
-  }
+  for (Slot& sl : sv->slots)
+    for (cudaStream_t st : sl.prio) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
   for (auto& kv : sv->plans) {
     nlos_plan_destroy(kv.second->plan);
     delete kv.second;
