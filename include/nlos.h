@@ -266,7 +266,8 @@ nlos_status_t nlos_batch_destroy(nlos_batch_t batch);
  * admission needs the room; a request is admitted in arrival order as soon
  * as one of n_slots streams is free and its workspace (the padded volume's
  * footprint) fits; admitted requests are launched outside the queue's lock
- * and overlap on the device, and each signals its completion through a host
+ * and overlap on the device, at stream priorities ranked by age (the oldest
+ * running request highest), and each signals its completion through a host
  * function on its stream. Workspaces come from the stream-ordered
  * allocator. Each result equals that of a standalone nlos_reconstruct with
  * the same description.

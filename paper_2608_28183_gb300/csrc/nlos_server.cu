@@ -13,7 +13,10 @@
 //     is free and its workspace (the padded volume's footprint) fits in what
 //     the budget leaves next to the resident plans and running requests;
 //   - the scheduler launches outside the lock, on the slot's stream, so work
-//     that arrives while others run overlaps with them on the GPU;
+//     that arrives while others run overlaps with them on the GPU; the
+//     stream's priority ranks the request by age (the k-th request running
+//     at its admission gets the k-th highest level), so a later arrival takes
+//     the SMs an older, larger request leaves idle instead of slowing it;
 //   - workspaces come from the stream-ordered allocator (cudaMallocAsync /
 //     cudaFreeAsync on the slot's stream), so admissions never force a
 //     device-wide synchronisation;
