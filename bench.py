@@ -36,7 +36,8 @@ FALLBACK_HBM_GBS = 6800.0
 # sources of the f-k kernels (temporal-frequency stage, fused lateral pairs);
 # a change to them invalidates the committed DRAM-traffic figures
 KERNEL_SOURCES = ["paper_2608_28183_gb300/csrc/nlos_fft.cuh", "paper_2608_28183_gb300/csrc/fk_zstage.cuh",
-                  "paper_2608_28183_gb300/csrc/fk_chain.cuh", "paper_2608_28183_gb300/csrc/axis_fft.cuh"]
+                  "paper_2608_28183_gb300/csrc/fk_chain.cuh", "paper_2608_28183_gb300/csrc/axis_fft.cuh",
+                  "paper_2608_28183_gb300/csrc/fk_zsplit.cuh"]
 
 
 def parse_args():
@@ -87,9 +88,11 @@ def measured_peaks():
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
 
-def stage_bytes(a, b, n, storage):
+def stage_bytes(a, b, n, storage, zlast=False):
     """Algorithmic bytes per launch of each stage: its unique input plus its
-    unique output, in the stored element sizes (a, b, n: grid and bins)."""
+    unique output, in the stored element sizes (a, b, n: grid and bins).
+    zlast: the float32 form with the inverse temporal transform last (the
+    lateral inverse then writes the complex kept spectrum, 8 V)."""
     cb = 8 if storage == "f32" else 4
     rb = 4 if storage == "f32" else 2
     V = a * b * n
@@ -102,7 +105,11 @@ def stage_bytes(a, b, n, storage):
         "fk_x_inverse": 2 * V * cb + V * 4,
         # fused pairs: the intermediate stays on chip / in L2
         "fk_xy_forward": V * rb + 2 * half * cb,
-        "fk_yx_inverse": 4 * V * cb + V * 4,
+        "fk_yx_inverse": 4 * V * cb + (V * 8 if zlast else V * 4),
+        # inverse temporal transform last: the Stolt stage writes the
+        # resampled spectrum, the last stage reads the kept one
+        "fk_stolt": 2 * half * cb + 4 * V * cb,
+        "fk_z_inverse": V * 8 + V * 4,
     }
     if storage != "f32":
         out["volume_scale"] = V * rb
@@ -835,7 +842,7 @@ def main():
 
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    sb = stage_bytes(g.nx, g.ny, g.nt, args.storage)
+    sb = stage_bytes(g.nx, g.ny, g.nt, args.storage, zlast="fk_z_inverse" in stages)
     per_launch_ms = {k: v / max(1, calls) for k, v in stages.items()}
     dom = max(per_launch_ms, key=per_launch_ms.get)
     achieved = sb[dom] / (per_launch_ms[dom] * 1e-3) / 1e9
@@ -846,14 +853,18 @@ def main():
     # the Stolt stage against the FP32 FMA peak as well: per stored pencil
     # (a + 1 of the 2a kx planes x 2b) one forward and two inverse length-2n
     # transforms at 5 N log2 N flop (the interpolation is not counted)
+    # (with the inverse temporal transform last: one forward transform per
+    # stored pencil in the Stolt stage)
     stolt_alu = None
-    if "fk_stolt_z" in per_launch_ms:
-        Lt = 2 * g.nt
-        fl = (g.nx + 1) * 2 * g.ny * 3 * 5 * Lt * math.log2(Lt)
-        fpk, fnote = ffma_peak()
-        ach = fl / (per_launch_ms["fk_stolt_z"] * 1e-3) / 1e12
-        stolt_alu = {"kernel": "fk_stolt_z", "bound": "alu", "flops": fl, "flops_model": "3 x 5 N log2 N per stored pencil",
-                     "achieved_tflops": ach, "peak_tflops": fpk, "frac": ach / fpk, "peak_note": fnote}
+    for key, per in (("fk_stolt_z", 3), ("fk_stolt", 1)):
+        if key in per_launch_ms:
+            Lt = 2 * g.nt
+            fl = (g.nx + 1) * 2 * g.ny * per * 5 * Lt * math.log2(Lt)
+            fpk, fnote = ffma_peak()
+            ach = fl / (per_launch_ms[key] * 1e-3) / 1e12
+            stolt_alu = {"kernel": key, "bound": "alu", "flops": fl,
+                         "flops_model": f"{per} x 5 N log2 N per stored pencil",
+                         "achieved_tflops": ach, "peak_tflops": fpk, "frac": ach / fpk, "peak_note": fnote}
 
     def pct(q, xs=None):
         xs = step_ms if xs is None else xs

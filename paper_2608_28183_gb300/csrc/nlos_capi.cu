@@ -60,6 +60,21 @@ cudaError_t launch_fk_chain(const FkChainLaunch& l, int storage, cudaStream_t s)
   }
 }
 
+cudaError_t launch_fk_stolt_r0(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_stolt_r1(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zinv_r0(const FkZInvParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zinv_r1(const FkZInvParams& p, int tile, cudaStream_t s);
+
+cudaError_t launch_fk_stolt(const FkZParams& p, int tile, cudaStream_t s) {
+  if (p.npencils <= 0 || p.L != 2 * p.n || p.pad != 2) return cudaErrorInvalidValue;
+  return p.L <= 1024 ? launch_fk_stolt_r0(p, tile, s) : launch_fk_stolt_r1(p, tile, s);
+}
+
+cudaError_t launch_fk_zinv(const FkZInvParams& p, int tile, cudaStream_t s) {
+  if (p.npencils <= 0 || p.L != 2 * p.n) return cudaErrorInvalidValue;
+  return p.L <= 1024 ? launch_fk_zinv_r0(p, tile, s) : launch_fk_zinv_r1(p, tile, s);
+}
+
 cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s) {
   static cudaError_t (*const fn[3][3])(const FkZParams&, int, cudaStream_t) = {
       {launch_fk_zstage_f32_r0, launch_fk_zstage_f32_r1, launch_fk_zstage_f32_r2},
@@ -174,6 +189,7 @@ struct nlos_plan_s {
   size_t off_scal = 0, off_part = 0;
   size_t off_sync = 0;                  // chunk counters of the fused lateral f-k stages
   bool fused = false;                   // f-k lateral transforms fused in pairs (fk_chain.cuh)
+  bool zlast = false;                   // f-k inverse temporal transform last (fk_zsplit.cuh)
   size_t ws_bytes = 0;
   void* ws = nullptr;
   // host-call staging
@@ -829,6 +845,50 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   z.G_n = ws_extent(p, 1);
   z.psi_n = ws_extent(p, 2);
   z.err = err;
+  if (p->zlast) {
+    // FK3 without its inverses: the resampled spectra of both partners
+    NLOS_CU(launch_fk_stolt(z, p->tiles[sid], s), "fk stolt stage");
+    NLOS_MARK(p, s, sid++);
+    // FK4: y inverse (keep y < b) then x inverse (keep x < a), complex, into
+    // the second buffer (the forward spectrum is no longer needed)
+    FkChainLaunch c{};
+    c.p = ch;
+    c.p.in = b2;
+    c.p.mid = b0;
+    c.p.out = b1;
+    c.p.s1 = g2b;
+    c.p.s2 = 1.0f;
+    c.p.in_n = ws_extent(p, 2);
+    c.p.mid_n = ws_extent(p, 0);
+    c.p.out_n = std::min<long long>(ws_extent(p, 1), a * b * n);
+    c.p.discard = p->tiles[sid] < 2;
+    c.nslot = p->tiles[sid] % 2 == 0 ? 3 : 2;
+    c.fwd = 0;
+    c.store_mode = kStoreCpx32;
+    const unsigned box = (unsigned)std::min<long long>(Lx, 256);
+    if (!encode_3d(&c.map1, b2, cb, n, Ly, Lx, n * cb, Ly * n * cb, 8, box, false) ||
+        !encode_3d(&c.map2, b0, cb, n, Lx, b, b * n * cb, n * cb, 8, box, false))
+      return fail(NLOS_ERR_CUDA, "fk yx-inverse: tensor map encoding failed");
+    NLOS_CU(cudaMemsetAsync(sync, 0, sync_bytes, s), "fk chain counters");
+    NLOS_CU(launch_fk_chain(c, st, s), "fk yx-inverse");
+    NLOS_MARK(p, s, sid++);
+    // FK5: z inverse of the a x b kept pencils, |psi|^2 (or psi) with the normalisation
+    FkZInvParams zi{};
+    zi.in = static_cast<const float2*>(b1);
+    zi.out = vol;
+    zi.tw = p->tw[(int)Lt];
+    zi.L = (int)Lt;
+    zi.n = (int)n;
+    zi.npencils = a * b;
+    zi.scale = fscale;
+    zi.complex_out = cpx ? 1 : 0;
+    zi.in_n = std::min<long long>(ws_extent(p, 1), a * b * n);
+    zi.out_n = a * b * n;
+    zi.err = err;
+    NLOS_CU(launch_fk_zinv(zi, p->tiles[sid], s), "fk z-inverse");
+    NLOS_MARK(p, s, sid++);
+    return NLOS_OK;
+  }
   NLOS_CU(launch_fk_zstage(z, st, p->tiles[sid], s), "fk stolt stage");
   NLOS_MARK(p, s, sid++);
   if (p->fused) {
@@ -1259,12 +1319,17 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   p->storage = desc->storage;
   p->fused = desc->method == NLOS_FK && !(flags & NLOS_PLAN_SEPARATE_AXES) &&
              fk_chain_eligible(p->a, p->b, p->n, p->Lx, p->Ly, desc->pad_factor);
+  // float32 plans with fused lateral stages and L = 2n take the inverse
+  // temporal transform last, on the kept pencils
+  p->zlast = p->fused && p->storage == kF32 && p->Lt == 2 * p->n;
   if (p->storage != kF32) p->stage_names.push_back("volume_scale");
   const char* fk_names[] = {"fk_x_forward", "fk_y_forward", "fk_stolt_z", "fk_y_inverse", "fk_x_inverse"};
   const char* fk_fused_names[] = {"fk_xy_forward", "fk_stolt_z", "fk_yx_inverse"};
+  const char* fk_zlast_names[] = {"fk_xy_forward", "fk_stolt", "fk_yx_inverse", "fk_z_inverse"};
   const char* pf_names[] = {"pf_band", "pf_y_forward", "pf_x_forward", "pf_depth_sum", "pf_y_inverse",
                             "pf_x_inverse"};
-  if (desc->method == NLOS_FK && p->fused) for (const char* nm : fk_fused_names) p->stage_names.push_back(nm);
+  if (desc->method == NLOS_FK && p->zlast) for (const char* nm : fk_zlast_names) p->stage_names.push_back(nm);
+  else if (desc->method == NLOS_FK && p->fused) for (const char* nm : fk_fused_names) p->stage_names.push_back(nm);
   else if (desc->method == NLOS_FK) for (const char* nm : fk_names) p->stage_names.push_back(nm);
   else for (const char* nm : pf_names) p->stage_names.push_back(nm);
   for (const std::string& nm : p->stage_names) {
@@ -1272,8 +1337,10 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
     const bool umma = nm == "pf_depth_sum" && desc->method == NLOS_PHASOR_RSD &&
                       (desc->storage == NLOS_F16 || desc->storage == NLOS_F32);
     const bool chain = nm == "fk_xy_forward" || nm == "fk_yx_inverse";
-    p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : nm == "fk_stolt_z" ? 2 : umma ? 4 : chain ? 5 : 0);
-    p->stage_len.push_back(xs ? p->Lx : ys ? p->Ly : nm == "fk_stolt_z" ? p->Lt : 0);
+    const bool zsplit = nm == "fk_stolt" || nm == "fk_z_inverse";
+    p->stage_kind.push_back(nm == "fk_x_forward" ? 3 : xs || ys ? 1 : nm == "fk_stolt_z" ? 2 : umma ? 4 : chain ? 5
+                            : zsplit ? 6 : 0);
+    p->stage_len.push_back(xs ? p->Lx : ys ? p->Ly : (nm == "fk_stolt_z" || zsplit) ? p->Lt : 0);
   }
   // default launch shapes: TMA-staged axis transforms (each falls back to
   // direct loads where the layout does not allow TMA); the autotuner may
@@ -1629,6 +1696,7 @@ int stage_variants(const nlos_plan_s* p, size_t i) {
   if (p->stage_kind[i] == 4) return 3;   // tensor cores (persistent), FFMA, tensor cores (CTA per tile)
   // fused lateral pair: {3, 2} slots per CTA x {intermediate dropped from L2 after use, kept}
   if (p->stage_kind[i] == 5) return 4;
+  if (p->stage_kind[i] == 6) return 2;   // temporal stages of the split inverse: two pencils-per-CTA counts
   return 1;
 }
 }  // namespace
