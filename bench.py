@@ -91,8 +91,8 @@ def measured_peaks():
 def stage_bytes(a, b, n, storage, zlast=False):
     """Algorithmic bytes per launch of each stage: its unique input plus its
     unique output, in the stored element sizes (a, b, n: grid and bins).
-    zlast: the float32 form with the inverse temporal transform last (the
-    lateral inverse then writes the complex kept spectrum, 8 V)."""
+    zlast: the form with the inverse temporal transform last (the lateral
+    inverse then writes the complex kept spectrum, V complex elements)."""
     cb = 8 if storage == "f32" else 4
     rb = 4 if storage == "f32" else 2
     V = a * b * n
@@ -105,11 +105,11 @@ def stage_bytes(a, b, n, storage, zlast=False):
         "fk_x_inverse": 2 * V * cb + V * 4,
         # fused pairs: the intermediate stays on chip / in L2
         "fk_xy_forward": V * rb + 2 * half * cb,
-        "fk_yx_inverse": 4 * V * cb + (V * 8 if zlast else V * 4),
+        "fk_yx_inverse": 4 * V * cb + (V * cb if zlast else V * 4),
         # inverse temporal transform last: the Stolt stage writes the
         # resampled spectrum, the last stage reads the kept one
         "fk_stolt": 2 * half * cb + 4 * V * cb,
-        "fk_z_inverse": V * 8 + V * 4,
+        "fk_z_inverse": V * cb + V * 4,
     }
     if storage != "f32":
         out["volume_scale"] = V * rb

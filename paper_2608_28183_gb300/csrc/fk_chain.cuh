@@ -374,11 +374,12 @@ cudaError_t launch_fk_chain_one(const FkChainLaunch& l, cudaStream_t s) {
   void (*k)(const __grid_constant__ CUtensorMap, const __grid_constant__ CUtensorMap, const FkChainParams) =
       l.fwd ? fk_chain_kernel<L, TS, true, kStoreCpx, NSLOT>
             : l.store_mode == kStoreCpx32 ? fk_chain_kernel<L, TS, false, kStoreCpx32, NSLOT>
+            : l.store_mode == kStoreCpx   ? fk_chain_kernel<L, TS, false, kStoreCpx, NSLOT>
                                           : fk_chain_kernel<L, TS, false, kStoreAbs2, NSLOT>;
   // one persistent CTA per resident slot (occupancy queried once per kernel)
-  static void* known[3] = {};
-  static int slots[3] = {};
-  const int key = l.fwd ? 0 : (l.store_mode == kStoreCpx32 ? 2 : 1);
+  static void* known[4] = {};
+  static int slots[4] = {};
+  const int key = l.fwd ? 0 : (l.store_mode == kStoreCpx32 ? 2 : l.store_mode == kStoreCpx ? 3 : 1);
   if (known[key] != (void*)k) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;

@@ -22,7 +22,8 @@
 // and FK5 one per kept pencil: the temporal transforms drop from
 // 3 (a + 1) 2b to (a + 1) 2b + a b per volume, for 24V more bytes moved
 // (V's 32V written and read once more at a quarter of its size: 8V, plus the
-// complex intermediate of FK4). Float32 storage, L = 2n.
+// complex intermediate of FK4). Any storage type (the 16-bit forms keep the
+// per-pass scales of the other stages), L = 2n.
 #pragma once
 #include "fk_stolt.cuh"
 #include "fk_zstage.cuh"
@@ -34,11 +35,11 @@ namespace nlos {
 
 // forward transform of the stored pencil in place in its buffer (the
 // transform's last pass reads all of the buffer before it writes)
-template <int L, bool kRamp>
+template <int L, class TS, bool kRamp>
 struct FkLiteFwdCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = false;
-  const float2* g;
+  const TS* g;
   float2* U;
   const float2* tw;
   bool valid;
@@ -47,7 +48,7 @@ struct FkLiteFwdCtx {
   int* err;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
     const float m = kRamp ? ldmul * (float)l * t_ramp : ldmul;
-    x[0] = (valid && bchk(g_off + l, g_n, err)) ? cscale(__ldg(g + l), m) : make_float2(0.f, 0.f);
+    x[0] = (valid && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), m) : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return U; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[pad16(l)] = x[0]; }
@@ -58,7 +59,7 @@ template <int L, int PPC> struct FkLiteTile {
   static constexpr size_t SMEM = sizeof(float2) * PPC * FftShape<L>::SMEM;
 };
 
-template <int L, int PPC, bool kRamp>
+template <int L, int PPC, class TS, bool kRamp>
 __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_stolt_kernel(const FkZParams p) {
   using S = FftShape<L>;
   extern __shared__ float2 fl_sm[];
@@ -73,8 +74,8 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_stolt_kernel(c
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
     const long long q = valid ? pid : 0;
-    FkLiteFwdCtx<L, kRamp> ctx{static_cast<const float2*>(p.G) + q * p.n, U, p.tw, valid, ldmul, p.t_ramp,
-                               q * p.n, p.G_n, p.err};
+    FkLiteFwdCtx<L, TS, kRamp> ctx{static_cast<const TS*>(p.G) + q * p.n, U, p.tw, valid, ldmul, p.t_ramp,
+                                   q * p.n, p.G_n, p.err};
     fftn_run<L, 1, true, false>(ctx, j0);
   }
   __syncthreads();
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_stolt_kernel(c
   const float2 ay = p.ay[ky];
   float2 A = two_sum(ax.x, ay.x);
   A = fast_two_sum(A.x, A.y + (ax.y + ay.y));
-  float2* V = static_cast<float2*>(p.psi);
+  TS* V = static_cast<TS*>(p.psi);
   const long long o0 = ((long long)kx * twob + ky) * p.n;
   const int mkx = (kx == 0) ? 0 : p.a_pad - kx;
   const int mky = (twob - ky) & (twob - 1);
@@ -102,18 +103,18 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_stolt_kernel(c
         e = make_float2(s * fmaf(c.alpha, w1.x - w0.x, w0.x), -s * fmaf(c.alpha, w1.y - w0.y, w0.y));
       }
     }
-    if (bchk(o0 + m, p.psi_n, p.err)) V[o0 + m] = d;
-    if (partner && bchk(o1 + m, p.psi_n, p.err)) V[o1 + m] = e;
+    if (bchk(o0 + m, p.psi_n, p.err)) Cpx<TS>::put(V + o0 + m, d);
+    if (partner && bchk(o1 + m, p.psi_n, p.err)) Cpx<TS>::put(V + o1 + m, e);
   }
 }
 
 // inverse temporal transform of a kept pencil as conj(DFT(conj(V))): input
 // m < L/2 (the upper half is zero), output z < L/2
-template <int L, bool kCpx>
+template <int L, class TS, bool kCpx>
 struct FkZInvCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = false;
-  const float2* in;
+  const TS* in;
   void* out;
   float2* W;
   const float2* tw;
@@ -122,7 +123,7 @@ struct FkZInvCtx {
   long long in_off, in_n, out_off, out_n;
   int* err;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    x[0] = (valid && bchk(in_off + l, in_n, err)) ? cconj(__ldg(in + l)) : make_float2(0.f, 0.f);
+    x[0] = (valid && bchk(in_off + l, in_n, err)) ? cconj(Cpx<TS>::get(in + l)) : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return W; }
   __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
@@ -132,7 +133,7 @@ struct FkZInvCtx {
   }
 };
 
-template <int L, int PPC, bool kCpx>
+template <int L, int PPC, class TS, bool kCpx>
 __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_zinv_kernel(const FkZInvParams p) {
   using S = FftShape<L>;
   extern __shared__ float2 zi_sm[];
@@ -143,15 +144,16 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_zinv_kernel(co
   const long long q = valid ? pid : 0;
   void* out = kCpx ? static_cast<void*>(static_cast<float2*>(p.out) + q * p.n)
                    : static_cast<void*>(static_cast<float*>(p.out) + q * p.n);
-  FkZInvCtx<L, kCpx> ctx{p.in + q * p.n, out, zi_sm + w * S::SMEM, p.tw, valid, p.scale,
-                         q * p.n, p.in_n, q * p.n, p.out_n, p.err};
+  const float scale = p.scale * (p.dev_scale ? *p.dev_scale : 1.0f);
+  FkZInvCtx<L, TS, kCpx> ctx{static_cast<const TS*>(p.in) + q * p.n, out, zi_sm + w * S::SMEM, p.tw, valid, scale,
+                             q * p.n, p.in_n, q * p.n, p.out_n, p.err};
   fftn_run<L, 1, true, true>(ctx, j0);
 }
 
-template <int L, int PPC, bool kRamp>
+template <int L, int PPC, class TS, bool kRamp>
 cudaError_t launch_fk_stolt_one(const FkZParams& p, cudaStream_t s) {
   using T = FkLiteTile<L, PPC>;
-  auto k = fk_stolt_kernel<L, PPC, kRamp>;
+  auto k = fk_stolt_kernel<L, PPC, TS, kRamp>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -161,10 +163,10 @@ cudaError_t launch_fk_stolt_one(const FkZParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int L, int PPC, bool kCpx>
+template <int L, int PPC, class TS, bool kCpx>
 cudaError_t launch_fk_zinv_one(const FkZInvParams& p, cudaStream_t s) {
   using T = FkLiteTile<L, PPC>;
-  auto k = fk_zinv_kernel<L, PPC, kCpx>;
+  auto k = fk_zinv_kernel<L, PPC, TS, kCpx>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -174,19 +176,24 @@ cudaError_t launch_fk_zinv_one(const FkZInvParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// launch shapes 0 / 1: the two pencils-per-CTA counts of fk_ppc
-template <int L>
+// launch shapes 0 / 1: the two pencils-per-CTA counts of fk_ppc (the
+// ramped form, float32 only, takes shape 0)
+template <int L, class TS>
 cudaError_t launch_fk_stolt_len(const FkZParams& p, int tile, cudaStream_t s) {
   constexpr int P0 = fk_ppc(L, 0), P1 = fk_ppc(L, 1);
-  if (p.t_ramp != 0.f) return launch_fk_stolt_one<L, P0, true>(p, s);
-  return tile == 1 ? launch_fk_stolt_one<L, P1, false>(p, s) : launch_fk_stolt_one<L, P0, false>(p, s);
+  if (p.t_ramp != 0.f) {
+    if constexpr (std::is_same<TS, float2>::value) return launch_fk_stolt_one<L, P0, TS, true>(p, s);
+    else return cudaErrorInvalidValue;
+  }
+  return tile == 1 ? launch_fk_stolt_one<L, P1, TS, false>(p, s) : launch_fk_stolt_one<L, P0, TS, false>(p, s);
 }
 
-template <int L>
+template <int L, class TS>
 cudaError_t launch_fk_zinv_len(const FkZInvParams& p, int tile, cudaStream_t s) {
   constexpr int P0 = fk_ppc(L, 0), P1 = fk_ppc(L, 1);
-  if (p.complex_out) return tile == 1 ? launch_fk_zinv_one<L, P1, true>(p, s) : launch_fk_zinv_one<L, P0, true>(p, s);
-  return tile == 1 ? launch_fk_zinv_one<L, P1, false>(p, s) : launch_fk_zinv_one<L, P0, false>(p, s);
+  if (p.complex_out)
+    return tile == 1 ? launch_fk_zinv_one<L, P1, TS, true>(p, s) : launch_fk_zinv_one<L, P0, TS, true>(p, s);
+  return tile == 1 ? launch_fk_zinv_one<L, P1, TS, false>(p, s) : launch_fk_zinv_one<L, P0, TS, false>(p, s);
 }
 
 }  // namespace nlos

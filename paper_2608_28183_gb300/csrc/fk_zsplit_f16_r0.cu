@@ -1,0 +1,26 @@
+// f-k with the inverse temporal transform last: __half2 storage, lengths 32-1024.
+#include "fk_zsplit.cuh"
+namespace nlos {
+cudaError_t launch_fk_stolt_f16_r0(const FkZParams& p, int tile, cudaStream_t s) {
+  switch (p.L) {
+    case 32: return launch_fk_stolt_len<32, __half2>(p, tile, s);
+    case 64: return launch_fk_stolt_len<64, __half2>(p, tile, s);
+    case 128: return launch_fk_stolt_len<128, __half2>(p, tile, s);
+    case 256: return launch_fk_stolt_len<256, __half2>(p, tile, s);
+    case 512: return launch_fk_stolt_len<512, __half2>(p, tile, s);
+    case 1024: return launch_fk_stolt_len<1024, __half2>(p, tile, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t launch_fk_zinv_f16_r0(const FkZInvParams& p, int tile, cudaStream_t s) {
+  switch (p.L) {
+    case 32: return launch_fk_zinv_len<32, __half2>(p, tile, s);
+    case 64: return launch_fk_zinv_len<64, __half2>(p, tile, s);
+    case 128: return launch_fk_zinv_len<128, __half2>(p, tile, s);
+    case 256: return launch_fk_zinv_len<256, __half2>(p, tile, s);
+    case 512: return launch_fk_zinv_len<512, __half2>(p, tile, s);
+    case 1024: return launch_fk_zinv_len<1024, __half2>(p, tile, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace nlos

@@ -1,0 +1,20 @@
+// f-k with the inverse temporal transform last: float2 storage, lengths 2048-8192.
+#include "fk_zsplit.cuh"
+namespace nlos {
+cudaError_t launch_fk_stolt_f32_r1(const FkZParams& p, int tile, cudaStream_t s) {
+  switch (p.L) {
+    case 2048: return launch_fk_stolt_len<2048, float2>(p, tile, s);
+    case 4096: return launch_fk_stolt_len<4096, float2>(p, tile, s);
+    case 8192: return launch_fk_stolt_len<8192, float2>(p, tile, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t launch_fk_zinv_f32_r1(const FkZInvParams& p, int tile, cudaStream_t s) {
+  switch (p.L) {
+    case 2048: return launch_fk_zinv_len<2048, float2>(p, tile, s);
+    case 4096: return launch_fk_zinv_len<4096, float2>(p, tile, s);
+    case 8192: return launch_fk_zinv_len<8192, float2>(p, tile, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace nlos

@@ -60,19 +60,32 @@ cudaError_t launch_fk_chain(const FkChainLaunch& l, int storage, cudaStream_t s)
   }
 }
 
-cudaError_t launch_fk_stolt_r0(const FkZParams& p, int tile, cudaStream_t s);
-cudaError_t launch_fk_stolt_r1(const FkZParams& p, int tile, cudaStream_t s);
-cudaError_t launch_fk_zinv_r0(const FkZInvParams& p, int tile, cudaStream_t s);
-cudaError_t launch_fk_zinv_r1(const FkZInvParams& p, int tile, cudaStream_t s);
+#define NLOS_ZSPLIT(t)                                                                   \
+  cudaError_t launch_fk_stolt_##t##_r0(const FkZParams& p, int tile, cudaStream_t s);    \
+  cudaError_t launch_fk_stolt_##t##_r1(const FkZParams& p, int tile, cudaStream_t s);    \
+  cudaError_t launch_fk_zinv_##t##_r0(const FkZInvParams& p, int tile, cudaStream_t s);  \
+  cudaError_t launch_fk_zinv_##t##_r1(const FkZInvParams& p, int tile, cudaStream_t s);
+NLOS_ZSPLIT(f32)
+NLOS_ZSPLIT(f16)
+NLOS_ZSPLIT(bf16)
+#undef NLOS_ZSPLIT
 
-cudaError_t launch_fk_stolt(const FkZParams& p, int tile, cudaStream_t s) {
-  if (p.npencils <= 0 || p.L != 2 * p.n || p.pad != 2) return cudaErrorInvalidValue;
-  return p.L <= 1024 ? launch_fk_stolt_r0(p, tile, s) : launch_fk_stolt_r1(p, tile, s);
+cudaError_t launch_fk_stolt(const FkZParams& p, int storage, int tile, cudaStream_t s) {
+  static cudaError_t (*const fn[3][2])(const FkZParams&, int, cudaStream_t) = {
+      {launch_fk_stolt_f32_r0, launch_fk_stolt_f32_r1},
+      {launch_fk_stolt_f16_r0, launch_fk_stolt_f16_r1},
+      {launch_fk_stolt_bf16_r0, launch_fk_stolt_bf16_r1}};
+  if (p.npencils <= 0 || p.L != 2 * p.n || p.pad != 2 || storage < 0 || storage > 2) return cudaErrorInvalidValue;
+  return fn[storage][p.L <= 1024 ? 0 : 1](p, tile, s);
 }
 
-cudaError_t launch_fk_zinv(const FkZInvParams& p, int tile, cudaStream_t s) {
-  if (p.npencils <= 0 || p.L != 2 * p.n) return cudaErrorInvalidValue;
-  return p.L <= 1024 ? launch_fk_zinv_r0(p, tile, s) : launch_fk_zinv_r1(p, tile, s);
+cudaError_t launch_fk_zinv(const FkZInvParams& p, int storage, int tile, cudaStream_t s) {
+  static cudaError_t (*const fn[3][2])(const FkZInvParams&, int, cudaStream_t) = {
+      {launch_fk_zinv_f32_r0, launch_fk_zinv_f32_r1},
+      {launch_fk_zinv_f16_r0, launch_fk_zinv_f16_r1},
+      {launch_fk_zinv_bf16_r0, launch_fk_zinv_bf16_r1}};
+  if (p.npencils <= 0 || p.L != 2 * p.n || storage < 0 || storage > 2) return cudaErrorInvalidValue;
+  return fn[storage][p.L <= 1024 ? 0 : 1](p, tile, s);
 }
 
 cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s) {
@@ -847,7 +860,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
   z.err = err;
   if (p->zlast) {
     // FK3 without its inverses: the resampled spectra of both partners
-    NLOS_CU(launch_fk_stolt(z, p->tiles[sid], s), "fk stolt stage");
+    NLOS_CU(launch_fk_stolt(z, st, p->tiles[sid], s), "fk stolt stage");
     NLOS_MARK(p, s, sid++);
     // FK4: y inverse (keep y < b) then x inverse (keep x < a), complex, into
     // the second buffer (the forward spectrum is no longer needed)
@@ -857,14 +870,14 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     c.p.mid = b0;
     c.p.out = b1;
     c.p.s1 = g2b;
-    c.p.s2 = 1.0f;
+    c.p.s2 = g2a;
     c.p.in_n = ws_extent(p, 2);
     c.p.mid_n = ws_extent(p, 0);
     c.p.out_n = std::min<long long>(ws_extent(p, 1), a * b * n);
-    c.p.discard = p->tiles[sid] < 2;
+    c.p.discard = st == kF32 && p->tiles[sid] < 2;
     c.nslot = p->tiles[sid] % 2 == 0 ? 3 : 2;
     c.fwd = 0;
-    c.store_mode = kStoreCpx32;
+    c.store_mode = kStoreCpx;   // the storage type
     const unsigned box = (unsigned)std::min<long long>(Lx, 256);
     if (!encode_3d(&c.map1, b2, cb, n, Ly, Lx, n * cb, Ly * n * cb, 8, box, false) ||
         !encode_3d(&c.map2, b0, cb, n, Lx, b, b * n * cb, n * cb, 8, box, false))
@@ -873,19 +886,22 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     NLOS_CU(launch_fk_chain(c, st, s), "fk yx-inverse");
     NLOS_MARK(p, s, sid++);
     // FK5: z inverse of the a x b kept pencils, |psi|^2 (or psi) with the normalisation
+    // (the pass scales applied before this last transform now include the x inverse's)
+    const double gz = gprod * g2a;
     FkZInvParams zi{};
-    zi.in = static_cast<const float2*>(b1);
+    zi.in = b1;
     zi.out = vol;
     zi.tw = p->tw[(int)Lt];
     zi.L = (int)Lt;
     zi.n = (int)n;
     zi.npencils = a * b;
-    zi.scale = fscale;
+    zi.scale = (float)(cpx ? 1.0 / (N * gz) : 1.0 / (N * N * gz * gz));
+    zi.dev_scale = cpx ? inv_s : inv_s2;
     zi.complex_out = cpx ? 1 : 0;
     zi.in_n = std::min<long long>(ws_extent(p, 1), a * b * n);
     zi.out_n = a * b * n;
     zi.err = err;
-    NLOS_CU(launch_fk_zinv(zi, p->tiles[sid], s), "fk z-inverse");
+    NLOS_CU(launch_fk_zinv(zi, st, p->tiles[sid], s), "fk z-inverse");
     NLOS_MARK(p, s, sid++);
     return NLOS_OK;
   }
@@ -1319,9 +1335,9 @@ nlos_status_t nlos_plan_create_ex(const nlos_plan_desc_t* desc, int flags, nlos_
   p->storage = desc->storage;
   p->fused = desc->method == NLOS_FK && !(flags & NLOS_PLAN_SEPARATE_AXES) &&
              fk_chain_eligible(p->a, p->b, p->n, p->Lx, p->Ly, desc->pad_factor);
-  // float32 plans with fused lateral stages and L = 2n take the inverse
-  // temporal transform last, on the kept pencils
-  p->zlast = p->fused && p->storage == kF32 && p->Lt == 2 * p->n;
+  // plans with fused lateral stages and L = 2n take the inverse temporal
+  // transform last, on the kept pencils
+  p->zlast = p->fused && p->Lt == 2 * p->n;
   if (p->storage != kF32) p->stage_names.push_back("volume_scale");
   const char* fk_names[] = {"fk_x_forward", "fk_y_forward", "fk_stolt_z", "fk_y_inverse", "fk_x_inverse"};
   const char* fk_fused_names[] = {"fk_xy_forward", "fk_stolt_z", "fk_yx_inverse"};

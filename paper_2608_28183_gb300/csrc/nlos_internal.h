@@ -105,27 +105,29 @@ struct FkZParams {
 };
 cudaError_t launch_fk_zstage(const FkZParams& p, int storage, int tile, cudaStream_t s);
 
-// f-k with the inverse temporal transform last (fk_zsplit.cuh; float32, L = 2n):
+// f-k with the inverse temporal transform last (fk_zsplit.cuh; L = 2n):
 // FK3 without its inverses (psi receives the resampled spectra V[kx][ky][m],
 // m < n) and FK5, the inverse temporal transform of the a x b kept pencils.
-cudaError_t launch_fk_stolt(const FkZParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_stolt(const FkZParams& p, int storage, int tile, cudaStream_t s);
 struct FkZInvParams {
-  const float2* in;            // [npencils][n] the laterally inverted spectra, m < n = L/2
+  const void* in;              // [npencils][n] the laterally inverted spectra (storage type), m < n = L/2
   void* out;                   // [npencils][n] float (|.|^2) or float2 (complex_out)
   const float2* tw;            // twiddles for L
   int L, n;
   long long npencils;          // a * b
   float scale;                 // normalisation (of |.|^2 or of the complex value)
+  const float* dev_scale;      // optional device scalar multiplying scale (16-bit storage)
   int complex_out;
   long long in_n, out_n;       // element extents (bounds-checked build; 0: unchecked)
   int* err;                    // device error word (bounds-checked build), may be null
 };
-cudaError_t launch_fk_zinv(const FkZInvParams& p, int tile, cudaStream_t s);
+cudaError_t launch_fk_zinv(const FkZInvParams& p, int storage, int tile, cudaStream_t s);
 
 // f-k lateral transforms fused in pairs (fk_chain.cuh):
 //   forward: in = H [a][b][n] real, mid = [L/2 + 1][b][n], out = G [L/2 + 1][L][n]
 //   inverse: in = psi [L][L][n], mid = [L][b][n], out = [a][b][n] float
-//            (|.|^2) or float2 (complex)
+//            (|.|^2), float2 (complex) or the storage type (complex, the
+//            spectrum whose temporal inverse comes last)
 struct FkChainParams {
   const void* in;
   void* mid;
