@@ -35,7 +35,7 @@ namespace nlos {
 
 // forward transform of the stored pencil in place in its buffer (the
 // transform's last pass reads all of the buffer before it writes)
-template <int L, class TS, bool kRamp>
+template <int L, class TS, bool kRamp, int E>
 struct FkLiteFwdCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = false;
@@ -51,17 +51,18 @@ struct FkLiteFwdCtx {
     x[0] = (valid && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), m) : make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ float2* sm(int) const { return U; }
-  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[pad16(l)] = x[0]; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[padE<E>(l)] = x[0]; }
 };
 
-template <int L, int PPC> struct FkLiteTile {
-  static constexpr int THREADS = PPC * (L / 16);
-  static constexpr size_t SMEM = sizeof(float2) * PPC * FftShape<L>::SMEM;
+// E: values per thread of the transforms (16: radix-16 passes, 32: radix-32)
+template <int L, int PPC, int E> struct FkLiteTile {
+  static constexpr int THREADS = PPC * (L / E);
+  static constexpr size_t SMEM = sizeof(float2) * PPC * FftShape<L, E>::SMEM;
 };
 
-template <int L, int PPC, class TS, bool kRamp>
-__global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_stolt_kernel(const FkZParams p) {
-  using S = FftShape<L>;
+template <int L, int PPC, class TS, bool kRamp, int E>
+__global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_stolt_kernel(const FkZParams p) {
+  using S = FftShape<L, E>;
   extern __shared__ float2 fl_sm[];
   const int w = threadIdx.x / S::TPC;
   const int j0 = threadIdx.x % S::TPC;
@@ -74,9 +75,9 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_stolt_kernel(c
   const float ldmul = p.ld_scale * (p.ld_dev_scale ? *p.ld_dev_scale : 1.0f);
   {
     const long long q = valid ? pid : 0;
-    FkLiteFwdCtx<L, TS, kRamp> ctx{static_cast<const TS*>(p.G) + q * p.n, U, p.tw, valid, ldmul, p.t_ramp,
-                                   q * p.n, p.G_n, p.err};
-    fftn_run<L, 1, true, false>(ctx, j0);
+    FkLiteFwdCtx<L, TS, kRamp, E> ctx{static_cast<const TS*>(p.G) + q * p.n, U, E == 32 ? p.tw32 : p.tw, valid,
+                                      ldmul, p.t_ramp, q * p.n, p.G_n, p.err};
+    fftn_run<L, 1, true, false, FkLiteFwdCtx<L, TS, kRamp, E>, E>(ctx, j0);
   }
   __syncthreads();
   if (!valid) return;
@@ -96,8 +97,8 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_stolt_kernel(c
     if (m >= 1) {
       const StoltCoord c = stolt_coord(A.x, A.y, m, L / 2);
       if (c.valid) {
-        const float2 u0 = U[pad16(c.k0)], u1 = U[pad16(c.k1)];
-        const float2 w0 = U[pad16((L - c.k0) & (L - 1))], w1 = U[pad16((L - c.k1) & (L - 1))];
+        const float2 u0 = U[padE<E>(c.k0)], u1 = U[padE<E>(c.k1)];
+        const float2 w0 = U[padE<E>((L - c.k0) & (L - 1))], w1 = U[padE<E>((L - c.k1) & (L - 1))];
         const float s = c.jac * p.st_scale;
         d = make_float2(s * fmaf(c.alpha, u1.x - u0.x, u0.x), s * fmaf(c.alpha, u1.y - u0.y, u0.y));
         e = make_float2(s * fmaf(c.alpha, w1.x - w0.x, w0.x), -s * fmaf(c.alpha, w1.y - w0.y, w0.y));
@@ -133,9 +134,9 @@ struct FkZInvCtx {
   }
 };
 
-template <int L, int PPC, class TS, bool kCpx>
-__global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_zinv_kernel(const FkZInvParams p) {
-  using S = FftShape<L>;
+template <int L, int PPC, class TS, bool kCpx, int E>
+__global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_zinv_kernel(const FkZInvParams p) {
+  using S = FftShape<L, E>;
   extern __shared__ float2 zi_sm[];
   const int w = threadIdx.x / S::TPC;
   const int j0 = threadIdx.x % S::TPC;
@@ -145,15 +146,15 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC>::THREADS) fk_zinv_kernel(co
   void* out = kCpx ? static_cast<void*>(static_cast<float2*>(p.out) + q * p.n)
                    : static_cast<void*>(static_cast<float*>(p.out) + q * p.n);
   const float scale = p.scale * (p.dev_scale ? *p.dev_scale : 1.0f);
-  FkZInvCtx<L, TS, kCpx> ctx{static_cast<const TS*>(p.in) + q * p.n, out, zi_sm + w * S::SMEM, p.tw, valid, scale,
-                             q * p.n, p.in_n, q * p.n, p.out_n, p.err};
-  fftn_run<L, 1, true, true>(ctx, j0);
+  FkZInvCtx<L, TS, kCpx> ctx{static_cast<const TS*>(p.in) + q * p.n, out, zi_sm + w * S::SMEM,
+                             E == 32 ? p.tw32 : p.tw, valid, scale, q * p.n, p.in_n, q * p.n, p.out_n, p.err};
+  fftn_run<L, 1, true, true, FkZInvCtx<L, TS, kCpx>, E>(ctx, j0);
 }
 
-template <int L, int PPC, class TS, bool kRamp>
+template <int L, int PPC, class TS, bool kRamp, int E = 16>
 cudaError_t launch_fk_stolt_one(const FkZParams& p, cudaStream_t s) {
-  using T = FkLiteTile<L, PPC>;
-  auto k = fk_stolt_kernel<L, PPC, TS, kRamp>;
+  using T = FkLiteTile<L, PPC, E>;
+  auto k = fk_stolt_kernel<L, PPC, TS, kRamp, E>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -163,10 +164,10 @@ cudaError_t launch_fk_stolt_one(const FkZParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-template <int L, int PPC, class TS, bool kCpx>
+template <int L, int PPC, class TS, bool kCpx, int E = 16>
 cudaError_t launch_fk_zinv_one(const FkZInvParams& p, cudaStream_t s) {
-  using T = FkLiteTile<L, PPC>;
-  auto k = fk_zinv_kernel<L, PPC, TS, kCpx>;
+  using T = FkLiteTile<L, PPC, E>;
+  auto k = fk_zinv_kernel<L, PPC, TS, kCpx, E>;
   if (T::SMEM > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::SMEM);
     if (e != cudaSuccess) return e;
@@ -176,8 +177,9 @@ cudaError_t launch_fk_zinv_one(const FkZInvParams& p, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// launch shapes 0 / 1: the two pencils-per-CTA counts of fk_ppc (the
-// ramped form, float32 only, takes shape 0)
+// launch shapes 0 / 1: radix-16 passes at the two pencils-per-CTA counts of
+// fk_ppc; 2 / 3: radix-32 passes (32 values per thread) at twice those
+// counts (the same threads per CTA). The ramped form, float32 only, takes shape 0.
 template <int L, class TS>
 cudaError_t launch_fk_stolt_len(const FkZParams& p, int tile, cudaStream_t s) {
   constexpr int P0 = fk_ppc(L, 0), P1 = fk_ppc(L, 1);
@@ -185,15 +187,31 @@ cudaError_t launch_fk_stolt_len(const FkZParams& p, int tile, cudaStream_t s) {
     if constexpr (std::is_same<TS, float2>::value) return launch_fk_stolt_one<L, P0, TS, true>(p, s);
     else return cudaErrorInvalidValue;
   }
-  return tile == 1 ? launch_fk_stolt_one<L, P1, TS, false>(p, s) : launch_fk_stolt_one<L, P0, TS, false>(p, s);
+  switch (tile) {
+    case 1: return launch_fk_stolt_one<L, P1, TS, false>(p, s);
+    case 2: return launch_fk_stolt_one<L, 2 * P0, TS, false, 32>(p, s);
+    case 3: return launch_fk_stolt_one<L, 2 * P1, TS, false, 32>(p, s);
+    default: return launch_fk_stolt_one<L, P0, TS, false>(p, s);
+  }
 }
 
 template <int L, class TS>
 cudaError_t launch_fk_zinv_len(const FkZInvParams& p, int tile, cudaStream_t s) {
   constexpr int P0 = fk_ppc(L, 0), P1 = fk_ppc(L, 1);
-  if (p.complex_out)
-    return tile == 1 ? launch_fk_zinv_one<L, P1, TS, true>(p, s) : launch_fk_zinv_one<L, P0, TS, true>(p, s);
-  return tile == 1 ? launch_fk_zinv_one<L, P1, TS, false>(p, s) : launch_fk_zinv_one<L, P0, TS, false>(p, s);
+  if (p.complex_out) {
+    switch (tile) {
+      case 1: return launch_fk_zinv_one<L, P1, TS, true>(p, s);
+      case 2: return launch_fk_zinv_one<L, 2 * P0, TS, true, 32>(p, s);
+      case 3: return launch_fk_zinv_one<L, 2 * P1, TS, true, 32>(p, s);
+      default: return launch_fk_zinv_one<L, P0, TS, true>(p, s);
+    }
+  }
+  switch (tile) {
+    case 1: return launch_fk_zinv_one<L, P1, TS, false>(p, s);
+    case 2: return launch_fk_zinv_one<L, 2 * P0, TS, false, 32>(p, s);
+    case 3: return launch_fk_zinv_one<L, 2 * P1, TS, false, 32>(p, s);
+    default: return launch_fk_zinv_one<L, P0, TS, false>(p, s);
+  }
 }
 
 }  // namespace nlos

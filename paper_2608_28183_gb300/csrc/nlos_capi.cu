@@ -892,6 +892,7 @@ nlos_status_t run_fk(nlos_plan_s* p, const void* H, void* vol, char* ws, cudaStr
     zi.in = b1;
     zi.out = vol;
     zi.tw = p->tw[(int)Lt];
+    zi.tw32 = p->tw32[(int)Lt];
     zi.L = (int)Lt;
     zi.n = (int)n;
     zi.npencils = a * b;
@@ -1712,7 +1713,8 @@ int stage_variants(const nlos_plan_s* p, size_t i) {
   if (p->stage_kind[i] == 4) return 3;   // tensor cores (persistent), FFMA, tensor cores (CTA per tile)
   // fused lateral pair: {3, 2} slots per CTA x {intermediate dropped from L2 after use, kept}
   if (p->stage_kind[i] == 5) return 4;
-  if (p->stage_kind[i] == 6) return 2;   // temporal stages of the split inverse: two pencils-per-CTA counts
+  // temporal stages of the split inverse: radix-16 / radix-32 passes x two pencils-per-CTA counts
+  if (p->stage_kind[i] == 6) return 4;
   return 1;
 }
 }  // namespace

@@ -113,6 +113,7 @@ struct FkZInvParams {
   const void* in;              // [npencils][n] the laterally inverted spectra (storage type), m < n = L/2
   void* out;                   // [npencils][n] float (|.|^2) or float2 (complex_out)
   const float2* tw;            // twiddles for L
+  const float2* tw32;          // twiddles of the radix-32 schedule for L
   int L, n;
   long long npencils;          // a * b
   float scale;                 // normalisation (of |.|^2 or of the complex value)

@@ -70,6 +70,8 @@ def test_graph_batch_matches_single_calls_and_replays():
 def test_every_launch_shape_gives_identical_volumes():
     from paper_2608_28183_gb300 import nlos
     for g, m, kw in [(synth.Geometry(64, 32, 256, 32e-12, 1.0, 1.0), "fk", {}),
+                     # fused lateral pairs, inverse temporal transform last
+                     (synth.Geometry(64, 64, 256, 32e-12, 1.0, 1.0), "fk", {}),
                      (synth.Geometry(32, 64, 512, 16e-12, 1.0, 1.0), "pf",
                       dict(n_depths=20, depth_min_m=0.4, depth_max_m=1.0))]:
         plan = nlos.plan_for_capture(g, m, "f32", **kw)
