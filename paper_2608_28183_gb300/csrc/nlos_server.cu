@@ -14,9 +14,10 @@
 //     the budget leaves next to the resident plans and running requests;
 //   - the scheduler launches outside the lock, on the slot's stream, so work
 //     that arrives while others run overlaps with them on the GPU; the
-//     stream's priority ranks the request by age (the k-th request running
-//     at its admission gets the k-th highest level), so a later arrival takes
-//     the SMs an older, larger request leaves idle instead of slowing it;
+//     stream's priority ranks the request by age (one level below the
+//     lowest-priority request running at its admission, the highest when
+//     none runs), so a later arrival takes the SMs an older, larger request
+//     leaves idle instead of slowing it;
 //   - workspaces come from the stream-ordered allocator (cudaMallocAsync /
 //     cudaFreeAsync on the slot's stream), so admissions never force a
 //     device-wide synchronisation;
@@ -87,6 +88,7 @@ constexpr int kPrioLevels = 4;
 struct Slot {
   cudaStream_t prio[kPrioLevels] = {};   // one stream per level, highest first
   cudaStream_t stream = nullptr;         // the running request's stream
+  int level = 0;                         // and its level
   Request* req = nullptr;
   Done done;
 };
@@ -189,13 +191,17 @@ void scheduler(nlos_server_s* sv) {
         }
       if (slot) evict_idle(sv, head->need, victims);
       if (slot && sv->resident + sv->in_use + head->need <= sv->budget) {
-        int running = 0;
-        for (Slot& sl : sv->slots) running += sl.req ? 1 : 0;
+        // one level below the lowest-priority running request (the highest
+        // level when none runs)
+        int level = 0;
+        for (Slot& sl : sv->slots)
+          if (sl.req) level = std::max(level, std::min(sl.level + 1, kPrioLevels - 1));
         r = head;
         sv->queue.pop_front();
         r->state = 1;
         slot->req = r;
-        slot->stream = slot->prio[std::min(running, kPrioLevels - 1)];
+        slot->level = level;
+        slot->stream = slot->prio[level];
         sv->in_use += r->need;
       }
     }
