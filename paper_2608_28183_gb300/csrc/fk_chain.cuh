@@ -120,6 +120,27 @@ struct ChainMidCtx : AxisTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> {
   }
 };
 
+// the second transform of either chain: its output is not read again while
+// the chain runs, so it is stored evict-first and leaves L2 to the intermediate
+template <int L, int IC, int ST, class TS>
+struct ChainOutCtx : ChainTmaCtx<L, IC, kLoadCpx, ST, TS> {
+  uint64_t stream;
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const {
+    float2 v = x[0];
+    if (!this->valid || l >= this->L_out) return;
+    const long long o = this->out_base + l * this->out_axis;
+    if (!bchk(o, this->out_n, this->err)) return;
+    if constexpr (ST == kStoreAbs2) {
+      st_global_hint(static_cast<float*>(this->out) + o, fmaf(v.x, v.x, v.y * v.y) * this->stmul, stream);
+    } else {
+      if (this->inverse) v = cconj(v);
+      v = cscale(v, this->stmul);
+      if constexpr (ST == kStoreCpx32 || sizeof(TS) == 8) st_global_hint(static_cast<float2*>(this->out) + o, v, stream);
+      else Cpx<TS>::put(static_cast<TS*>(this->out) + o, v);
+    }
+  }
+};
+
 template <int L> __device__ __forceinline__ void consumer_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(ChainTile<L>::CONSUMERS) : "memory");
 }
@@ -255,6 +276,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
 
   // ------------------------------ consumers ------------------------------
   const uint64_t keep = l2_policy_evict_last();
+  const uint64_t once = l2_policy_evict_first();
   const int c = threadIdx.x % IC;
   const int j0 = threadIdx.x / IC;
   const float ldm = p.ld_dev_scale ? *p.ld_dev_scale : 1.0f;
@@ -311,9 +333,11 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
           }
         }
       } else if (kFwd) {
-        // y forward of kx = idx: rows y < b, all L outputs
-        ChainTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS> ctx;
+        // y forward of kx = idx: rows y < b, all L outputs (stored evict-first:
+        // the spectrum is read by the next stage, after this one)
+        ChainOutCtx<L, IC, kStoreCpx, TS> ctx;
         chain_ctx(ctx, buf(slot), tw, c, 0);
+        ctx.stream = once;
         ctx.out = p.out;
         ctx.out_n = p.out_n;
         ctx.err = p.err;
@@ -322,7 +346,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         ctx.L_in = p.b;
         ctx.L_out = L;
         ctx.stmul = p.s2;
-        fftn_run<L, 1, true, false, ChainTmaCtx<L, IC, kLoadCpx, kStoreCpx, TS>, E>(ctx, j0);
+        fftn_run<L, 1, true, false, ChainOutCtx<L, IC, kStoreCpx, TS>, E>(ctx, j0);
       } else if (!it.second) {
         // y inverse of kx = idx: keep y < b
         ChainMidCtx<L, IC, TS> ctx;
@@ -339,8 +363,9 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         fftn_run<L, 1, false, true, ChainMidCtx<L, IC, TS>, E>(ctx, j0);
       } else {
         // x inverse of wall row y = idx: keep x < a, |.|^2 (or complex)
-        ChainTmaCtx<L, IC, kLoadCpx, ST, TS> ctx;
+        ChainOutCtx<L, IC, ST, TS> ctx;
         chain_ctx(ctx, buf(slot), tw, c, 1);
+        ctx.stream = once;
         ctx.out = p.out;
         ctx.out_n = p.out_n;
         ctx.err = p.err;
@@ -349,7 +374,7 @@ fk_chain_kernel(const __grid_constant__ CUtensorMap map1, const __grid_constant_
         ctx.L_in = L;
         ctx.L_out = p.a;
         ctx.stmul = p.s2 * std_;
-        fftn_run<L, 1, false, true, ChainTmaCtx<L, IC, kLoadCpx, ST, TS>, E>(ctx, j0);
+        fftn_run<L, 1, false, true, ChainOutCtx<L, IC, ST, TS>, E>(ctx, j0);
       }
     }
     // no consumer touches the slot any more: order the shared-memory

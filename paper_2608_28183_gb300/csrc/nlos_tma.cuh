@@ -111,6 +111,11 @@ __device__ __forceinline__ void st_global_hint(float2* p, float2 v, uint64_t pol
                : "memory");
 }
 
+// 4-byte global store with an L2 cache-eviction policy
+__device__ __forceinline__ void st_global_hint(float* p, float v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(policy) : "memory");
+}
+
 // tma_load_3d with an L2 cache-eviction policy for the lines it reads
 __device__ __forceinline__ void tma_load_3d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1,
                                                  int c2, uint64_t policy) {
