@@ -73,13 +73,17 @@ def test_every_launch_shape_gives_identical_volumes():
                      # fused lateral pairs, inverse temporal transform last
                      (synth.Geometry(64, 64, 256, 32e-12, 1.0, 1.0), "fk", {}),
                      (synth.Geometry(32, 64, 512, 16e-12, 1.0, 1.0), "pf",
-                      dict(n_depths=20, depth_min_m=0.4, depth_max_m=1.0))]:
+                      dict(n_depths=20, depth_min_m=0.4, depth_max_m=1.0)),
+                     # fused y-then-x inverse
+                     (synth.Geometry(64, 64, 512, 16e-12, 1.0, 1.0), "pf",
+                      dict(n_depths=32, depth_min_m=0.4, depth_max_m=1.0))]:
         plan = nlos.plan_for_capture(g, m, "f32", **kw)
         cap = synth.render(g, synth.Scene(points=np.array([(0.1, 0.05, 0.6, 1.0)])), peak=100.0,
                            background=0.5, seed=5)
         x = to_device(cap.counts, torch.float32)
         base = plan.reconstruct(x).clone()
         n = len(plan.tiles)
+        names = [nlos.load_library().nlos_plan_stage_name(plan.handle, i).decode() for i in range(n)]
         for stage in range(n):
             for v in range(1, 10):
                 tiles = [0] * n
@@ -90,9 +94,12 @@ def test_every_launch_shape_gives_identical_volumes():
                     continue          # stage has fewer variants
                 got = plan.reconstruct(x)
                 # same arithmetic up to rounding order (packing two real columns
-                # per transform in the x pass rounds differently)
+                # per transform in the x pass rounds differently); the phasor
+                # depth sum's FMA form against its three f16-part products
+                # differs by the dropped lo x lo term (~2^-22 per product)
                 err = float(torch.linalg.vector_norm((got - base).double()) / torch.linalg.vector_norm(base.double()))
-                assert err <= 1e-6, (stage, v, err)
+                tol = 5e-6 if names[stage] == "pf_depth_sum" else 1e-6
+                assert err <= tol, (names[stage], v, err)
 
 
 def test_autotune_picks_valid_shapes_and_caches():
