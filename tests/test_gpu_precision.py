@@ -113,3 +113,26 @@ def test_pf_fp16_tensor_core_and_ffma_depth_sums(depths):
     assert rel_l2(out[0], out[1]) <= 2e-3
     # the persistent form adds the parts of split tail tiles with f16 atomics
     assert rel_l2(out[2], out[0]) <= 1e-3
+
+
+@pytest.mark.parametrize("storage,output,tol", [("f16", "magnitude", 2e-3), ("f16", "complex", 2e-3),
+                                                ("bf16", "magnitude", 3e-2)])
+def test_fk_reduced_precision_inverse_temporal_last(storage, output, tol):
+    """A fused 64 x 64 x 256 plan takes the inverse temporal transform last in
+    16-bit storage too (the kept spectrum stored in the storage type with its
+    pass scale, the volume scale applied by the last stage)."""
+    from paper_2608_28183_gb300 import nlos
+    g = synth.Geometry(64, 64, 256, 32e-12, 1.0, 1.0)
+    plan = nlos.plan_for_capture(g, "fk", storage, output=output)
+    names = [nlos.load_library().nlos_plan_stage_name(plan.handle, i).decode() for i in range(len(plan.tiles))]
+    assert "fk_z_inverse" in names
+    cap = synth.make_capture("fk_32x32x256", 0, geom=g)
+    dt = plan.input_dtype()
+    got = plan.reconstruct(to_device(cap.counts, dt)).cpu().numpy()
+    cpx = output == "complex"
+    ref = fk.fk_reconstruct(exact_input(cap.counts, dt), g.bin_width_s, g.wall_w_m, g.wall_h_m, return_complex=cpx)
+    err = rel_l2(got.astype(np.complex128 if cpx else np.float64), ref)
+    print(f"f-k {storage} {output} 64x64x256 rel L2 {err:.3e}")
+    assert err <= tol
+    if storage == "f16":
+        assert same_peak(np.abs(got), np.abs(ref), rtol=2e-3)
