@@ -258,8 +258,9 @@ nlos_status_t nlos_batch_destroy(nlos_batch_t batch);
 /*
  * Continuous-batching server (Sec. 4.1's producer-consumer front end, served
  * from many clients). Requests of any description are queued by any thread
- * and served by one scheduler thread: plans are created once per distinct
- * description and stay resident; memory_budget_bytes covers the resident
+ * and served by one scheduler thread: plans are created and autotuned
+ * (nlos_plan_autotune, whose process-wide cache serves repeats) once per
+ * distinct description and stay resident; memory_budget_bytes covers the resident
  * plans (tables, radial kernels, tensor-core operand stores, dense kernels)
  * and the workspaces of running requests, and idle plans (no request queued
  * or running) are evicted least recently used first when a new plan or an

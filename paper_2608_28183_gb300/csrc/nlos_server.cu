@@ -2,8 +2,9 @@
 //
 // Requests (a capture description plus caller-owned device input and output
 // buffers) are queued by any thread and served by one scheduler thread:
-//   - plans are created once per distinct description (outside the queue's
-//     lock, so running work is not held up) and stay resident on the device;
+//   - plans are created and autotuned once per distinct description (outside
+//     the queue's lock, so running work is not held up) and stay resident on
+//     the device;
 //   - the memory budget covers both the resident plans (tables, twiddles,
 //     radial kernels, tensor-core operand stores, dense kernels) and the
 //     workspaces of the requests on the device; a new plan that does not fit
@@ -268,6 +269,12 @@ nlos_status_t acquire_plan(nlos_server_s* sv, const nlos_plan_desc_t& d, PlanEnt
     snprintf(msg, sizeof msg, "plan (%zu bytes) and workspace (%zu bytes) exceed the budget of %zu bytes", bytes,
              need, sv->budget);
     return nlos::set_error(NLOS_ERR_OUT_OF_MEMORY, msg);
+  }
+  // launch shapes picked once per description (the process-wide autotune
+  // cache): a resident plan serves every later request with the tuned shapes
+  if ((st = nlos_plan_autotune(p, nullptr)) != NLOS_OK) {
+    nlos_plan_destroy(p);
+    return st;
   }
   std::vector<nlos_plan_t> victims;
   {

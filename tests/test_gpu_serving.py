@@ -1,7 +1,7 @@
 """Continuous-batching server: requests of mixed sizes, methods and storage
 types submitted back to back overlap on the device, and every result equals
-the standalone reconstruction of the same capture bit for bit (same alone and
-in the mix). The memory budget covers resident plans and running workspaces."""
+the standalone reconstruction of the same capture (with the same autotuned
+launch shapes) bit for bit (same alone and in the mix). The memory budget covers resident plans and running workspaces."""
 import numpy as np
 import pytest
 
@@ -46,6 +46,7 @@ def test_results_identical_alone_and_in_the_mix():
         desc = nlos.desc_for_capture(g, m, st, **kw)
         server.preload(desc)
         plan = nlos.plan_for_capture(g, m, st, **kw)
+        plan.autotune()          # the server's launch shapes (the autotune cache is process-wide)
         x = to_device(cap.counts, plan.input_dtype())
         alone.append(plan.reconstruct(x).clone())
         inputs.append((desc, x))
@@ -65,6 +66,7 @@ def test_budget_admission_serialises_and_rejects():
     from paper_2608_28183_gb300 import nlos
     g = synth.Geometry(64, 64, 512, 16e-12, 1.0, 1.0)
     plan = nlos.plan_for_capture(g, "fk", "f32")
+    plan.autotune()              # the launch shapes the server's plan will take from the shared cache
     need = plan.workspace_bytes
     server = nlos.Server(memory_budget_bytes=need + need // 2, n_slots=4)   # one at a time fits
     desc = nlos.desc_for_capture(g, "fk", "f32")
@@ -97,6 +99,8 @@ def test_plan_memory_counts_and_idle_plans_give_way():
         kw = dict(n_depths=48, depth_min_m=0.4, depth_max_m=nt * g.bin_depth_m)
         shapes.append((g, kw))
     plans = [nlos.plan_for_capture(g, "pf", "f32", **kw) for g, kw in shapes]
+    for p in plans:
+        p.autotune()             # the launch shapes the server's plans will take from the shared cache
     # what a plan holds besides its own default workspace (the server's plans have none)
     sizes = [p.resident_bytes - p.workspace_bytes for p in plans]
     assert min(sizes) > 1 << 20                       # tables and kernels, not just the workspace
