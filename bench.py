@@ -295,11 +295,13 @@ def batch_bench(torch, nlos, synth, reps=20):
             "max_rel_l2_fp16_vs_fp32": rel, "autotuned": True}
 
 
-def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000, 0), seconds=2.0, budget_gb=120, saturating_n=1000):
-    """Poisson arrivals at each rate; each request a capture of side 32..256
-    and 256/512/1024 bins, f-k or phasor at 50/50, FP16, through the
+def serving_bench(torch, nlos, synth, rates=(10, 100, 500, 2000, 0), seconds=4.0, budget_gb=120, saturating_n=1000):
+    """Poisson arrivals at each rate for `seconds` (4 s: the p99 of a few
+    thousand requests); each request a capture of side 32..256 and
+    256/512/1024 bins, f-k or phasor at 50/50, FP16, through the
     continuous-batching server (budget 120 GB for plans and workspaces, 8
-    slots); against the plain FP32 one-at-a-time path fed by the same
+    slots, plans autotuned once when created); against the plain FP32
+    one-at-a-time path fed by the same
     arrivals. Rate 0 is the saturating point: saturating_n requests offered at
     once (more than either arm serves per second), so volumes/s measures
     capacity."""
