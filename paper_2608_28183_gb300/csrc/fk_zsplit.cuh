@@ -33,12 +33,21 @@
 
 namespace nlos {
 
+// Barrier threads of a transform context: a warp where the transform is one
+// warp (L / E = 32 threads, each pencil's buffer private to its warp), else
+// the CTA.
+template <int L, int E> constexpr int fk_lite_bar() { return FftShape<L, E>::TPC == 32 ? 32 : 0; }
+
 // forward transform of the stored pencil in place in its buffer (the
-// transform's last pass reads all of the buffer before it writes)
+// transform's last pass reads all of the buffer before it writes). The last
+// pass stores the spectrum unpadded, U[l]: its lanes write consecutive l, and
+// the Stolt gather then indexes U without the padding arithmetic. The load
+// scale of the non-ramped form is applied after the transform (it is linear).
 template <int L, class TS, bool kRamp, int E>
 struct FkLiteFwdCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = false;
+  static constexpr int kBarThreads = fk_lite_bar<L, E>();
   const TS* g;
   float2* U;
   const float2* tw;
@@ -47,21 +56,31 @@ struct FkLiteFwdCtx {
   long long g_off, g_n;
   int* err;
   __device__ __forceinline__ void load(int l, float2 (&x)[1]) const {
-    const float m = kRamp ? ldmul * (float)l * t_ramp : ldmul;
-    x[0] = (valid && bchk(g_off + l, g_n, err)) ? cscale(Cpx<TS>::get(g + l), m) : make_float2(0.f, 0.f);
+    if (!(valid && bchk(g_off + l, g_n, err))) {
+      x[0] = make_float2(0.f, 0.f);
+    } else if constexpr (kRamp) {
+      x[0] = cscale(Cpx<TS>::get(g + l), ldmul * (float)l * t_ramp);
+    } else {
+      x[0] = Cpx<TS>::get(g + l);
+    }
   }
   __device__ __forceinline__ float2* sm(int) const { return U; }
-  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[padE<E>(l)] = x[0]; }
+  __device__ __forceinline__ void store(int l, const float2 (&x)[1]) const { U[l] = x[0]; }
 };
 
 // E: values per thread of the transforms (16: radix-16 passes, 32: radix-32)
+// MINB: CTAs per SM the register allocation must allow (0: left to the
+// compiler). The radix-32 length-1024 form (one warp per transform) keeps to
+// 80 registers per thread: six 128-thread CTAs, which its shared memory also
+// allows.
 template <int L, int PPC, int E> struct FkLiteTile {
   static constexpr int THREADS = PPC * (L / E);
   static constexpr size_t SMEM = sizeof(float2) * PPC * FftShape<L, E>::SMEM;
+  static constexpr int MINB = (E == 32 && L == 1024 && THREADS * 80 <= 65536) ? 65536 / (THREADS * 80) : 0;
 };
 
 template <int L, int PPC, class TS, bool kRamp, int E>
-__global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_stolt_kernel(const FkZParams p) {
+__global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS, FkLiteTile<L, PPC, E>::MINB) fk_stolt_kernel(const FkZParams p) {
   using S = FftShape<L, E>;
   extern __shared__ float2 fl_sm[];
   const int w = threadIdx.x / S::TPC;
@@ -79,7 +98,8 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_stolt_kerne
                                       ldmul, p.t_ramp, q * p.n, p.G_n, p.err};
     fftn_run<L, 1, true, false, FkLiteFwdCtx<L, TS, kRamp, E>, E>(ctx, j0);
   }
-  __syncthreads();
+  if constexpr (fk_lite_bar<L, E>() == 32) __syncwarp();
+  else __syncthreads();
   if (!valid) return;
   const float2 ax = p.ax[kx];
   const float2 ay = p.ay[ky];
@@ -92,16 +112,21 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_stolt_kerne
   const long long o1 = ((long long)mkx * twob + mky) * p.n;
   // the partner is stored only where it is not itself a stored pencil
   const bool partner = kx > 0 && 2 * kx < p.a_pad;
+  const float st = kRamp ? p.st_scale : p.st_scale * ldmul;
   for (int m = j0; m < L / 2; m += S::TPC) {
     float2 d = make_float2(0.f, 0.f), e = d;
     if (m >= 1) {
       const StoltCoord c = stolt_coord(A.x, A.y, m, L / 2);
       if (c.valid) {
-        const float2 u0 = U[padE<E>(c.k0)], u1 = U[padE<E>(c.k1)];
-        const float2 w0 = U[padE<E>((L - c.k0) & (L - 1))], w1 = U[padE<E>((L - c.k1) & (L - 1))];
-        const float s = c.jac * p.st_scale;
-        d = make_float2(s * fmaf(c.alpha, u1.x - u0.x, u0.x), s * fmaf(c.alpha, u1.y - u0.y, u0.y));
-        e = make_float2(s * fmaf(c.alpha, w1.x - w0.x, w0.x), -s * fmaf(c.alpha, w1.y - w0.y, w0.y));
+        // k0 + 1 <= L/2 is in the spectrum; at k0 = L/2 - 1 its weight alpha is 0
+        const int k1 = c.k0 + 1;
+        const float2 u0 = U[c.k0], u1 = U[k1];
+        const float2 w0 = U[(L - c.k0) & (L - 1)], w1 = U[(L - k1) & (L - 1)];
+        // (1 - alpha) u0 + alpha u1, times the Jacobian m/mu and the scale
+        const float b1 = c.jac * st * c.alpha;
+        const float b0 = fmaf(c.jac, st, -b1);
+        d = make_float2(fmaf(b1, u1.x, b0 * u0.x), fmaf(b1, u1.y, b0 * u0.y));
+        e = make_float2(fmaf(b1, w1.x, b0 * w0.x), -fmaf(b1, w1.y, b0 * w0.y));
       }
     }
     if (bchk(o0 + m, p.psi_n, p.err)) Cpx<TS>::put(V + o0 + m, d);
@@ -111,10 +136,11 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_stolt_kerne
 
 // inverse temporal transform of a kept pencil as conj(DFT(conj(V))): input
 // m < L/2 (the upper half is zero), output z < L/2
-template <int L, class TS, bool kCpx>
+template <int L, class TS, bool kCpx, int E>
 struct FkZInvCtx {
   static constexpr int SSTRIDE = 1;
   static constexpr bool kSmemInput = false;
+  static constexpr int kBarThreads = fk_lite_bar<L, E>();
   const TS* in;
   void* out;
   float2* W;
@@ -135,7 +161,7 @@ struct FkZInvCtx {
 };
 
 template <int L, int PPC, class TS, bool kCpx, int E>
-__global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_zinv_kernel(const FkZInvParams p) {
+__global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS, FkLiteTile<L, PPC, E>::MINB) fk_zinv_kernel(const FkZInvParams p) {
   using S = FftShape<L, E>;
   extern __shared__ float2 zi_sm[];
   const int w = threadIdx.x / S::TPC;
@@ -146,9 +172,9 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS) fk_zinv_kernel
   void* out = kCpx ? static_cast<void*>(static_cast<float2*>(p.out) + q * p.n)
                    : static_cast<void*>(static_cast<float*>(p.out) + q * p.n);
   const float scale = p.scale * (p.dev_scale ? *p.dev_scale : 1.0f);
-  FkZInvCtx<L, TS, kCpx> ctx{static_cast<const TS*>(p.in) + q * p.n, out, zi_sm + w * S::SMEM,
+  FkZInvCtx<L, TS, kCpx, E> ctx{static_cast<const TS*>(p.in) + q * p.n, out, zi_sm + w * S::SMEM,
                              E == 32 ? p.tw32 : p.tw, valid, scale, q * p.n, p.in_n, q * p.n, p.out_n, p.err};
-  fftn_run<L, 1, true, true, FkZInvCtx<L, TS, kCpx>, E>(ctx, j0);
+  fftn_run<L, 1, true, true, FkZInvCtx<L, TS, kCpx, E>, E>(ctx, j0);
 }
 
 template <int L, int PPC, class TS, bool kRamp, int E = 16>
