@@ -199,9 +199,9 @@ nlos_status_t nlos_reconstruct_batch(const nlos_plan_t* plans, const void* const
  * reconstruction time: real-time loops, where an allocation may synchronise
  * the device and stall a frame, and applications that give this library a
  * fixed share of device memory and manage the rest in their own pool.) The
- * plan must already exist. The first call on each device looks the array's
- * address up with cudaGetSymbolAddress and should come before any stream
- * capture. Errors: INVALID_ARG if the plan's workspace_bytes exceed 32 MiB,
+ * plan must already exist. The first call on each device also looks the
+ * array's address up with cudaGetSymbolAddress (a synchronous runtime call;
+ * later calls on that device reuse it). Errors: INVALID_ARG if the plan's workspace_bytes exceed 32 MiB,
  * if an argument is NULL, or if stage tracing is enabled on the plan; CUDA if
  * the lookup fails. All calls share the array, which keeps the previous
  * call's contents: calls that overlap on the GPU race and must be serialised

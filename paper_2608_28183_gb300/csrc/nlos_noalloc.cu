@@ -14,9 +14,9 @@
 // (32 MiB). Every GPU that loads this library holds its own copy until the
 // process exits. Host code only sees a host-side stand-in for the array's
 // name, so the device address is looked up with cudaGetSymbolAddress once per
-// device (with that device current) and cached; that lookup happens in the
-// first call on each device, which should therefore come before any stream
-// capture. Plans whose workspace exceeds the array are rejected with
+// device (with that device current) and cached; that synchronous lookup
+// happens in the first call on each device only. Plans whose workspace
+// exceeds the array are rejected with
 // NLOS_ERR_INVALID_ARG. Every call shares the array and it keeps the previous
 // call's contents: each stage writes its scratch before reading it, and the
 // only accumulator (the phasor-field depth sum) is cleared by the sequence
