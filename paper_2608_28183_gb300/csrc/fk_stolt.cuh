@@ -52,4 +52,43 @@ __device__ __forceinline__ StoltCoord stolt_coord(float Ahi, float Alo, int m, i
   return c;
 }
 
+// The same coordinate from a per-pencil split of A into an integer and a
+// fraction: S = A + m^2 = (Ai + m^2) + Af, where Ai + m^2 is an exact integer
+// (below 2^24 wherever the source can lie in a spectrum: mu < L/2 <= 4096)
+// and Af = A - Ai in [0, 1] is one float (absolute error <= 2^-25, so mu to
+// about 1.5e-8 / mu). S then takes one exact sum instead of two, and the
+// weight's rollover at an integer one floor instead of two branches.
+struct StoltSplitA {
+  int Ai;
+  float Af;
+};
+__device__ __forceinline__ StoltSplitA stolt_split_a(float Ahi, float Alo) {
+  // sources with A >= 2^24 lie outside every spectrum; clamping keeps Ai + m^2 in range
+  const float h = fminf(Ahi, 16777216.f);
+  const int Ai = (int)h;   // floor: A >= 0; h - Ai is exact
+  return {Ai, (h - (float)Ai) + Alo};
+}
+// m >= 1, fm = (float)m
+__device__ __forceinline__ StoltCoord stolt_coord_split(const StoltSplitA& a, int m, float fm, int n) {
+  StoltCoord c;
+  const float sx = (float)(a.Ai + m * m);
+  const float sh = sx + a.Af;                 // |sx| >= 1 > |Af|: fast two-sum
+  const float sl = a.Af - (sh - sx);
+  const float rs = rsqrtf(sh);
+  const float y0 = sh * rs;
+  const float res = fmaf(-y0, y0, sh) + sl;   // S - y0^2
+  const float mlo = res * (0.5f * rs);        // mu = y0 + mlo
+  int k0 = (int)floorf(y0);
+  float al = (y0 - (float)k0) + mlo;
+  const float roll = floorf(al);              // -1, 0 or 1: y0 is within a few ulp of mu
+  k0 += (int)roll;
+  al -= roll;
+  c.valid = (k0 < n - 1) || (k0 == n - 1 && al == 0.f);
+  c.k0 = k0;
+  c.k1 = k0 + 1;
+  c.alpha = al;
+  c.jac = fm * rs;
+  return c;
+}
+
 }  // namespace nlos

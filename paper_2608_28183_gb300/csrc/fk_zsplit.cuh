@@ -113,13 +113,15 @@ __global__ void __launch_bounds__(FkLiteTile<L, PPC, E>::THREADS, FkLiteTile<L, 
   // the partner is stored only where it is not itself a stored pencil
   const bool partner = kx > 0 && 2 * kx < p.a_pad;
   const float st = kRamp ? p.st_scale : p.st_scale * ldmul;
-  for (int m = j0; m < L / 2; m += S::TPC) {
+  const StoltSplitA As = stolt_split_a(A.x, A.y);
+  float fm = (float)j0;
+  for (int m = j0; m < L / 2; m += S::TPC, fm += (float)S::TPC) {
     float2 d = make_float2(0.f, 0.f), e = d;
     if (m >= 1) {
-      const StoltCoord c = stolt_coord(A.x, A.y, m, L / 2);
+      const StoltCoord c = stolt_coord_split(As, m, fm, L / 2);
       if (c.valid) {
         // k0 + 1 <= L/2 is in the spectrum; at k0 = L/2 - 1 its weight alpha is 0
-        const int k1 = c.k0 + 1;
+        const int k1 = c.k1;
         const float2 u0 = U[c.k0], u1 = U[k1];
         const float2 w0 = U[(L - c.k0) & (L - 1)], w1 = U[(L - k1) & (L - 1)];
         // (1 - alpha) u0 + alpha u1, times the Jacobian m/mu and the scale
