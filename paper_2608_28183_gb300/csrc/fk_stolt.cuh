@@ -63,16 +63,17 @@ struct StoltSplitA {
   float Af;
 };
 __device__ __forceinline__ StoltSplitA stolt_split_a(float Ahi, float Alo) {
-  // sources with A >= 2^24 lie outside every spectrum; clamping keeps Ai + m^2 in range
-  const float h = fminf(Ahi, 16777216.f);
-  const int Ai = (int)h;   // floor: A >= 0; h - Ai is exact
-  return {Ai, (h - (float)Ai) + Alo};
+  // sources with A >= 2^24 lie outside every spectrum: A is clamped to
+  // exactly 2^24 (and the sum stays positive and in range); so is a NaN
+  if (!(Ahi < 16777216.f)) return {16777216, 0.f};
+  const int Ai = (int)Ahi;   // floor: A >= 0; Ahi - Ai is exact
+  return {Ai, (Ahi - (float)Ai) + Alo};
 }
 // m >= 1, fm = (float)m
 __device__ __forceinline__ StoltCoord stolt_coord_split(const StoltSplitA& a, int m, float fm, int n) {
   StoltCoord c;
   const float sx = (float)(a.Ai + m * m);
-  const float sh = sx + a.Af;                 // |sx| >= 1 > |Af|: fast two-sum
+  const float sh = sx + a.Af;                 // |sx| >= 1 >= |Af|: fast two-sum
   const float sl = a.Af - (sh - sx);
   const float rs = rsqrtf(sh);
   const float y0 = sh * rs;
