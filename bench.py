@@ -33,11 +33,16 @@ METRIC = "recon volumes/s + p50/p99 ms at 256x256x512 f-k; HBM GB/s vs peak"
 UNIT = "volumes/s"
 PAPER_SECONDS_PER_VOLUME = 0.143   # offline f-k 256x256x512, padded, FP32, RTX 4080 SUPER (incl. alloc/free)
 FALLBACK_HBM_GBS = 6800.0
-# sources of the f-k kernels (temporal-frequency stage, fused lateral pairs);
-# a change to them invalidates the committed DRAM-traffic figures
-KERNEL_SOURCES = ["paper_2608_28183_gb300/csrc/nlos_fft.cuh", "paper_2608_28183_gb300/csrc/fk_zstage.cuh",
-                  "paper_2608_28183_gb300/csrc/fk_chain.cuh", "paper_2608_28183_gb300/csrc/axis_fft.cuh",
-                  "paper_2608_28183_gb300/csrc/fk_zsplit.cuh"]
+# sources each f-k stage's kernel is built from (its translation unit and the
+# headers it includes); a change to them invalidates that stage's committed
+# DRAM-traffic figure
+_CSRC = "paper_2608_28183_gb300/csrc/"
+_CHAIN_SOURCES = ["fk_chain.cuh", "fk_chain_f32.cu", "axis_fft.cuh", "nlos_fft.cuh", "nlos_tma.cuh",
+                  "nlos_bounds.cuh", "nlos_internal.h"]
+_ZSPLIT_SOURCES = ["fk_zsplit.cuh", "fk_zsplit_f32_r0.cu", "fk_stolt.cuh", "fk_zstage.cuh", "fk_zwarp.cuh",
+                   "nlos_fft.cuh", "nlos_bounds.cuh", "nlos_internal.h"]
+STAGE_SOURCES = {"fk_xy_forward": _CHAIN_SOURCES, "fk_yx_inverse": _CHAIN_SOURCES,
+                 "fk_stolt": _ZSPLIT_SOURCES, "fk_z_inverse": _ZSPLIT_SOURCES}
 
 
 def parse_args():
@@ -124,24 +129,34 @@ def pipeline_bytes(a, b, n, storage):
     return V * (104 if storage == "f32" else 54)
 
 
-def kernel_hash():
+def sources_hash(contents):
+    """Hash of a list of source files' bytes, in order."""
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+    for c in contents:
+        h.update(c)
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(stage):
-    """DRAM bytes per launch of `stage` from the committed ncu summary, or None
-    if there is none or the kernels changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "fk_256x256x512_traffic.json")
+def stage_hash(stage):
+    """Hash of the sources `stage`'s kernel is built from, as they are now."""
+    contents = []
+    for name in STAGE_SOURCES[stage]:
+        with open(os.path.join(ROOT, _CSRC + name), "rb") as f:
+            contents.append(f.read())
+    return sources_hash(contents)
+
+
+def profiled_traffic(stage, path=None):
+    """DRAM bytes per launch of `stage` from the committed ncu summary (or the
+    summary at `path`), or None if there is none or that stage's kernel
+    sources changed since it was taken."""
+    path = path or os.path.join(ROOT, "profiles", "fk_256x256x512_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
     except Exception:
         return None
-    if d.get("kernel_hash") != kernel_hash():
+    if stage not in STAGE_SOURCES or d.get("kernel_hashes", {}).get(stage) != stage_hash(stage):
         return None
     return d.get("dram_bytes_per_launch", {}).get(stage)
 

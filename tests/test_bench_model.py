@@ -67,8 +67,22 @@ def test_committed_traffic_summary_uses_the_same_algorithmic_bytes(bench):
     with open(os.path.join(ROOT, "profiles", "fk_256x256x512_traffic.json")) as f:
         d = json.load(f)
     sb = bench.stage_bytes(256, 256, 512, "f32", zlast=True)
+    # each stage's figure is tied to the sources its kernel is built from
+    assert set(d["kernel_hashes"]) == set(bench.STAGE_SOURCES) == set(d["per_stage"])
     for stage, rec in d["per_stage"].items():
         assert rec["algorithmic_bytes"] == sb[stage], stage
         assert d["dram_bytes_per_launch"][stage] == rec["dram_read"] + rec["dram_write"]
         assert rec["traffic_over_algorithmic"] == pytest.approx(
             (rec["dram_read"] + rec["dram_write"]) / rec["algorithmic_bytes"], abs=1e-3)
+
+
+def test_traffic_is_reported_only_while_the_stage_sources_match(bench, tmp_path):
+    d = {"kernel_hashes": {s: bench.stage_hash(s) for s in bench.STAGE_SOURCES},
+         "dram_bytes_per_launch": {s: 1000 + i for i, s in enumerate(bench.STAGE_SOURCES)}}
+    d["kernel_hashes"]["fk_stolt"] = "0" * 16          # as if the Stolt kernel changed since
+    path = tmp_path / "traffic.json"
+    path.write_text(json.dumps(d))
+    assert bench.profiled_traffic("fk_yx_inverse", str(path)) == d["dram_bytes_per_launch"]["fk_yx_inverse"]
+    assert bench.profiled_traffic("fk_stolt", str(path)) is None
+    assert bench.profiled_traffic("no_such_stage", str(path)) is None
+    assert bench.profiled_traffic("fk_yx_inverse", str(tmp_path / "missing.json")) is None
